@@ -1,0 +1,139 @@
+"""CPU oracle for the GAP PageRank kernel — TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, single-threaded FP64 code (``gap_oracle.c``, built with
+``-ffp-contract=off``) that states what the CUDA path computes:
+
+* :func:`build_csr` / :func:`build_csc` — CSR construction with the cleaning
+  steps paper §2.3 allows (drop self-loops and duplicates, sort neighbours).
+* :func:`pagerank` — the §2.1 PageRank equation iterated in the push
+  direction from x0 = 1/n until the summed change drops below tol (§2.1
+  tolerance equation), or for a fixed count with tol = 0.
+* :func:`verify` — the §3 verifier: one extra serial push iteration, returning
+  the summed absolute change (correct when below 1e-4).
+* :func:`ppr` — personalized PageRank (not in the paper): teleport (1-d)/|S|
+  on a seed set S instead of (1-d)/n.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path.
+Every function here is pinned by ``tests/test_oracle_pins.py`` against
+closed forms, dense linear solves and invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gap_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lib = None
+
+DAMPING = 0.85
+TOL = 1e-4
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so in-tree (gcc -O2 -ffp-contract=off, single-threaded)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+        lib.oracle_build_csr.argtypes = [i64, i64, vp, vp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, vp, vp, ctypes.POINTER(i64)]
+        lib.oracle_pagerank.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, vp]
+        lib.oracle_pr_verify.argtypes = [i64, vp, vp, dbl, vp, ctypes.POINTER(dbl)]
+        lib.oracle_ppr.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, i32, vp, vp]
+        for f in (lib.oracle_build_csr, lib.oracle_pagerank, lib.oracle_pr_verify, lib.oracle_ppr):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def build_csr(n: int, src, dst, symmetrize: bool = False, dedup: bool = True,
+              drop_self_loops: bool = True):
+    """Out-direction CSR (row u lists v for arcs u->v, ascending).  Returns
+    (offsets int64[n+1], idx int32[m])."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = len(src)
+    if len(dst) != m:
+        raise ValueError("src and dst differ in length")
+    cap = 2 * m if symmetrize else m
+    offsets = np.zeros(n + 1, np.int64)
+    idx = np.empty(max(cap, 1), np.int32)
+    m_out = ctypes.c_int64(0)
+    rc = _load().oracle_build_csr(n, m, _ptr(src), _ptr(dst), int(symmetrize), int(dedup),
+                                  int(drop_self_loops), _ptr(offsets), _ptr(idx),
+                                  ctypes.byref(m_out))
+    if rc != 0:
+        raise ValueError(f"oracle_build_csr failed ({rc})")
+    return offsets, idx[: m_out.value].copy()
+
+
+def build_csc(n: int, src, dst, symmetrize: bool = False, dedup: bool = True,
+              drop_self_loops: bool = True):
+    """In-direction CSR (row v lists u for arcs u->v, ascending): the CSR of
+    the reversed draws."""
+    return build_csr(n, dst, src, symmetrize, dedup, drop_self_loops)
+
+
+def pagerank(offsets, idx, d: float = DAMPING, tol: float = TOL, max_iters: int = 100):
+    """Push-direction FP64 PageRank on an out-CSR.  Returns (x, iterations, deltas)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = len(offsets) - 1
+    x = np.empty(n, np.float64)
+    hist = np.zeros(max(max_iters, 1), np.float64)
+    k = _load().oracle_pagerank(n, _ptr(offsets), _ptr(idx), d, tol, max_iters, _ptr(x),
+                                _ptr(hist))
+    if k < 0:
+        raise ValueError(f"oracle_pagerank failed ({k})")
+    return x, int(k), hist[:k].copy()
+
+
+def verify(offsets, idx, y, d: float = DAMPING) -> float:
+    """§3 verifier: summed absolute change of one extra push iteration from y."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = len(offsets) - 1
+    out = ctypes.c_double(0.0)
+    rc = _load().oracle_pr_verify(n, _ptr(offsets), _ptr(idx), d, _ptr(y), ctypes.byref(out))
+    if rc != 0:
+        raise ValueError(f"oracle_pr_verify failed ({rc})")
+    return float(out.value)
+
+
+def ppr(offsets, idx, seeds, d: float = DAMPING, tol: float = TOL, max_iters: int = 100):
+    """Personalized PageRank with teleport uniform over the distinct seeds.
+    Returns (x, iterations, deltas)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    n = len(offsets) - 1
+    x = np.empty(n, np.float64)
+    hist = np.zeros(max(max_iters, 1), np.float64)
+    k = _load().oracle_ppr(n, _ptr(offsets), _ptr(idx), d, tol, max_iters, _ptr(seeds),
+                           len(seeds), _ptr(x), _ptr(hist))
+    if k < 0:
+        raise ValueError(f"oracle_ppr failed ({k})")
+    return x, int(k), hist[:k].copy()

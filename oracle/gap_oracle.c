@@ -1,0 +1,227 @@
+/*
+ * gap_oracle.c — TEST INFRASTRUCTURE ONLY.  A plain, slow, single-threaded
+ * FP64 CPU statement of the GAP PageRank kernel, used to check the CUDA path.
+ * Only the test suite, the smoke check and the CPU-baseline leg of the bench
+ * may load it; the product library never links or calls it, and it shares no
+ * code with the product (only the input generators feed both).
+ *
+ * Build flags: -O2 -ffp-contract=off (no fused multiply-add anywhere, so
+ * every product and sum is rounded exactly as written).
+ *
+ * What it follows (GAP Benchmark Suite, Beamer, Asanovic & Patterson):
+ *   - §2 notation: n = |V|, N+(v) out-neighbours, N-(v) in-neighbours.
+ *   - §2.1 PageRank equation: PR(v) = (1-d)/|V| + d * sum_{u in N-(v)} PR(u)/|N+(u)|.
+ *   - §2.1 tolerance equation: a result is correct when one more classical
+ *     iteration changes the scores by a summed absolute change below 1e-4.
+ *   - §2.3: duplicate edges and self-loops may be removed, neighbour lists
+ *     may be reordered; the graph is held in CSR.
+ *   - §3 PageRank verifier: serial, push direction, one extra iteration.
+ * Readings where the paper is silent (dangling vertices drop their mass,
+ * x0 = 1/n, strict '<', the newest iterate is returned) are listed at each
+ * function below.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* qsort comparator for int32 neighbour ids */
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Build a CSR (row u lists the heads v of arcs u->v) from m draws (src[i],
+ * dst[i]) — §2.3 allows dropping self-loops and duplicates and reordering
+ * neighbours.  Textbook construction: count arcs per row, prefix-sum the
+ * counts into offsets, scatter heads, sort each row ascending, then remove
+ * repeated heads when `dedup`.  With `symmetrize`, each draw (u,v) also adds
+ * (v,u).  The in-direction (CSC) is the same routine applied to (dst, src).
+ *
+ * offsets: int64[n+1] (out); idx: int32[capacity] (out), capacity must be at
+ * least (symmetrize ? 2m : m); *m_out receives the number of arcs kept.
+ * Returns 0, or -1 on a bad argument / vertex id, -2 on allocation failure.
+ */
+int oracle_build_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int symmetrize,
+                     int dedup, int drop_self_loops, int64_t* offsets, int32_t* idx,
+                     int64_t* m_out) {
+  if (n < 0 || m < 0) return -1;
+  for (int64_t i = 0; i < m; ++i)
+    if (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n) return -1;
+  int64_t* cursor = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!cursor) return -2;
+  for (int64_t v = 0; v <= n; ++v) offsets[v] = 0;
+  /* 1. count arcs per tail */
+  for (int64_t i = 0; i < m; ++i) {
+    int32_t u = src[i], v = dst[i];
+    if (drop_self_loops && u == v) continue;
+    offsets[u + 1] += 1;
+    if (symmetrize) offsets[v + 1] += 1;
+  }
+  /* 2. inclusive scan of counts -> row starts */
+  for (int64_t v = 0; v < n; ++v) offsets[v + 1] += offsets[v];
+  for (int64_t v = 0; v < n; ++v) cursor[v] = offsets[v];
+  /* 3. scatter heads */
+  for (int64_t i = 0; i < m; ++i) {
+    int32_t u = src[i], v = dst[i];
+    if (drop_self_loops && u == v) continue;
+    idx[cursor[u]++] = v;
+    if (symmetrize) idx[cursor[v]++] = u;
+  }
+  /* 4. sort each row */
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t len = offsets[v + 1] - offsets[v];
+    if (len > 1) qsort(idx + offsets[v], (size_t)len, sizeof(int32_t), cmp_i32);
+  }
+  /* 5. remove repeated heads within a row, compacting in place */
+  if (dedup) {
+    int64_t w = 0;
+    int64_t row_start = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      int64_t b = row_start, e = offsets[v + 1];
+      row_start = e;
+      offsets[v] = w;
+      for (int64_t j = b; j < e; ++j)
+        if (j == b || idx[j] != idx[j - 1]) idx[w++] = idx[j];
+    }
+    offsets[n] = w;
+  }
+  *m_out = offsets[n];
+  free(cursor);
+  return 0;
+}
+
+/*
+ * One classical push iteration (§2.1 equation, §3 verifier direction):
+ *   c[u]   = x[u] / |N+(u)|   (0 when |N+(u)| = 0: a dangling vertex sends
+ *                              nothing, so its mass leaves the system — the
+ *                              equation sums only over real in-edges)
+ *   s[v]   = sum over arcs u->v of c[u], accumulated by visiting u ascending
+ *            and each row of the CSR in stored (ascending) order
+ *   y[v]   = base[v] + d * s[v]
+ * `base` is either the scalar (1-d)/n (plain PR, base_vec == NULL) or a
+ * per-vertex vector (personalized PR).  Returns sum_v |y[v] - x[v]| summed in
+ * ascending v.  `c` and `s` are caller scratch of length n.
+ */
+static double push_iteration(int64_t n, const int64_t* off, const int32_t* idx, double d,
+                             double base, const double* base_vec, const double* x, double* y,
+                             double* c, double* s) {
+  for (int64_t u = 0; u < n; ++u) {
+    int64_t deg = off[u + 1] - off[u];
+    c[u] = deg > 0 ? x[u] / (double)deg : 0.0;
+    s[u] = 0.0;
+  }
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t j = off[u]; j < off[u + 1]; ++j) s[idx[j]] += c[u];
+  double delta = 0.0;
+  for (int64_t v = 0; v < n; ++v) {
+    double b = base_vec ? base_vec[v] : base;
+    double prod = d * s[v];
+    y[v] = b + prod;
+    double diff = y[v] - x[v];
+    delta += diff < 0 ? -diff : diff;
+  }
+  return delta;
+}
+
+/*
+ * Iterate the §2.1 equation from x0[v] = 1/n (reading: the paper does not
+ * state x0; the uniform start has total mass 1).  After each iteration k the
+ * summed change delta_k = sum_v |x_k[v] - x_{k-1}[v]| is recorded; the loop
+ * stops after the first iteration with delta < tol (strict, as in the §2.1
+ * tolerance equation) or after max_iters iterations.  The newest iterate is
+ * returned (reading: since delta_{k+1} <= d * delta_k, the returned scores
+ * also satisfy the §2.1 criterion).  tol = 0 gives a fixed iteration count.
+ *
+ * off/idx: out-CSR (push direction).  x: double[n] (out).  delta_hist:
+ * double[max_iters] (out, may be NULL).  Returns the iteration count, or -1
+ * on a bad argument, -2 on allocation failure.
+ */
+int oracle_pagerank(int64_t n, const int64_t* off, const int32_t* idx, double d, double tol,
+                    int32_t max_iters, double* x, double* delta_hist) {
+  if (n <= 0 || max_iters < 0) return -1;
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* c = (double*)malloc(sizeof(double) * (size_t)n);
+  double* s = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!y || !c || !s) {
+    free(y); free(c); free(s);
+    return -2;
+  }
+  const double base = (1.0 - d) / (double)n;
+  for (int64_t v = 0; v < n; ++v) x[v] = 1.0 / (double)n;
+  int32_t k = 0;
+  while (k < max_iters) {
+    double delta = push_iteration(n, off, idx, d, base, NULL, x, y, c, s);
+    memcpy(x, y, sizeof(double) * (size_t)n);
+    if (delta_hist) delta_hist[k] = delta;
+    ++k;
+    if (delta < tol) break;
+  }
+  free(y); free(c); free(s);
+  return k;
+}
+
+/*
+ * §3 verifier: one extra serial push iteration from a candidate score vector
+ * y (e.g. a GPU result promoted to FP64); returns sum_v |y'[v] - y[v]| through
+ * *delta.  The §2.1 criterion holds when *delta < 1e-4.
+ */
+int oracle_pr_verify(int64_t n, const int64_t* off, const int32_t* idx, double d, const double* y,
+                     double* delta) {
+  if (n <= 0) return -1;
+  double* z = (double*)malloc(sizeof(double) * (size_t)n);
+  double* c = (double*)malloc(sizeof(double) * (size_t)n);
+  double* s = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!z || !c || !s) {
+    free(z); free(c); free(s);
+    return -2;
+  }
+  *delta = push_iteration(n, off, idx, d, (1.0 - d) / (double)n, NULL, y, z, c, s);
+  free(z); free(c); free(s);
+  return 0;
+}
+
+/*
+ * Personalized PageRank (not in the paper; the serving workload's variant of
+ * the §2.1 equation): the teleport term (1-d)/n becomes (1-d) * t[v] with t
+ * uniform over the seed set S (t[v] = 1/|S| for v in S, else 0).  Repeated
+ * seeds count once.  Start x0 = t; stop rule and returned iterate as in
+ * oracle_pagerank.  Returns the iteration count or a negative error.
+ */
+int oracle_ppr(int64_t n, const int64_t* off, const int32_t* idx, double d, double tol,
+               int32_t max_iters, const int32_t* seeds, int32_t nseeds, double* x,
+               double* delta_hist) {
+  if (n <= 0 || max_iters < 0 || nseeds <= 0) return -1;
+  for (int32_t i = 0; i < nseeds; ++i)
+    if (seeds[i] < 0 || seeds[i] >= n) return -1;
+  double* t = (double*)calloc((size_t)n, sizeof(double));
+  double* bv = (double*)malloc(sizeof(double) * (size_t)n);
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* c = (double*)malloc(sizeof(double) * (size_t)n);
+  double* s = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!t || !bv || !y || !c || !s) {
+    free(t); free(bv); free(y); free(c); free(s);
+    return -2;
+  }
+  int64_t distinct = 0;
+  for (int32_t i = 0; i < nseeds; ++i)
+    if (t[seeds[i]] == 0.0) {
+      t[seeds[i]] = 1.0;
+      ++distinct;
+    }
+  for (int64_t v = 0; v < n; ++v) {
+    t[v] = t[v] != 0.0 ? 1.0 / (double)distinct : 0.0;
+    bv[v] = (1.0 - d) * t[v];
+    x[v] = t[v];
+  }
+  int32_t k = 0;
+  while (k < max_iters) {
+    double delta = push_iteration(n, off, idx, d, 0.0, bv, x, y, c, s);
+    memcpy(x, y, sizeof(double) * (size_t)n);
+    if (delta_hist) delta_hist[k] = delta;
+    ++k;
+    if (delta < tol) break;
+  }
+  free(t); free(bv); free(y); free(c); free(s);
+  return k;
+}

@@ -1,0 +1,322 @@
+"""Pins for the CPU oracle: checks against things other than the oracle itself.
+
+Each test ties one part of the oracle to a fact fixed by the paper or by
+mathematics — closed forms of the §2.1 PageRank equation on small graphs, a
+dense linear solve of its fixed point, the contraction that the §2.1
+tolerance argument rests on, brute-force CSR construction (§2.3) — so that a
+plausible slip in the oracle (a dropped d, 1/n vs 1, in- vs out-degree, a
+transposed operand, dangling mass redistributed, '<=' for '<', returning the
+older iterate) fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+D = 0.85
+
+
+# ---------------------------------------------------------------- helpers ---
+
+def csr_from_arcs(n, arcs):
+    """Tiny out-CSR from an explicit arc list, no cleaning."""
+    src = np.array([a for a, _ in arcs], np.int32)
+    dst = np.array([b for _, b in arcs], np.int32)
+    return oracle.build_csr(n, src, dst, symmetrize=False, dedup=False, drop_self_loops=False)
+
+
+def dense_fixed_point(n, arcs, d=D, teleport=None):
+    """Solve (I - d * A^T D^-1) x = (1-d) t with numpy (library solve).
+    A[u, v] counts arcs u->v; dangling columns (out-degree 0) are zero."""
+    A = np.zeros((n, n))
+    for u, v in arcs:
+        A[u, v] += 1.0
+    outdeg = A.sum(axis=1)
+    P = np.zeros((n, n))
+    for u in range(n):
+        if outdeg[u] > 0:
+            P[:, u] = A[u, :] / outdeg[u]
+    t = np.full(n, 1.0 / n) if teleport is None else teleport
+    return np.linalg.solve(np.eye(n) - d * P, (1.0 - d) * t)
+
+
+def random_arcs(rng, n, m, self_loops=True):
+    arcs = []
+    for _ in range(m):
+        u, v = int(rng.integers(n)), int(rng.integers(n))
+        if not self_loops and u == v:
+            continue
+        arcs.append((u, v))
+    return arcs
+
+
+# --------------------------------------------------------- CSR builder §2.3 ---
+
+@pytest.mark.parametrize("symmetrize", [False, True])
+@pytest.mark.parametrize("dedup", [False, True])
+@pytest.mark.parametrize("drop", [False, True])
+@pytest.mark.parametrize("seed", range(6))
+def test_csr_matches_brute_force(symmetrize, dedup, drop, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 12))
+    m = int(rng.integers(0, 40))
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    arcs = []
+    for u, v in zip(src.tolist(), dst.tolist()):
+        if drop and u == v:
+            continue
+        arcs.append((u, v))
+        if symmetrize:
+            arcs.append((v, u))
+    if dedup:
+        arcs = sorted(set(arcs))
+    rows = [sorted(v for (u, v) in arcs if u == r) for r in range(n)]
+    off, idx = oracle.build_csr(n, src, dst, symmetrize, dedup, drop)
+    assert off[0] == 0 and len(off) == n + 1
+    for r in range(n):
+        assert idx[off[r]:off[r + 1]].tolist() == rows[r]
+    assert off[n] == len(idx) == sum(len(r) for r in rows)
+
+
+def test_csc_is_transpose():
+    rng = np.random.default_rng(7)
+    n, m = 30, 200
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    off, idx = oracle.build_csr(n, src, dst)
+    coff, cidx = oracle.build_csc(n, src, dst)
+    out_arcs = {(u, int(v)) for u in range(n) for v in idx[off[u]:off[u + 1]]}
+    in_arcs = {(int(u), v) for v in range(n) for u in cidx[coff[v]:coff[v + 1]]}
+    assert out_arcs == in_arcs
+    assert all(u != v for u, v in out_arcs)
+
+
+def test_csr_rejects_bad_ids():
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([0, 3], np.int32), np.array([1, 1], np.int32))
+
+
+# ------------------------------------------------------ closed forms §2.1 ---
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64])
+def test_directed_cycle_is_uniform(n):
+    arcs = [(i, (i + 1) % n) for i in range(n)] if n > 1 else []
+    off, idx = csr_from_arcs(n, arcs)
+    if n == 1:
+        pytest.skip("a 1-cycle is a self-loop; covered by the empty-graph test")
+    x, k, deltas = oracle.pagerank(off, idx, tol=0.0, max_iters=5)
+    assert k == 5
+    np.testing.assert_allclose(x, 1.0 / n, rtol=0, atol=1e-16)
+    assert deltas[0] < 1e-15
+
+
+@pytest.mark.parametrize("n", [2, 5, 16])
+def test_complete_digraph_is_uniform(n):
+    arcs = [(u, v) for u in range(n) for v in range(n) if u != v]
+    off, idx = csr_from_arcs(n, arcs)
+    x, _, deltas = oracle.pagerank(off, idx, tol=0.0, max_iters=4)
+    np.testing.assert_allclose(x, 1.0 / n, rtol=1e-15)
+    assert max(deltas) < 1e-14
+
+
+@pytest.mark.parametrize("k", [1, 3, 10, 63])
+def test_undirected_star_closed_form(k):
+    # Fixed point of the §2.1 equation on a star with centre 0 and k leaves:
+    #   C = (1-d)/n + d*k*L,  L = (1-d)/n + d*C/k   (n = k+1)
+    # => C = (1+dk)/(n(1+d)),  L = (1-d)/n + d(1+dk)/(k n (1+d)).
+    n = k + 1
+    arcs = [(0, i) for i in range(1, n)] + [(i, 0) for i in range(1, n)]
+    off, idx = csr_from_arcs(n, arcs)
+    x, _, _ = oracle.pagerank(off, idx, tol=1e-15, max_iters=2000)
+    C = (1 + D * k) / (n * (1 + D))
+    L = (1 - D) / n + D * (1 + D * k) / (k * n * (1 + D))
+    assert abs(x[0] - C) < 1e-13
+    np.testing.assert_allclose(x[1:], L, rtol=0, atol=1e-13)
+    assert abs(x.sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 4, 50])
+def test_in_star_drops_dangling_mass(k):
+    # Leaves point at a centre that has no out-edges (dangling).  Leaves have no
+    # in-edges, so from iteration 1 on they hold (1-d)/n; the centre receives
+    # d * k * (previous leaf score).  Exact after two iterations, and the mass
+    # (1-d)(n+dk)/n < 1 shows the dangling mass is dropped, not redistributed.
+    n = k + 1
+    arcs = [(i, 0) for i in range(1, n)]
+    off, idx = csr_from_arcs(n, arcs)
+    x1, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=1)
+    assert x1[0] == pytest.approx((1 - D) / n + D * k / n, rel=1e-15)
+    x, iters, deltas = oracle.pagerank(off, idx, tol=0.0, max_iters=4)
+    leaf = (1 - D) / n
+    assert x[0] == pytest.approx(leaf * (1 + D * k), rel=1e-14)
+    np.testing.assert_allclose(x[1:], leaf, rtol=1e-15)
+    assert x.sum() == pytest.approx((1 - D) * (n + D * k) / n, rel=1e-14)
+    assert deltas[2] == 0.0 and deltas[3] == 0.0
+    # max_iters = 2 must return the second iterate (the newest), already exact
+    x2, k2, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=2)
+    assert k2 == 2 and x2[0] == x[0]
+
+
+@pytest.mark.parametrize("n", [1, 4, 1000])
+def test_empty_graph(n):
+    off, idx = csr_from_arcs(n, [])
+    x, k, deltas = oracle.pagerank(off, idx)  # tol = 1e-4
+    np.testing.assert_allclose(x, (1 - D) / n, rtol=1e-15)
+    assert deltas[0] == pytest.approx(D, rel=1e-12)
+    assert k == 2 and deltas[1] == 0.0
+
+
+def test_stop_rule_is_strict():
+    # §2.1 tolerance equation uses '<': with tol equal to the first change, the
+    # oracle must not stop after iteration 1.
+    off, idx = csr_from_arcs(8, [])
+    _, _, deltas = oracle.pagerank(off, idx, tol=0.0, max_iters=3)
+    _, k, _ = oracle.pagerank(off, idx, tol=float(deltas[0]), max_iters=10)
+    assert k == 2
+    _, k, _ = oracle.pagerank(off, idx, tol=float(np.nextafter(deltas[0], 1.0)), max_iters=10)
+    assert k == 1
+
+
+# ------------------------------------------------- dense solve, n <= 64 ---
+
+@pytest.mark.parametrize("seed", range(12))
+def test_matches_dense_solve(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 65))
+    arcs = random_arcs(rng, n, int(rng.integers(0, 4 * n)), self_loops=False)
+    off, idx = csr_from_arcs(n, arcs)  # multigraph: repeated arcs each count
+    x, k, _ = oracle.pagerank(off, idx, tol=1e-15, max_iters=5000)
+    xs = dense_fixed_point(n, arcs)
+    assert np.abs(x - xs).sum() <= 1e-12
+    # the contraction the §2.1 tolerance argument rests on:
+    #   ||x_k - x*||_1 <= d^k ||x_0 - x*||_1
+    e0 = np.abs(1.0 / n - xs).sum()
+    for kk in (1, 2, 5, 10):
+        xk, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=kk)
+        assert np.abs(xk - xs).sum() <= D ** kk * e0 + 1e-14
+
+
+def test_directed_asymmetry_pins_operand_order():
+    # 0 -> 1, 0 -> 2, 1 -> 2 : pushing along reversed arcs or dividing by
+    # in-degree gives a different fixed point than the dense solve.
+    arcs = [(0, 1), (0, 2), (1, 2)]
+    off, idx = csr_from_arcs(3, arcs)
+    x, _, _ = oracle.pagerank(off, idx, tol=1e-15, max_iters=1000)
+    b = (1 - D) / 3
+    x1 = b + D * b / 2
+    x2 = b + D * (b / 2 + x1)
+    np.testing.assert_allclose(x, [b, x1, x2], rtol=1e-14)
+    np.testing.assert_allclose(x, dense_fixed_point(3, arcs), rtol=1e-13)
+
+
+# ------------------------------------------------------------ invariants ---
+
+@pytest.mark.parametrize("seed", range(8))
+def test_invariants(seed):
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(5, 300))
+    src = rng.integers(0, n, 6 * n).astype(np.int32)
+    dst = rng.integers(0, n, 6 * n).astype(np.int32)
+    sym = bool(seed % 2)
+    off, idx = oracle.build_csr(n, src, dst, symmetrize=sym)
+    outdeg = np.diff(off)
+    x, k, deltas = oracle.pagerank(off, idx, tol=0.0, max_iters=30)
+    assert np.all(x >= (1 - D) / n * (1 - 1e-15))
+    if np.all(outdeg > 0):
+        assert abs(x.sum() - 1.0) < 1e-12
+    else:
+        assert x.sum() <= 1.0 + 1e-12
+    for a, b in zip(deltas[:-1], deltas[1:]):
+        assert b <= D * a + 1e-15 * n
+
+
+# -------------------------------------------------------- verifier (§3) ---
+
+def test_verifier_agrees_with_next_delta():
+    rng = np.random.default_rng(3)
+    n = 200
+    src = rng.integers(0, n, 1500).astype(np.int32)
+    dst = rng.integers(0, n, 1500).astype(np.int32)
+    off, idx = oracle.build_csr(n, src, dst)
+    x5, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=5)
+    _, _, d6 = oracle.pagerank(off, idx, tol=0.0, max_iters=6)
+    assert oracle.verify(off, idx, x5) == d6[5]
+    x, k, deltas = oracle.pagerank(off, idx)
+    assert deltas[-1] < 1e-4 and oracle.verify(off, idx, x) < 1e-4
+    bad = x.copy()
+    bad[:10] += 1e-3
+    assert oracle.verify(off, idx, bad) > 1e-4
+
+
+def test_iteration_band_on_paper_shaped_graphs():
+    # §2.1: 1e-4 gives "5 - 20" iterations for most graphs (a sanity band).
+    import gapgen
+    for src, dst, n, sym in [(*gapgen.kron(12, 16, 9), 1 << 12, True),
+                             (*gapgen.urand(1 << 12, 16 << 12, 9), 1 << 12, False)]:
+        off, idx = oracle.build_csr(n, src, dst, symmetrize=sym)
+        _, k, _ = oracle.pagerank(off, idx)
+        assert 5 <= k <= 20
+
+
+# --------------------------------------------------- personalized PR ---
+
+def test_ppr_all_seeds_is_pagerank():
+    rng = np.random.default_rng(11)
+    n = 120
+    src = rng.integers(0, n, 700).astype(np.int32)
+    dst = rng.integers(0, n, 700).astype(np.int32)
+    off, idx = oracle.build_csr(n, src, dst)
+    x, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=25)
+    y, _, _ = oracle.ppr(off, idx, np.arange(n, dtype=np.int32), tol=0.0, max_iters=25)
+    assert np.abs(x - y).sum() < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ppr_matches_dense_solve(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(3, 65))
+    arcs = random_arcs(rng, n, 3 * n, self_loops=False)
+    off, idx = csr_from_arcs(n, arcs)
+    seeds = rng.integers(0, n, int(rng.integers(1, 6))).astype(np.int32)
+    x, _, _ = oracle.ppr(off, idx, seeds, tol=1e-15, max_iters=5000)
+    t = np.zeros(n)
+    t[np.unique(seeds)] = 1.0 / len(np.unique(seeds))
+    xs = dense_fixed_point(n, arcs, teleport=t)
+    assert np.abs(x - xs).sum() <= 1e-12
+    # repeated seeds count once
+    y, _, _ = oracle.ppr(off, idx, np.unique(seeds), tol=1e-15, max_iters=5000)
+    np.testing.assert_array_equal(x, y)
+
+
+def test_ppr_single_seed_star():
+    # Seed at the centre of an undirected star with k leaves: by symmetry the
+    # fixed point solves C = (1-d) + d*k*L, L = d*C/k.
+    k = 9
+    n = k + 1
+    arcs = [(0, i) for i in range(1, n)] + [(i, 0) for i in range(1, n)]
+    off, idx = csr_from_arcs(n, arcs)
+    x, _, _ = oracle.ppr(off, idx, np.array([0], np.int32), tol=1e-15, max_iters=5000)
+    C = (1 - D) / (1 - D * D)
+    L = D * C / k
+    assert x[0] == pytest.approx(C, rel=1e-13)
+    np.testing.assert_allclose(x[1:], L, rtol=1e-13)
+
+
+# ------------------------------------------------ cross-machine fixture ---
+
+def test_oracle_golden_fingerprint():
+    """The oracle and generator give the same bits on every machine (x86 here,
+    Arm on the GPU host): FP64 with no FMA contraction and integer-only draws."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    sys.path.insert(0, here)
+    try:
+        import make_golden
+    finally:
+        sys.path.remove(here)
+    with open(os.path.join(here, "urand4096_oracle.json")) as f:
+        want = json.load(f)
+    assert make_golden.fingerprint() == want
