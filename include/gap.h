@@ -1,0 +1,208 @@
+/*
+ * gap.h — C ABI of the GB300-native GAP PageRank library (libgap.so).
+ *
+ * The library computes the PageRank kernel of the GAP Benchmark Suite
+ * (Beamer, Asanovic & Patterson, arXiv:1508.03619):
+ *
+ *   §2.1 PageRank equation:  PR(v) = (1-d)/|V| + d * sum_{u in N-(v)} PR(u)/|N+(u)|
+ *   §2.1 tolerance equation: the returned scores PR_k are correct when one more
+ *        classical iteration PR_{k+1} satisfies sum_v |PR_k(v) - PR_{k+1}(v)| < 1e-4.
+ *   §3   the reference iterates this equation in the pull direction (an SpMV over
+ *        the transposed CSR), checking the tolerance every iteration.
+ *   Table 1 the output of a trial is a |V|-sized array of 32-bit floats.
+ *
+ * All compute runs in hand-written CUDA kernels for sm_103a on one GPU.
+ * Readings of the paper used throughout:
+ *   - Dangling vertices (|N+(u)| = 0) contribute nothing: the equation sums only
+ *     over real in-edges, so their mass is dropped and sum(PR) < 1 when they exist.
+ *   - The start vector is x0 = 1/n; the newest iterate is returned; the stop test
+ *     is strict (delta < tol).  tol = 0 runs exactly max_iters iterations.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are plain host or device addresses (unified addressing decides
+ *     which); sizes are element counts; vertex IDs are int32 (§2.3 allows 32-bit
+ *     IDs), edge offsets int64 (§2.3 requires support for more than 2^32 edges).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     PageRank calls are stream-ordered and asynchronous: they enqueue work and
+ *     return; gap_pr_stats() synchronizes and reports convergence and device errors.
+ *   - Every function returns a gap_status; none aborts the process.  On error,
+ *     gap_last_error_message() returns a thread-local description.
+ *   - Ownership: a gap_graph_t owns all its device memory; callers own every buffer
+ *     they pass.  Per-run scratch comes from the allocator (stream-ordered
+ *     cudaMallocAsync unless gap_set_allocator installed another) and is released
+ *     on the same stream before the call returns its work to the stream; nothing
+ *     but the graph survives between runs (§2.3: only the graph may be reused
+ *     between trials).
+ */
+#ifndef GAP_H
+#define GAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GAP_API __attribute__((visibility("default")))
+#else
+#define GAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status --- */
+typedef int32_t gap_status;
+#define GAP_OK 0
+#define GAP_ERR_INVALID_ARG (-1) /* bad argument: NULL pointer, n/m out of range, id >= n */
+#define GAP_ERR_OOM (-2)         /* the allocator returned NULL */
+#define GAP_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define GAP_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define GAP_ERR_BOUNDS (-5)      /* a device-side index check failed */
+#define GAP_ERR_UNSUPPORTED (-6) /* option combination not available */
+#define GAP_WARN_NOT_CONVERGED 1 /* scores valid, but max_iters ran out with delta >= tol */
+
+/* Static, never-NULL name of a status code. */
+GAP_API const char* gap_status_string(gap_status s);
+/* Thread-local detail of the last error raised on this thread ("" if none). */
+GAP_API const char* gap_last_error_message(void);
+/* Library version as 10000*major + 100*minor + patch. */
+GAP_API int32_t gap_version(void);
+
+/* ---------------------------------------------------------- allocator --- */
+/* Optional scratch allocator.  alloc(bytes, stream, ctx) returns device memory
+ * usable on `stream` (or NULL on failure); free(ptr, bytes, stream, ctx) releases
+ * it in stream order.  Passing NULL restores the default (cudaMallocAsync /
+ * cudaFreeAsync).  Process-wide; not thread-safe against concurrent runs. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} gap_allocator;
+GAP_API gap_status gap_set_allocator(const gap_allocator* a);
+
+/* -------------------------------------------------------------- graph --- */
+typedef struct gap_graph gap_graph_t;
+
+/* Construction flags (§2.3 permits removing duplicate edges and self-loops and
+ * reordering neighbours; graph construction is outside the timed trial). */
+#define GAP_SYMMETRIZE 0x1u      /* add (v,u) for every (u,v): an undirected graph */
+#define GAP_DEDUP 0x2u           /* keep one copy of repeated arcs */
+#define GAP_DROP_SELF_LOOPS 0x4u /* remove arcs (v,v) */
+#define GAP_INPUT_ON_DEVICE 0x8u /* input arrays are device pointers (else host) */
+
+/* Build a graph from m draws (src[i] -> dst[i]), 0 <= ids < n, n <= 2^31-1.
+ * The device builder sorts arcs (own radix sort), applies the flags, and stores
+ * the in-direction CSR ("CSC": row v lists the sources u of arcs u->v in
+ * ascending order) plus out-degrees.  Without GAP_DEDUP, repeated arcs each
+ * count (a multigraph).  Synchronous: returns after the build finished.
+ * Errors: INVALID_ARG (bad n/m/pointer, or an id outside [0,n)), OOM, CUDA. */
+GAP_API gap_status gap_graph_create_from_edges(int64_t n, int64_t m, const int32_t* src,
+                                       const int32_t* dst, uint32_t flags, void* stream,
+                                       gap_graph_t** out);
+
+/* Same, from an out-direction CSR: row u (row_offsets[u] .. row_offsets[u+1]-1
+ * of col_idx) lists the heads v of arcs u->v; row_offsets has n+1 entries with
+ * row_offsets[0] = 0 and row_offsets[n] = m. */
+GAP_API gap_status gap_graph_create(int64_t n, int64_t m, const int64_t* row_offsets,
+                            const int32_t* col_idx, uint32_t flags, void* stream,
+                            gap_graph_t** out);
+
+/* n vertices, m stored arcs, and the number of vertices with out-degree 0. */
+GAP_API gap_status gap_graph_info(const gap_graph_t* g, int64_t* n, int64_t* m, int64_t* n_dangling);
+
+/* Copy the stored CSR of one direction (dir 0 = out-edges, 1 = in-edges) into
+ * caller buffers (host or device): offsets int64[n+1], idx int32[m], rows
+ * sorted ascending.  The out-direction is built on first request.  Blocks
+ * until the copy finished. */
+GAP_API gap_status gap_graph_export_csr(gap_graph_t* g, int dir, int64_t* offsets, int32_t* idx,
+                                void* stream);
+
+/* Out-degrees int32[n] into a caller buffer (host or device); blocks. */
+GAP_API gap_status gap_graph_export_outdeg(gap_graph_t* g, int32_t* outdeg, void* stream);
+
+/* Release all device memory of the graph (after synchronizing its last run). */
+GAP_API void gap_graph_destroy(gap_graph_t* g);
+
+/* ----------------------------------------------------------- PageRank --- */
+/* One PageRank trial (§2.3: allocation of every non-graph structure, degree
+ * binning and all iterations happen inside the call).  d = damping (0.85 in the
+ * paper), tol = stop threshold on the summed absolute change (1e-4 in the paper;
+ * 0 = run max_iters iterations), max_iters >= 0.  `scores` receives n FP32
+ * scores (device or host memory; a host buffer is filled by a D2H copy at the
+ * end of the run).  FP32 scores, FP32 accumulation, FP64 convergence reduction. */
+GAP_API gap_status gap_pr_run(gap_graph_t* g, double damping, double tol, int32_t max_iters,
+                      float* scores, void* stream);
+
+/* FP64 end to end (scores double[n]).  With options.deterministic (see
+ * gap_pr_run_ex) each row is summed by one thread in ascending source order. */
+GAP_API gap_status gap_pr_run_f64(gap_graph_t* g, double damping, double tol, int32_t max_iters,
+                          double* scores, void* stream);
+
+#define GAP_PREC_F32 0u /* FP32 scores and accumulation */
+#define GAP_PREC_F64 1u /* FP64 scores and accumulation */
+#define GAP_CONTRIB_F32 0u  /* contributions PR(u)/|N+(u)| stored as FP32 */
+#define GAP_CONTRIB_BF16 1u /* stored as BF16 (halves gather bytes); see ladder */
+#define GAP_LOOP_GRAPH 0u   /* convergence loop on the device: CUDA-graph while node */
+#define GAP_LOOP_HOST 1u    /* host loop: one synchronization per iteration */
+#define GAP_NO_LADDER INT32_MIN
+
+typedef struct {
+  uint32_t precision;     /* GAP_PREC_F32 | GAP_PREC_F64 */
+  uint32_t contrib;       /* GAP_CONTRIB_F32 | GAP_CONTRIB_BF16 (F32 precision only) */
+  int32_t bf16_until_log2_delta; /* BF16 contributions while delta > 2^k, then FP32;
+                                    GAP_NO_LADDER keeps BF16 throughout */
+  uint32_t kahan_hubs;    /* compensated sums on rows above hub_threshold in-edges */
+  int64_t hub_threshold;  /* default 10000 */
+  uint32_t deterministic; /* FP64: thread-per-row ascending-source sums */
+  uint32_t l2_window;     /* L2 persistence window on the contribution arrays */
+  uint32_t loop;          /* GAP_LOOP_GRAPH | GAP_LOOP_HOST */
+  uint32_t timing;        /* 1: time every kernel with CUDA events (forces the host
+                             loop); per-phase times land in gap_pr_stats_t */
+} gap_pr_options;
+
+/* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on
+ * (threshold 10000), not deterministic, no L2 window, graph loop, no timing. */
+GAP_API void gap_pr_options_default(gap_pr_options* o);
+
+/* gap_pr_run with options; `scores` is float* (F32) or double* (F64). */
+GAP_API gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters,
+                         const gap_pr_options* opt, void* scores, void* stream);
+
+#define GAP_PR_HIST 256
+/* Phases timed with options.timing (index into phase_ms / phase_launches). */
+#define GAP_PHASE_BIN 0      /* degree binning */
+#define GAP_PHASE_INIT 1     /* x0 and first contributions */
+#define GAP_PHASE_PULL_G1 2  /* gather + update, one thread per row (deg <= 4) */
+#define GAP_PHASE_PULL_G4 3  /* 4 lanes per row (deg <= 16) */
+#define GAP_PHASE_PULL_G8 4  /* 8 lanes per row (deg <= 64) */
+#define GAP_PHASE_PULL_G32 5 /* one warp per row (deg <= 2048) */
+#define GAP_PHASE_PULL_CTA 6 /* one CTA per row (deg <= 32768) */
+#define GAP_PHASE_PULL_HUB 7 /* hub chunks (deg > 32768) */
+#define GAP_PHASE_HUB_FIXUP 8
+#define GAP_PHASE_FINALIZE 9 /* delta reduction and stop test */
+#define GAP_PHASE_OUTPUT 10  /* mass reduction and output copy */
+#define GAP_PR_PHASES 11
+#define GAP_PR_BINS 6
+typedef struct {
+  int32_t iterations;   /* iterations performed */
+  int32_t converged;    /* 1 when the last delta < tol */
+  double final_delta;   /* summed |x_k - x_{k-1}| of the last iteration (FP64) */
+  double mass;          /* sum of the returned scores, FP64 */
+  int32_t bf16_iters;   /* iterations that gathered BF16 contributions */
+  int32_t device_error; /* 0, or a GAP_ERR_* raised on the device */
+  double delta_hist[GAP_PR_HIST]; /* per-iteration deltas (first GAP_PR_HIST) */
+  int64_t bin_rows[GAP_PR_BINS];  /* rows per degree bin (G1, G4, G8, G32, CTA, HUB) */
+  int64_t bin_arcs[GAP_PR_BINS];  /* stored arcs in those rows */
+  double phase_ms[GAP_PR_PHASES]; /* summed kernel time per phase (options.timing) */
+  int32_t phase_launches[GAP_PR_PHASES];
+  int32_t kernel_launches; /* CUDA kernels this run launched (set by gap_pr_stats) */
+} gap_pr_stats_t;
+
+/* Synchronize the stream of the last run on g and report it.  Returns GAP_OK,
+ * GAP_WARN_NOT_CONVERGED, or the device error of that run. */
+GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAP_H */

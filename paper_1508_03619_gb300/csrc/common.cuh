@@ -1,0 +1,130 @@
+// common.cuh — internals shared by the libgap translation units: status and
+// error-message plumbing, the scratch allocator, launch sizing for the GB300
+// (SM count from the device), and warp/block reduction helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/gap.h"
+
+namespace gap {
+
+// ---- thread-local error message ------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+gap_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define GAP_CUDA(call)                                                    \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) return ::gap::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define GAP_LAUNCH_CHECK()                                                          \
+  do {                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                            \
+    if (e_ != cudaSuccess) return ::gap::cuda_fail(e_, "kernel launch", __FILE__, __LINE__); \
+  } while (0)
+
+#define GAP_TRY(expr)              \
+  do {                             \
+    gap_status s_ = (expr);        \
+    if (s_ != GAP_OK) return s_;   \
+  } while (0)
+
+// ---- scratch allocation ---------------------------------------------------
+void* scratch_alloc(size_t bytes, cudaStream_t s);
+void scratch_free(void* p, size_t bytes, cudaStream_t s);
+
+// RAII holder for one scratch block, released in stream order.
+struct Scratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() { release(); }
+  gap_status get(size_t nbytes, cudaStream_t stream) {
+    release();
+    s = stream;
+    bytes = nbytes < 256 ? 256 : nbytes;
+    p = scratch_alloc(bytes, stream);
+    if (!p) {
+      set_error("scratch allocation of %zu bytes failed", bytes);
+      return GAP_ERR_OOM;
+    }
+    return GAP_OK;
+  }
+  void release() {
+    if (p) scratch_free(p, bytes, s);
+    p = nullptr;
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// ---- device properties ------------------------------------------------------
+struct DeviceInfo {
+  int device = 0;
+  int sms = 148;
+  int max_threads_per_sm = 2048;
+  size_t l2_bytes = 0;
+  size_t max_persist_l2 = 0;
+  int max_window = 0;
+};
+const DeviceInfo& device_info();
+
+// Grid for a grid-stride kernel: min(ceil(work / per_block), sms * blocks_per_sm).
+inline int stride_grid(int64_t work, int per_block, int blocks_per_sm) {
+  const DeviceInfo& d = device_info();
+  int64_t want = (work + per_block - 1) / per_block;
+  int64_t cap = (int64_t)d.sms * blocks_per_sm;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+inline bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int bits_for(int64_t v) {  // number of bits to hold values in [0, v]
+  int b = 0;
+  while (b < 63 && (int64_t(1) << b) <= v) ++b;
+  return b < 1 ? 1 : b;
+}
+
+// ---- device helpers ---------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum for blockDim.x a multiple of 32 (<= 1024); result valid in all
+// threads.  `sh` must hold 32 elements.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  T r = lane < nw ? sh[lane] : T(0);
+  r = warp_sum(r);
+  return r;
+}
+
+}  // namespace gap

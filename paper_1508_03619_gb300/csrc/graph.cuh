@@ -1,0 +1,45 @@
+// graph.cuh — the graph handle behind gap_graph_t and the builder's internal
+// entry points.
+//
+// HBM layout of a graph (all owned by the handle, allocated once, untimed):
+//   in_off  int64[n+1]  row starts of the in-direction CSR (CSC): row v holds
+//                       the sources u of arcs u->v, sorted ascending
+//   in_idx  int32[m]    those sources
+//   outdeg  int32[n]    |N+(u)| (arcs kept after cleaning)
+//   out_off/out_idx     out-direction CSR, built on first export request
+// Pull PageRank reads in_off/in_idx/outdeg only.
+#pragma once
+
+#include "common.cuh"
+
+struct gap_graph {
+  int64_t n = 0;
+  int64_t m = 0;
+  int64_t n_dangling = 0;
+  int64_t max_in_degree = 0;
+  int key_bits = 1;  // bits per vertex id in sort keys
+  int64_t* in_off = nullptr;
+  int32_t* in_idx = nullptr;
+  int32_t* outdeg = nullptr;
+  int64_t* out_off = nullptr;
+  int32_t* out_idx = nullptr;
+  int device = 0;
+  // last PageRank run on this graph
+  cudaStream_t last_stream = nullptr;
+  int has_run = 0;
+  double last_tol = 0;
+  gap_pr_stats_t* stats_host = nullptr;  // pinned, written by a D2H copy at run end
+  int32_t* flag_host = nullptr;          // pinned word for the host-driven loop
+  int32_t launches_fixed = 0;            // kernels of the last run outside the loop
+  int32_t launches_per_iter = 0;         // kernels per iteration of the last run
+};
+
+namespace gap {
+
+// Sort uint64 keys on their low `bits` bits (stable LSD radix sort, 8-bit
+// digits).  `keys` and `alt` hold `count` keys; the sorted keys end up in
+// *result (== keys or alt).
+gap_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t count, int bits, cudaStream_t s,
+                          uint64_t** result);
+
+}  // namespace gap

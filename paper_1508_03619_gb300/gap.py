@@ -1,0 +1,313 @@
+"""Thin ctypes binding of libgap.so (include/gap.h), same names as the C ABI.
+
+Argument marshalling only: every step of PageRank runs in the library's CUDA
+kernels.  Array arguments may be torch tensors (host or CUDA) or numpy
+arrays; their raw addresses are passed through.  ``stream`` defaults to
+torch's current CUDA stream.  If the library is missing this module raises —
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+GAP_OK = 0
+GAP_ERR_INVALID_ARG = -1
+GAP_ERR_OOM = -2
+GAP_ERR_CUDA = -3
+GAP_ERR_TIMEOUT = -4
+GAP_ERR_BOUNDS = -5
+GAP_ERR_UNSUPPORTED = -6
+GAP_WARN_NOT_CONVERGED = 1
+
+GAP_SYMMETRIZE = 0x1
+GAP_DEDUP = 0x2
+GAP_DROP_SELF_LOOPS = 0x4
+GAP_INPUT_ON_DEVICE = 0x8
+
+GAP_PREC_F32 = 0
+GAP_PREC_F64 = 1
+GAP_CONTRIB_F32 = 0
+GAP_CONTRIB_BF16 = 1
+GAP_LOOP_GRAPH = 0
+GAP_LOOP_HOST = 1
+GAP_NO_LADDER = -(2 ** 31)
+GAP_PR_HIST = 256
+GAP_PR_PHASES = 11
+GAP_PR_BINS = 6
+PHASE_NAMES = ("bin", "init", "pull_g1", "pull_g4", "pull_g8", "pull_g32", "pull_cta", "pull_hub",
+               "hub_fixup", "finalize", "output")
+BIN_NAMES = ("g1", "g4", "g8", "g32", "cta", "hub")
+
+# every symbol include/gap.h declares (checked by the ABI test)
+EXPORTED = (
+    "gap_status_string", "gap_last_error_message", "gap_version", "gap_set_allocator",
+    "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
+    "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
+    "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats",
+)
+
+
+class gap_pr_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_uint32), ("contrib", ctypes.c_uint32),
+                ("bf16_until_log2_delta", ctypes.c_int32), ("kahan_hubs", ctypes.c_uint32),
+                ("hub_threshold", ctypes.c_int64), ("deterministic", ctypes.c_uint32),
+                ("l2_window", ctypes.c_uint32), ("loop", ctypes.c_uint32),
+                ("timing", ctypes.c_uint32)]
+
+
+class gap_pr_stats_t(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("final_delta", ctypes.c_double), ("mass", ctypes.c_double),
+                ("bf16_iters", ctypes.c_int32), ("device_error", ctypes.c_int32),
+                ("delta_hist", ctypes.c_double * GAP_PR_HIST),
+                ("bin_rows", ctypes.c_int64 * GAP_PR_BINS), ("bin_arcs", ctypes.c_int64 * GAP_PR_BINS),
+                ("phase_ms", ctypes.c_double * GAP_PR_PHASES),
+                ("phase_launches", ctypes.c_int32 * GAP_PR_PHASES),
+                ("kernel_launches", ctypes.c_int32)]
+
+    def to_dict(self):
+        k = min(self.iterations, GAP_PR_HIST)
+        return {"iterations": self.iterations, "converged": bool(self.converged),
+                "final_delta": self.final_delta, "mass": self.mass, "bf16_iters": self.bf16_iters,
+                "device_error": self.device_error, "deltas": list(self.delta_hist[:k]),
+                "bin_rows": dict(zip(BIN_NAMES, self.bin_rows)),
+                "bin_arcs": dict(zip(BIN_NAMES, self.bin_arcs)),
+                "phase_ms": dict(zip(PHASE_NAMES, self.phase_ms)),
+                "phase_launches": dict(zip(PHASE_NAMES, self.phase_launches)),
+                "kernel_launches": self.kernel_launches}
+
+
+class GapError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {status_string(status)} ({status}): {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgap.so (building it in-tree first if asked).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is not built")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    i64, i32, u32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double, ctypes.c_void_p
+    st = ctypes.c_int32
+    sig = {
+        "gap_status_string": ([st], ctypes.c_char_p),
+        "gap_last_error_message": ([], ctypes.c_char_p),
+        "gap_version": ([], i32),
+        "gap_set_allocator": ([vp], st),
+        "gap_graph_create_from_edges": ([i64, i64, vp, vp, u32, vp, ctypes.POINTER(vp)], st),
+        "gap_graph_create": ([i64, i64, vp, vp, u32, vp, ctypes.POINTER(vp)], st),
+        "gap_graph_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
+        "gap_graph_export_csr": ([vp, ctypes.c_int, vp, vp, vp], st),
+        "gap_graph_export_outdeg": ([vp, vp, vp], st),
+        "gap_graph_destroy": ([vp], None),
+        "gap_pr_run": ([vp, dbl, dbl, i32, vp, vp], st),
+        "gap_pr_run_f64": ([vp, dbl, dbl, i32, vp, vp], st),
+        "gap_pr_options_default": ([ctypes.POINTER(gap_pr_options)], None),
+        "gap_pr_run_ex": ([vp, dbl, dbl, i32, ctypes.POINTER(gap_pr_options), vp, vp], st),
+        "gap_pr_stats": ([vp, ctypes.POINTER(gap_pr_stats_t)], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load().gap_status_string(s).decode()
+
+
+def last_error_message() -> str:
+    return load().gap_last_error_message().decode()
+
+
+def _check(status: int, where: str, ok=(GAP_OK,)):
+    if status not in ok:
+        raise GapError(status, where, last_error_message())
+    return status
+
+
+def _ptr(a):
+    """Raw address of a torch tensor / numpy array / int / None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"cannot pass {type(a)} as a pointer")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _on_device(a) -> bool:
+    return bool(getattr(a, "is_cuda", False))
+
+
+# ------------------------------------------------------------------ graph ---
+
+def gap_graph_create_from_edges(n: int, src, dst, flags: int, stream=None):
+    if len(src) != len(dst):
+        raise ValueError("src and dst differ in length")
+    if _on_device(src) != _on_device(dst):
+        raise ValueError("src and dst must both be host or both device arrays")
+    if _on_device(src):
+        flags |= GAP_INPUT_ON_DEVICE
+    out = ctypes.c_void_p()
+    _check(load().gap_graph_create_from_edges(n, len(src), _ptr(src), _ptr(dst), flags,
+                                              _stream(stream), ctypes.byref(out)),
+           "gap_graph_create_from_edges")
+    return out
+
+
+def gap_graph_create(n: int, row_offsets, col_idx, flags: int, stream=None):
+    if _on_device(row_offsets):
+        flags |= GAP_INPUT_ON_DEVICE
+    out = ctypes.c_void_p()
+    _check(load().gap_graph_create(n, len(col_idx), _ptr(row_offsets), _ptr(col_idx), flags,
+                                   _stream(stream), ctypes.byref(out)), "gap_graph_create")
+    return out
+
+
+def gap_graph_info(h):
+    n, m, nd = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().gap_graph_info(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nd)),
+           "gap_graph_info")
+    return n.value, m.value, nd.value
+
+
+def gap_graph_export_csr(h, direction: int, offsets, idx, stream=None):
+    _check(load().gap_graph_export_csr(h, direction, _ptr(offsets), _ptr(idx), _stream(stream)),
+           "gap_graph_export_csr")
+
+
+def gap_graph_export_outdeg(h, outdeg, stream=None):
+    _check(load().gap_graph_export_outdeg(h, _ptr(outdeg), _stream(stream)),
+           "gap_graph_export_outdeg")
+
+
+def gap_graph_destroy(h):
+    if h is not None and h.value:
+        load().gap_graph_destroy(h)
+
+
+# --------------------------------------------------------------- PageRank ---
+
+def gap_pr_options_default() -> gap_pr_options:
+    o = gap_pr_options()
+    load().gap_pr_options_default(ctypes.byref(o))
+    return o
+
+
+def gap_pr_run(h, damping: float, tol: float, max_iters: int, scores, stream=None):
+    return _check(load().gap_pr_run(h, damping, tol, max_iters, _ptr(scores), _stream(stream)),
+                  "gap_pr_run")
+
+
+def gap_pr_run_f64(h, damping: float, tol: float, max_iters: int, scores, stream=None):
+    return _check(load().gap_pr_run_f64(h, damping, tol, max_iters, _ptr(scores), _stream(stream)),
+                  "gap_pr_run_f64")
+
+
+def gap_pr_run_ex(h, damping: float, tol: float, max_iters: int, options: gap_pr_options, scores,
+                  stream=None):
+    return _check(load().gap_pr_run_ex(h, damping, tol, max_iters, ctypes.byref(options),
+                                       _ptr(scores), _stream(stream)), "gap_pr_run_ex")
+
+
+def gap_pr_stats(h):
+    """Synchronize the last run on h; returns (status, stats dict).  Raises on
+    errors; GAP_WARN_NOT_CONVERGED is returned, not raised."""
+    st = gap_pr_stats_t()
+    s = _check(load().gap_pr_stats(h, ctypes.byref(st)), "gap_pr_stats",
+               ok=(GAP_OK, GAP_WARN_NOT_CONVERGED))
+    return s, st.to_dict()
+
+
+# -------------------------------------------------------- convenience ---
+
+class Graph:
+    """Owning wrapper around a gap_graph_t handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.n, self.m, self.n_dangling = gap_graph_info(handle)
+
+    @classmethod
+    def from_edges(cls, n, src, dst, symmetrize=False, dedup=True, drop_self_loops=True,
+                   stream=None):
+        flags = ((GAP_SYMMETRIZE if symmetrize else 0) | (GAP_DEDUP if dedup else 0)
+                 | (GAP_DROP_SELF_LOOPS if drop_self_loops else 0))
+        return cls(gap_graph_create_from_edges(n, src, dst, flags, stream))
+
+    @classmethod
+    def from_csr(cls, n, row_offsets, col_idx, symmetrize=False, dedup=True, drop_self_loops=True,
+                 stream=None):
+        flags = ((GAP_SYMMETRIZE if symmetrize else 0) | (GAP_DEDUP if dedup else 0)
+                 | (GAP_DROP_SELF_LOOPS if drop_self_loops else 0))
+        return cls(gap_graph_create(n, row_offsets, col_idx, flags, stream))
+
+    def export_csr(self, direction: int = 1):
+        import numpy as np
+        off = np.empty(self.n + 1, np.int64)
+        idx = np.empty(max(self.m, 1), np.int32)
+        gap_graph_export_csr(self.handle, direction, off, idx)
+        return off, idx[: self.m]
+
+    def export_outdeg(self):
+        import numpy as np
+        out = np.empty(self.n, np.int32)
+        gap_graph_export_outdeg(self.handle, out)
+        return out
+
+    def close(self):
+        if self.handle is not None:
+            gap_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI (no GPU compute): the library builds and loads,
+exports every symbol include/*.h declares, its structs match the C layout,
+and argument validation rejects bad input before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1508_03619_gb300 import gap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(INCLUDE):
+        if fn.endswith(".h"):
+            text = open(os.path.join(INCLUDE, fn)).read()
+            names |= set(re.findall(r"GAP_API\s+[\w\s\*]*?\b(gap_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = gap.load()
+    declared = declared_symbols()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", gap.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (gap_\w+)", out))
+    assert declared <= exported, declared - exported
+    assert set(gap.EXPORTED) == declared
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_struct_layout_matches_c(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gap.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(gap_pr_options),'
+                   ' sizeof(gap_pr_stats_t), offsetof(gap_pr_options, hub_threshold),'
+                   ' offsetof(gap_pr_stats_t, delta_hist), offsetof(gap_pr_stats_t, device_error));}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", f"-I{INCLUDE}", str(src), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                       check=True).stdout.split()))
+    want = [ctypes.sizeof(gap.gap_pr_options), ctypes.sizeof(gap.gap_pr_stats_t),
+            gap.gap_pr_options.hub_threshold.offset, gap.gap_pr_stats_t.delta_hist.offset,
+            gap.gap_pr_stats_t.device_error.offset]
+    assert got == want
+
+
+def test_status_strings_and_defaults():
+    assert gap.status_string(gap.GAP_OK) == "GAP_OK"
+    assert gap.status_string(gap.GAP_WARN_NOT_CONVERGED) == "GAP_WARN_NOT_CONVERGED"
+    assert gap.status_string(12345) == "GAP_STATUS_UNKNOWN"
+    o = gap.gap_pr_options_default()
+    assert (o.precision, o.contrib, o.kahan_hubs, o.hub_threshold, o.deterministic, o.loop) == \
+        (gap.GAP_PREC_F32, gap.GAP_CONTRIB_F32, 1, 10000, 0, gap.GAP_LOOP_GRAPH)
+    assert o.bf16_until_log2_delta == gap.GAP_NO_LADDER
+
+
+@pytest.mark.parametrize("n,m", [(0, 0), (-1, 0), (2 ** 31, 0)])
+def test_create_rejects_bad_sizes(n, m):
+    src = np.zeros(max(m, 1), np.int32)
+    with pytest.raises(gap.GapError) as e:
+        out = ctypes.c_void_p()
+        gap._check(gap.load().gap_graph_create_from_edges(n, m, gap._ptr(src), gap._ptr(src), 0,
+                                                          None, ctypes.byref(out)), "create")
+    assert e.value.status == gap.GAP_ERR_INVALID_ARG
+    assert "n =" in str(e.value)
+
+
+def test_create_rejects_null_arrays():
+    out = ctypes.c_void_p()
+    s = gap.load().gap_graph_create_from_edges(4, 3, None, None, 0, None, ctypes.byref(out))
+    assert s == gap.GAP_ERR_INVALID_ARG
+    s = gap.load().gap_graph_create_from_edges(4, 0, None, None, 0, None, None)
+    assert s == gap.GAP_ERR_INVALID_ARG
+
+
+def test_run_rejects_null_graph():
+    x = np.zeros(4, np.float32)
+    assert gap.load().gap_pr_run(None, 0.85, 1e-4, 10, gap._ptr(x), None) == gap.GAP_ERR_INVALID_ARG
+    assert "graph is NULL" in gap.last_error_message()
+    st = gap.gap_pr_stats_t()
+    assert gap.load().gap_pr_stats(None, ctypes.byref(st)) == gap.GAP_ERR_INVALID_ARG
+
+
+def test_allocator_hook_validation():
+    lib = gap.load()
+    assert lib.gap_set_allocator(None) == gap.GAP_OK

@@ -1,0 +1,195 @@
+"""CUDA PageRank vs the FP64 oracle, element by element, on seeded inputs.
+
+Bars (stated in gpu_helpers): FP64 deterministic mode bit-identical to the
+oracle; FP64 binned within L1 1e-12; FP32 within L1 1e-5 and per-vertex
+relative 1e-3 after the same fixed iteration count, the same iteration count
++-1 in tolerance mode, and the paper's §3 verifier (< 1e-4) on every
+tolerance-mode result.
+"""
+import numpy as np
+import pytest
+
+import gapgen
+import oracle
+from gpu_helpers import D, FP64_L1, assert_fp32_parity, gpu_graph, oracle_graph, run_gpu
+from paper_1508_03619_gb300 import gap
+
+pytestmark = pytest.mark.gpu
+
+
+def graph_cases():
+    """(name, n, src, dst, symmetrize): small, paper-shaped, several tiles."""
+    yield ("urand4096", 4096, *gapgen.urand(4096, 65536, 0x1), False)
+    yield ("kron14", 1 << 14, *gapgen.kron(14, 16, 0x14), True)
+    yield ("grid96x97", 96 * 97, *gapgen.grid(96, 97, 0.05, 0x4), True)
+    n = 1 << 13
+    yield ("chunglu8k", n, *gapgen.chung_lu(n, 16 * n, 2.1, 0x5), False)
+
+
+CASES = list(graph_cases())
+
+
+def threshold_graph(seed=0x7):
+    """Rows whose in-degrees sit at every bin boundary +-1, plus a hub above the
+    hub-chunk size and a 1.2M-arc hub, on 2^21 vertices."""
+    rng = np.random.default_rng(seed)
+    n = 1 << 21
+    degs = [0, 1, 4, 5, 16, 17, 64, 65, 2047, 2048, 2049, 9999, 10000, 10001, 32767, 32768,
+            32769, 65537, 100_000, 1_200_000]
+    src, dst = [], []
+    for v, dg in enumerate(degs):
+        s = rng.choice(n, size=dg, replace=False).astype(np.int32)
+        s[s == v] = (v + 1) % n
+        src.append(s)
+        dst.append(np.full(dg, v, np.int32))
+    s2, d2 = gapgen.urand(n, 4 * n, seed)  # background arcs so sources have out-degree
+    src.append(s2)
+    dst.append(d2)
+    return n, np.concatenate(src), np.concatenate(dst)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp32_fixed_iterations(cuda_device, case):
+    name, n, src, dst, sym = case
+    off, idx = oracle_graph(n, src, dst, sym)
+    xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 20)
+    g = gpu_graph(n, src, dst, sym)
+    x, st, status = run_gpu(g, 0.0, 20)
+    assert status == gap.GAP_OK and st["iterations"] == 20
+    assert_fp32_parity(x, xo)
+    g.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp32_tolerance_mode(cuda_device, case):
+    name, n, src, dst, sym = case
+    off, idx = oracle_graph(n, src, dst, sym)
+    xo, ko, do = oracle.pagerank(off, idx, D, 1e-4, 100)
+    g = gpu_graph(n, src, dst, sym)
+    x, st, status = run_gpu(g, 1e-4, 100)
+    assert status == gap.GAP_OK and st["converged"]
+    assert abs(st["iterations"] - ko) <= 1
+    assert oracle.verify(off, idx, x) < 1e-4  # paper §3 verifier
+    np.testing.assert_allclose(st["deltas"], do[: st["iterations"]], rtol=1e-3, atol=1e-7)
+    assert st["mass"] == pytest.approx(x.sum(), rel=1e-12)
+    g.close()
+
+
+def test_fp64_deterministic_bitexact(cuda_device):
+    n, src, dst, sym = CASES[0][1:]
+    off, idx = oracle_graph(n, src, dst, sym)
+    g = gpu_graph(n, src, dst, sym)
+    for tol, iters in ((0.0, 20), (1e-4, 100)):
+        xo, ko, do = oracle.pagerank(off, idx, D, tol, iters)
+        x, st, status = run_gpu(g, tol, iters, f64=True, deterministic=1)
+        assert st["iterations"] == ko
+        assert np.array_equal(x, xo), np.abs(x - xo).max()
+        np.testing.assert_allclose(st["deltas"], do, rtol=1e-12)
+    g.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp64_binned(cuda_device, case):
+    name, n, src, dst, sym = case
+    off, idx = oracle_graph(n, src, dst, sym)
+    xo, ko, _ = oracle.pagerank(off, idx, D, 0.0, 20)
+    g = gpu_graph(n, src, dst, sym)
+    x, st, _ = run_gpu(g, 0.0, 20, f64=True)
+    assert np.abs(x - xo).sum() <= FP64_L1
+    g.close()
+
+
+def test_bin_boundaries_and_hubs(cuda_device):
+    n, src, dst = threshold_graph()
+    off, idx = oracle_graph(n, src, dst, False)
+    xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 12)
+    g = gpu_graph(n, src, dst, False)
+    for kahan in (1, 0):
+        x, st, _ = run_gpu(g, 0.0, 12, kahan_hubs=kahan)
+        assert_fp32_parity(x, xo)
+        hub_rel = np.abs(x[:20] - xo[:20]) / xo[:20]
+        print(f"kahan={kahan}: max rel error on the 20 boundary/hub rows {hub_rel.max():.3e}")
+        if kahan:
+            assert hub_rel.max() < 1e-5
+    x64, _, _ = run_gpu(g, 0.0, 12, f64=True)
+    assert np.abs(x64 - xo).sum() <= FP64_L1
+    g.close()
+
+
+def test_loop_modes_agree(cuda_device):
+    n, src, dst, sym = CASES[1][1:]
+    g = gpu_graph(n, src, dst, sym)
+    xa, sa, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_GRAPH)
+    xb, sb, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_HOST)
+    assert sa["iterations"] == sb["iterations"]
+    assert np.array_equal(xa, xb)
+    xc, sc, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_GRAPH)
+    assert np.array_equal(xa, xc)  # run-to-run reproducible
+    g.close()
+
+
+def test_host_scores_buffer(cuda_device):
+    n, src, dst, sym = CASES[0][1:]
+    g = gpu_graph(n, src, dst, sym)
+    xa, _, _ = run_gpu(g, 1e-4, 100)
+    xb, _, _ = run_gpu(g, 1e-4, 100, host_scores=True)
+    assert np.array_equal(xa, xb)
+    g.close()
+
+
+def test_bf16_contributions_ladder(cuda_device):
+    n, src, dst, sym = CASES[1][1:]
+    off, idx = oracle_graph(n, src, dst, sym)
+    xo, ko, _ = oracle.pagerank(off, idx, D, 1e-4, 100)
+    g = gpu_graph(n, src, dst, sym)
+    x, st, status = run_gpu(g, 1e-4, 100, contrib=gap.GAP_CONTRIB_BF16, bf16_until_log2_delta=-10)
+    assert status == gap.GAP_OK
+    assert st["bf16_iters"] >= 1
+    assert st["bf16_iters"] < st["iterations"]
+    assert oracle.verify(off, idx, x) < 1e-4
+    l1 = np.abs(x - xo).sum()
+    print(f"bf16 ladder: iters {st['iterations']} (bf16 {st['bf16_iters']}), L1 vs FP64 oracle {l1:.3e}")
+    assert l1 < 1e-3
+    # BF16 throughout: error is reported, not bounded by the FP32 bar
+    x2, st2, _ = run_gpu(g, 1e-4, 100, contrib=gap.GAP_CONTRIB_BF16)
+    assert st2["bf16_iters"] == st2["iterations"]
+    print(f"bf16 always: L1 vs FP64 oracle {np.abs(x2 - xo).sum():.3e}")
+    g.close()
+
+
+def test_degenerate_runs(cuda_device):
+    e = np.zeros(0, np.int32)
+    g = gpu_graph(1, e, e)
+    x, st, status = run_gpu(g, 1e-4, 100)
+    assert st["iterations"] == 2 and x[0] == np.float32(1 - D)
+    g.close()
+    g = gpu_graph(1000, e, e)
+    x, st, status = run_gpu(g, 0.0, 0)
+    assert st["iterations"] == 0 and np.all(x == np.float32(1 / 1000))
+    x, st, status = run_gpu(g, 1e-4, 1)
+    assert status == gap.GAP_WARN_NOT_CONVERGED and st["iterations"] == 1
+    x, st, status = run_gpu(g, 1e-4, 100, f64=True)
+    assert st["iterations"] == 2 and np.allclose(x, (1 - D) / 1000, rtol=1e-15)
+    g.close()
+
+
+def test_kron22_full_config(cuda_device):
+    """Kronecker scale 22, edge factor 16, symmetrized: FP32 and FP64 vs oracle."""
+    scale = 22
+    n = 1 << scale
+    src, dst = gapgen.kron(scale, 16, 0x22)
+    off, idx = oracle_graph(n, src, dst, True)
+    g = gpu_graph(n, src, dst, True)
+    coff, cidx = g.export_csr(1)
+    assert np.array_equal(coff, off) and np.array_equal(cidx, idx)  # symmetric: CSC == CSR
+    xo, ko, do = oracle.pagerank(off, idx, D, 0.0, 20)
+    x, st, _ = run_gpu(g, 0.0, 20)
+    l1, rel = assert_fp32_parity(x, xo)
+    x64, _, _ = run_gpu(g, 0.0, 20, f64=True)
+    assert np.abs(x64 - xo).sum() <= FP64_L1
+    xt, stt, _ = run_gpu(g, 1e-4, 100)
+    _, kt, _ = oracle.pagerank(off, idx, D, 1e-4, 100)
+    assert abs(stt["iterations"] - kt) <= 1
+    assert oracle.verify(off, idx, xt) < 1e-4
+    print(f"kron22: m={g.m} fp32 L1 {l1:.3e} rel {rel:.3e} iters {stt['iterations']} (oracle {kt})")
+    g.close()
