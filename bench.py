@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gap", choices=["gap", "reference"])
-    ap.add_argument("--scale", type=int, default=26, help="Kronecker scale of the workload")
+    ap.add_argument("--graph", default="kron", choices=["kron", "urand"],
+                    help="kron: Kronecker (symmetrized); urand: uniform random digraph")
+    ap.add_argument("--scale", type=int, default=26, help="log2 of the vertex count")
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=lambda s: int(s, 0), default=0x26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -54,6 +56,12 @@ def parse():
 
 
 def workload_config(a):
+    if a.graph == "urand":
+        return {"workload": f"urand{a.scale}-deg{a.edge_factor} directed pull PageRank FP32, d=0.85, "
+                            f"tol=1e-4", "graph": "uniform random digraph", "scale": a.scale,
+                "edge_factor": a.edge_factor, "symmetrized": False, "seed": hex(a.seed),
+                "trial": "alloc+binning+iterations+output (paper §2.3)",
+                "l2": "inputs larger than L2 (CSC > 129 MB), no flush"}
     return {"workload": f"kron{a.scale}-ef{a.edge_factor}-sym pull PageRank FP32, d=0.85, tol=1e-4",
             "graph": "kronecker", "scale": a.scale, "edge_factor": a.edge_factor,
             "A_B_C": [0.57, 0.19, 0.19], "symmetrized": True, "seed": hex(a.seed),
@@ -198,8 +206,12 @@ def main():
         pg = dist
 
     # ---- graph (untimed) ----
-    src, dst = gapgen.kron_device(a.scale, a.edge_factor, a.seed, device=dev)
-    g = gap.Graph.from_edges(1 << a.scale, src, dst, symmetrize=True)
+    if a.graph == "urand":
+        src, dst = gapgen.urand_device(1 << a.scale, a.edge_factor << a.scale, a.seed, device=dev)
+        g = gap.Graph.from_edges(1 << a.scale, src, dst, symmetrize=False)
+    else:
+        src, dst = gapgen.kron_device(a.scale, a.edge_factor, a.seed, device=dev)
+        g = gap.Graph.from_edges(1 << a.scale, src, dst, symmetrize=True)
     del src, dst
     torch.cuda.empty_cache()
     n, m = g.n, g.m
