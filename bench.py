@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--seed", type=lambda s: int(s, 0), default=0x26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="convergence loop driver (host: one launch per kernel, visible to ncu)")
+    ap.add_argument("--segment-bytes", type=int, default=0, help="L2 blocking segment size (0 = default)")
     return ap.parse_args()
 
 
@@ -129,6 +132,51 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def roofline_entry(sp, m, n, segments, contrib_bytes=4):
+    """Roofline of the dominant pull kernel from a timing=1 trial: algorithmic
+    bytes of its degree bin (8 B per arc: index + gathered contribution; 24 B per
+    row: offsets, out-degree, x read/write, c write) over its launch time."""
+    from paper_1508_03619_gb300 import gap
+    pulls = list(gap.PULL_PHASES)
+    dom = max(pulls, key=lambda k: sp["phase_ms"][k])
+    q = pulls.index(dom)
+    b = sp["bins"][q]
+    per_arc = 4 + contrib_bytes
+    per_row = 20 + contrib_bytes
+    alg_bin = per_arc * b["arcs"] + per_row * b["rows"]
+    launches = max(1, sp["phase_launches"][dom])
+    iters = max(1, sp["iterations"])
+    per_launch_alg = alg_bin * iters / launches
+    per_launch_ms = sp["phase_ms"][dom] / launches
+    peak, peak_kind = measured_hbm_peak()
+    achieved = per_launch_alg / (per_launch_ms / 1e3) / 1e9
+    lanes = b["lanes"]
+    kname = {0: "k_pull_hub_chunks", 256: "k_pull_cta"}.get(
+        lanes, ("k_pull_group_seg<%d>" if b["segmented"] else "k_pull_group<%d>") % lanes)
+    if q == 0:
+        kname = "k_pull_zero"
+    elif q == 1 and lanes == 1:
+        kname = "k_pull_short"
+    loop_ms = sum(sp["phase_ms"][k] for k in pulls + ["hub_fixup", "finalize"])
+    iter_ms = loop_ms / iters
+    iter_bytes = per_arc * m + per_row * n
+    total_ms = sum(sp["phase_ms"].values())
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kname),
+            "kernel": f"{kname} (bin {q}: in-degree <= {b['max_degree']}, "
+                      f"{'segmented' if b['segmented'] else 'whole rows'})",
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s",
+            "alg_bytes_per_launch": per_launch_alg, "launch_ms": per_launch_ms,
+            "share_of_trial": sp["phase_ms"][dom] / total_ms if total_ms else None,
+            "segments": segments,
+            "iteration": {"alg_bytes": iter_bytes, "ms": iter_ms,
+                          "achieved_gbs": iter_bytes / (iter_ms / 1e3) / 1e9,
+                          "frac": iter_bytes / (iter_ms / 1e3) / 1e9 / peak,
+                          "gedges_per_s": m / (iter_ms / 1e3) / 1e9},
+            "phase_ms": sp["phase_ms"], "bins": sp["bins"]}
 
 
 def cpu_baseline(a, seconds=12.0):
@@ -218,6 +266,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     scores = torch.empty(n, dtype=torch.float32, device=dev)
     opts = gap.gap_pr_options_default()
+    opts.loop = gap.GAP_LOOP_HOST if a.loop == "host" else gap.GAP_LOOP_GRAPH
+    opts.segment_bytes = a.segment_bytes
 
     def trial(out, o=opts):
         gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, o, out)
@@ -274,30 +324,10 @@ def main():
     # ---- per-kernel durations (CUDA events around every launch) ----
     prof = gap.gap_pr_options_default()
     prof.timing = 1
+    prof.segment_bytes = a.segment_bytes
     trial(scores, prof)
     _, sp = gap.gap_pr_stats(g.handle)
-    pulls = ["pull_g1", "pull_g4", "pull_g8", "pull_g32", "pull_cta", "pull_hub"]
-    bins = ["g1", "g4", "g8", "g32", "cta", "hub"]
-    dom = max(pulls, key=lambda k: sp["phase_ms"][k])
-    b = bins[pulls.index(dom)]
-    per_launch_ms = sp["phase_ms"][dom] / max(1, sp["phase_launches"][dom])
-    alg_bytes = 8 * sp["bin_arcs"][b] + 24 * sp["bin_rows"][b]
-    peak, peak_kind = measured_hbm_peak()
-    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    loop_ms = sum(sp["phase_ms"][k] for k in pulls + ["hub_fixup", "finalize"])
-    iter_ms = loop_ms / max(1, sp["iterations"])
-    iter_bytes = 8 * m + 24 * n
-    total_ms = sum(sp["phase_ms"].values())
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom),
-                "kernel": f"k_pull_{b} ({dom})", "peak_source": f"{peak_kind} hbm_gbs",
-                "alg_bytes_per_launch": alg_bytes, "launch_ms": per_launch_ms,
-                "share_of_trial": sp["phase_ms"][dom] / total_ms if total_ms else None,
-                "iteration": {"alg_bytes": iter_bytes, "ms": iter_ms,
-                              "achieved_gbs": iter_bytes / (iter_ms / 1e3) / 1e9,
-                              "frac": iter_bytes / (iter_ms / 1e3) / 1e9 / peak,
-                              "gedges_per_s": m / (iter_ms / 1e3) / 1e9},
-                "phase_ms": sp["phase_ms"]}
+    roofline = roofline_entry(sp, m, n, sp["segments"])
 
     # ---- FP64 GPU path on the same graph (metric: FP32 vs FP64 at L1 <= 1e-4) ----
     fp64 = None

@@ -158,10 +158,15 @@ typedef struct {
   uint32_t loop;          /* GAP_LOOP_GRAPH | GAP_LOOP_HOST */
   uint32_t timing;        /* 1: time every kernel with CUDA events (forces the host
                              loop); per-phase times land in gap_pr_stats_t */
+  int64_t segment_bytes;  /* L2 blocking: when the contribution array is larger than
+                             this, rows above 64 in-edges are pulled one source segment
+                             of about this many bytes at a time (0 = library default,
+                             tuned per GPU; < 0 disables) */
 } gap_pr_options;
 
 /* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on
- * (threshold 10000), not deterministic, no L2 window, graph loop, no timing. */
+ * (threshold 10000), not deterministic, no L2 window, graph loop, no timing,
+ * default segment size. */
 GAP_API void gap_pr_options_default(gap_pr_options* o);
 
 /* gap_pr_run with options; `scores` is float* (F32) or double* (F64). */
@@ -169,20 +174,16 @@ GAP_API gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int
                          const gap_pr_options* opt, void* scores, void* stream);
 
 #define GAP_PR_HIST 256
-/* Phases timed with options.timing (index into phase_ms / phase_launches). */
-#define GAP_PHASE_BIN 0      /* degree binning */
+/* Phases timed with options.timing (index into phase_ms / phase_launches).
+ * Pull phases are per degree bin (see gap_pr_stats_t.bin_*). */
+#define GAP_PHASE_BIN 0      /* degree binning (and segment split points) */
 #define GAP_PHASE_INIT 1     /* x0 and first contributions */
-#define GAP_PHASE_PULL_G1 2  /* gather + update, one thread per row (deg <= 4) */
-#define GAP_PHASE_PULL_G4 3  /* 4 lanes per row (deg <= 16) */
-#define GAP_PHASE_PULL_G8 4  /* 8 lanes per row (deg <= 64) */
-#define GAP_PHASE_PULL_G32 5 /* one warp per row (deg <= 2048) */
-#define GAP_PHASE_PULL_CTA 6 /* one CTA per row (deg <= 32768) */
-#define GAP_PHASE_PULL_HUB 7 /* hub chunks (deg > 32768) */
-#define GAP_PHASE_HUB_FIXUP 8
-#define GAP_PHASE_FINALIZE 9 /* delta reduction and stop test */
-#define GAP_PHASE_OUTPUT 10  /* mass reduction and output copy */
-#define GAP_PR_PHASES 11
-#define GAP_PR_BINS 6
+#define GAP_PHASE_PULL0 2    /* gather + update of bin 0 .. bin 6: phases 2 .. 8 */
+#define GAP_PHASE_HUB_FIXUP 9
+#define GAP_PHASE_FINALIZE 10 /* delta reduction and stop test */
+#define GAP_PHASE_OUTPUT 11   /* mass reduction and output copy */
+#define GAP_PR_PHASES 12
+#define GAP_PR_BINS 7
 typedef struct {
   int32_t iterations;   /* iterations performed */
   int32_t converged;    /* 1 when the last delta < tol */
@@ -191,8 +192,13 @@ typedef struct {
   int32_t bf16_iters;   /* iterations that gathered BF16 contributions */
   int32_t device_error; /* 0, or a GAP_ERR_* raised on the device */
   double delta_hist[GAP_PR_HIST]; /* per-iteration deltas (first GAP_PR_HIST) */
-  int64_t bin_rows[GAP_PR_BINS];  /* rows per degree bin (G1, G4, G8, G32, CTA, HUB) */
+  int64_t bin_rows[GAP_PR_BINS];  /* rows per in-degree bin */
   int64_t bin_arcs[GAP_PR_BINS];  /* stored arcs in those rows */
+  int64_t bin_max_degree[GAP_PR_BINS]; /* inclusive upper in-degree of each bin */
+  int32_t bin_lanes[GAP_PR_BINS]; /* threads per row: 1/4/8/32, 256 = CTA, 0 = hub chunks
+                                     (bin 0 holds rows without in-edges) */
+  int32_t bin_segmented[GAP_PR_BINS]; /* 1: rows pulled one source segment at a time */
+  int32_t segments;     /* source segments per iteration (1 = whole contribution array) */
   double phase_ms[GAP_PR_PHASES]; /* summed kernel time per phase (options.timing) */
   int32_t phase_launches[GAP_PR_PHASES];
   int32_t kernel_launches; /* CUDA kernels this run launched (set by gap_pr_stats) */

@@ -2,41 +2,62 @@
 // PageRank and tolerance equations; §3: pull, so no atomics, tolerance
 // checked every iteration).
 //
-// One trial (gap_pr_run*) = everything the paper's §2.3 puts in the trial
-// time: scratch allocation, degree binning, x0 / c0, the iterations, output.
+// One trial (gap_pr_run*) = everything paper §2.3 puts in the trial time:
+// scratch allocation, degree binning, segment split points, x0 / c0, the
+// iterations and the output.
 //
 // Per iteration, for every vertex v (row v of the in-direction CSR):
 //   sum[v] = sum_{u in N-(v)} c[u]                       (gather-SpMV)
 //   x'[v]  = (1-d)/n + d*sum[v]                          (update, fused)
 //   delta += |x'[v] - x[v]|   (FP64, block partials reduced in fixed order)
 //   c'[v]  = x'[v] / |N+(v)|, or 0 for a dangling v      (next contribution)
-// x is updated in place (row v is owned by one thread group); c ping-pongs
+// x is updated in place (a row is owned by one thread group); c ping-pongs
 // between two buffers because every row gathers from all of c.
 //
 // Degree bins (hardware tuning constants, the same for every graph, §2.3):
-//   G1  deg <= 4        one thread per row
-//   G4  deg <= 16       4 lanes per row
-//   G8  deg <= 64       8 lanes per row
-//   G32 deg <= 2048     one warp per row
-//   CTA deg <= 32768    one 256-thread CTA per row (compensated sums)
-//   HUB deg >  32768    rows split into 32768-arc chunks across CTAs; a
-//                       fix-up warp adds the chunk partials in order
-// Rows of each bin are listed in ascending vertex order by a stable
-// compaction, so every sum has a fixed order and results are reproducible.
+//   bin 0  no in-edges: x' = (1-d)/n exactly, so only iterations 1 and 2 (which
+//          fill both c buffers) touch these rows
+//   bin 1  deg <= 4      one thread per row, four rows per thread
+//   bin 2  deg <= 16     4 lanes per row
+//   bin 3  deg <= 64     8 lanes per row
+//   bin 4  deg <= 2048   one warp per row        | segmented: deg <= 512, 8 lanes
+//   bin 5  deg <= 32768  one CTA per row         | segmented: one warp
+//   bin 6  larger        32768-arc chunks per CTA + ordered fix-up (hub rows)
+//
+// L2 blocking ("segmented" bins): when the contribution array is larger than
+// the segment size, rows of bins 4-6 are pulled one source segment
+// [s*W, (s+1)*W) at a time.  CSC rows are sorted by source, so a segment is a
+// contiguous sub-range of every row (split points found once per trial by
+// binary search); one pass per segment keeps that segment's contributions hot
+// in L2 while the index stream flows through with evict-first loads.  Row
+// partial sums (FP64) are added in ascending segment order, so every sum still
+// has a fixed order and results are reproducible run to run.
 #include <cuda_bf16.h>
 
 #include <type_traits>
+#include <vector>
 
 #include "graph.cuh"
 #include "scan.cuh"
 
 namespace gap {
 
-enum { BIN_G1 = 0, BIN_G4, BIN_G8, BIN_G32, BIN_CTA, BIN_HUB, NBINS };
+constexpr int NBINS = GAP_PR_BINS;
+enum { BIN_ZERO = 0, BIN_1, BIN_2, BIN_3, BIN_4, BIN_5, BIN_HUB };
+constexpr int LANES_CTA = 256;
+constexpr int LANES_HUB = 0;
+
+struct BinSpec {
+  int64_t hi;   // inclusive upper in-degree
+  int32_t lanes;
+  int32_t seg;
+};
 
 struct Tuning {
-  int64_t hi[NBINS - 1];  // inclusive upper in-degree of bins 0..NBINS-2
-  int64_t hub_chunk;      // arcs per hub chunk
+  BinSpec bin[NBINS];
+  int64_t hub_chunk;
+  int segments;
+  int64_t seg_width;  // vertices per source segment
 };
 
 struct PrCtrl {
@@ -45,7 +66,8 @@ struct PrCtrl {
   int32_t read_bf16;
   int32_t write_bf16;
   int32_t ladder;  // 1: switch BF16 -> FP32 once delta <= ladder_thresh
-  int32_t pad[3];
+  int32_t zero_fill_until;  // rows without in-edges are written while iter < this
+  int32_t pad[2];
   double ladder_thresh;
   gap_pr_stats_t st;
 };
@@ -62,8 +84,19 @@ struct PrArgs {
   void* c1;
   Acc base, d;
   const PrCtrl* ctrl;
-  double* partial;  // this kernel's block partials of delta
+  double* partial;  // this launch's block partials of delta
   int kahan;
+  int64_t kahan_thr;
+};
+
+// Per-trial data of the segmented rows list[base .. base+rows), indexed by the
+// local position li = i - base (so every stream below is read sequentially).
+struct SegArgs {
+  int64_t base;
+  int S;
+  const int64_t* __restrict__ rs;   // row start off[v]
+  const int32_t* __restrict__ bnd;  // bnd[li*S + k] = end of segment k within the row
+  double* __restrict__ pp;          // running row sum over finished segments
 };
 
 // ---- loads ------------------------------------------------------------------
@@ -78,6 +111,20 @@ __device__ __forceinline__ float ld_c_f<__nv_bfloat16>(const __nv_bfloat16* c, i
   return __bfloat162float(__ldg(c + u));
 }
 
+template <class Acc, class CT>
+__device__ __forceinline__ Acc ld_c(const CT* c, int32_t u) {
+  if constexpr (std::is_same<Acc, double>::value)
+    return __ldg(reinterpret_cast<const double*>(c) + u);
+  else
+    return ld_c_f(c, u);
+}
+
+template <class Acc>
+__device__ __forceinline__ Acc add_rn(Acc a, Acc b) {
+  if constexpr (std::is_same<Acc, double>::value) return __dadd_rn(a, b);
+  else return __fadd_rn(a, b);
+}
+
 // Sum of c[idx[j]] for j = b + lane, b + lane + G, ... < e (lane-strided, fixed order).
 template <int G, class Acc, class CT>
 __device__ __forceinline__ Acc gather_lane(const int32_t* __restrict__ idx, const CT* __restrict__ c, int64_t b,
@@ -87,34 +134,13 @@ __device__ __forceinline__ Acc gather_lane(const int32_t* __restrict__ idx, cons
   for (; j + 3 * G < e; j += 4 * G) {
     const int32_t u0 = ld_idx(idx + j), u1 = ld_idx(idx + j + G), u2 = ld_idx(idx + j + 2 * G),
                   u3 = ld_idx(idx + j + 3 * G);
-    Acc c0, c1, c2, c3;
-    if constexpr (std::is_same<Acc, double>::value) {
-      c0 = __ldg(reinterpret_cast<const double*>(c) + u0);
-      c1 = __ldg(reinterpret_cast<const double*>(c) + u1);
-      c2 = __ldg(reinterpret_cast<const double*>(c) + u2);
-      c3 = __ldg(reinterpret_cast<const double*>(c) + u3);
-      s = __dadd_rn(s, c0);
-      s = __dadd_rn(s, c1);
-      s = __dadd_rn(s, c2);
-      s = __dadd_rn(s, c3);
-    } else {
-      c0 = ld_c_f(c, u0);
-      c1 = ld_c_f(c, u1);
-      c2 = ld_c_f(c, u2);
-      c3 = ld_c_f(c, u3);
-      s = __fadd_rn(s, c0);
-      s = __fadd_rn(s, c1);
-      s = __fadd_rn(s, c2);
-      s = __fadd_rn(s, c3);
-    }
+    const Acc c0 = ld_c<Acc>(c, u0), c1 = ld_c<Acc>(c, u1), c2 = ld_c<Acc>(c, u2), c3 = ld_c<Acc>(c, u3);
+    s = add_rn(s, c0);
+    s = add_rn(s, c1);
+    s = add_rn(s, c2);
+    s = add_rn(s, c3);
   }
-  for (; j < e; j += G) {
-    const int32_t u = ld_idx(idx + j);
-    if constexpr (std::is_same<Acc, double>::value)
-      s = __dadd_rn(s, __ldg(reinterpret_cast<const double*>(c) + u));
-    else
-      s = __fadd_rn(s, ld_c_f(c, u));
-  }
+  for (; j < e; j += G) s = add_rn(s, ld_c<Acc>(c, ld_idx(idx + j)));
   return s;
 }
 
@@ -145,16 +171,33 @@ __device__ __forceinline__ double gather_lane_kahan(const int32_t* __restrict__ 
   return (double)s - (double)comp;
 }
 
+// Row sum over [b, e) by one lane of a group with STRIDE lanes: FP64 kernels
+// sum in FP64; FP32 kernels sum in FP32 (Kahan when asked) and return FP64.
+template <int STRIDE, class Acc>
+__device__ __forceinline__ double lane_sum(const PrArgs<Acc>& a, const void* cin, bool rb, int64_t b, int64_t e,
+                                           int lane, bool kahan) {
+  if constexpr (std::is_same<Acc, double>::value) {
+    return gather_lane<STRIDE, double, double>(a.idx, reinterpret_cast<const double*>(cin), b, e, lane);
+  } else {
+    if (kahan)
+      return rb ? gather_lane_kahan(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, lane, STRIDE)
+                : gather_lane_kahan(a.idx, reinterpret_cast<const float*>(cin), b, e, lane, STRIDE);
+    return rb ? (double)gather_lane<STRIDE, float, __nv_bfloat16>(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin),
+                                                                  b, e, lane)
+              : (double)gather_lane<STRIDE, float, float>(a.idx, reinterpret_cast<const float*>(cin), b, e, lane);
+  }
+}
+
 template <class Acc>
 __device__ __forceinline__ double update_row(const PrArgs<Acc>& a, int64_t v, Acc sum, void* cout, bool wb) {
-  const Acc xo = a.x[v];
+  const Acc xo = __ldcs(a.x + v);
   Acc xn;
   if constexpr (std::is_same<Acc, double>::value)
     xn = __dadd_rn(a.base, __dmul_rn(a.d, sum));
   else
     xn = __fadd_rn(a.base, __fmul_rn(a.d, sum));
-  a.x[v] = xn;
-  const int32_t deg = a.outdeg[v];
+  __stcs(a.x + v, xn);
+  const int32_t deg = __ldcs(a.outdeg + v);
   const Acc cv = deg > 0 ? xn / (Acc)deg : Acc(0);
   if constexpr (std::is_same<Acc, double>::value) {
     reinterpret_cast<double*>(cout)[v] = cv;
@@ -168,16 +211,105 @@ __device__ __forceinline__ double update_row(const PrArgs<Acc>& a, int64_t v, Ac
   return dd < 0 ? -dd : dd;
 }
 
-// ---- group-per-row kernels (G lanes per row, G in {1,4,8,32}) -------------
+struct IterState {
+  int it;
+  bool rb, wb;
+  const void* cin;
+  void* cout;
+};
+
+template <class Acc>
+__device__ __forceinline__ IterState iter_state(const PrArgs<Acc>& a) {
+  IterState s;
+  s.it = a.ctrl->iter;
+  s.rb = a.ctrl->read_bf16 != 0;
+  s.wb = a.ctrl->write_bf16 != 0;
+  s.cin = (s.it & 1) ? a.c1 : a.c0;
+  s.cout = (s.it & 1) ? a.c0 : a.c1;
+  return s;
+}
+
 constexpr int PR_THREADS = 256;
 
+__device__ __forceinline__ void write_partial(double dl, double* partial) {
+  __shared__ double sh[32];
+  dl = block_sum(dl, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = dl;
+}
+
+// ---- bin 0: rows without in-edges -------------------------------------------
+// x' = (1-d)/n exactly; once two iterations have written both c buffers in the
+// current contribution format, x and c already hold their final values and the
+// launch returns at once (block partial 0).  A BF16 -> FP32 ladder switch asks
+// for two more writes.
+template <class Acc>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_zero(PrArgs<Acc> a) {
+  const IterState st = iter_state(a);
+  double dl = 0.0;
+  if (st.it < a.ctrl->zero_fill_until) {
+    for (int64_t i = a.begin + blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; i < a.end;
+         i += (int64_t)gridDim.x * PR_THREADS)
+      dl += update_row(a, __ldcs(a.list + i), Acc(0), st.cout, st.wb);
+  }
+  write_partial(dl, a.partial);
+}
+
+// ---- bin 1: short rows, one thread per row, RPT rows per thread -------------
+// All loads of RPT rows are issued before the first dependent add, so each
+// thread keeps up to RPT*MAXD gathers in flight.
+template <class Acc, int RPT, int MAXD>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_short(PrArgs<Acc> a) {
+  const IterState st = iter_state(a);
+  double dl = 0.0;
+  const int64_t T = (int64_t)gridDim.x * PR_THREADS;
+  for (int64_t i0 = a.begin + (blockIdx.x * (int64_t)PR_THREADS + threadIdx.x); i0 < a.end; i0 += T * RPT) {
+    int64_t v[RPT], b[RPT];
+    int n[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int64_t i = i0 + r * T;
+      v[r] = i < a.end ? __ldcs(a.list + i) : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      b[r] = v[r] >= 0 ? a.off[v[r]] : 0;
+      n[r] = v[r] >= 0 ? (int)(a.off[v[r] + 1] - b[r]) : 0;
+    }
+    int32_t u[RPT][MAXD];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) u[r][k] = k < n[r] ? ld_idx(a.idx + b[r] + k) : -1;
+    Acc s[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      Acc cv[MAXD];
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) {
+        if constexpr (std::is_same<Acc, double>::value) {
+          cv[k] = u[r][k] >= 0 ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u[r][k]) : 0.0;
+        } else {
+          cv[k] = u[r][k] >= 0 ? (st.rb ? ld_c_f(reinterpret_cast<const __nv_bfloat16*>(st.cin), u[r][k])
+                                        : ld_c_f(reinterpret_cast<const float*>(st.cin), u[r][k]))
+                               : 0.f;
+        }
+      }
+      s[r] = Acc(0);
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k)
+        if (k < n[r]) s[r] = add_rn(s[r], cv[k]);
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (v[r] >= 0) dl += update_row(a, v[r], s[r], st.cout, st.wb);
+  }
+  write_partial(dl, a.partial);
+}
+
+// ---- group-per-row kernels (G lanes per row) --------------------------------
 template <int G, class Acc>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_group(PrArgs<Acc> a) {
-  __shared__ double sh[32];
-  const int it = a.ctrl->iter;
-  const bool rb = a.ctrl->read_bf16 != 0, wb = a.ctrl->write_bf16 != 0;
-  const void* cin = (it & 1) ? a.c1 : a.c0;
-  void* cout = (it & 1) ? a.c0 : a.c1;
+  const IterState st = iter_state(a);
   constexpr int RPW = 32 / G;  // rows per warp per round
   const int lane = threadIdx.x & (G - 1);
   const int grp = (threadIdx.x & 31) / G;
@@ -187,120 +319,146 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_group(PrArgs<Acc> a) {
   for (int64_t wb0 = a.begin + warp_id * RPW; wb0 < a.end; wb0 += nwarps * RPW) {
     const int64_t i = wb0 + grp;
     const bool has = i < a.end;
-    const int64_t v = has ? a.list[i] : 0;
+    const int64_t v = has ? __ldcs(a.list + i) : 0;
     const int64_t b = has ? a.off[v] : 0, e = has ? a.off[v + 1] : 0;
     Acc s;
     if constexpr (std::is_same<Acc, double>::value) {
-      s = gather_lane<G, double, double>(a.idx, reinterpret_cast<const double*>(cin), b, e, lane);
+      s = gather_lane<G, double, double>(a.idx, reinterpret_cast<const double*>(st.cin), b, e, lane);
     } else {
-      if (rb)
-        s = gather_lane<G, float, __nv_bfloat16>(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, lane);
-      else
-        s = gather_lane<G, float, float>(a.idx, reinterpret_cast<const float*>(cin), b, e, lane);
+      s = st.rb ? gather_lane<G, float, __nv_bfloat16>(a.idx, reinterpret_cast<const __nv_bfloat16*>(st.cin), b,
+                                                       e, lane)
+                : gather_lane<G, float, float>(a.idx, reinterpret_cast<const float*>(st.cin), b, e, lane);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
-    if (has && lane == 0) dl += update_row(a, v, s, cout, wb);
+    if (has && lane == 0) dl += update_row(a, v, s, st.cout, st.wb);
   }
-  dl = block_sum(dl, sh);
-  if (threadIdx.x == 0) a.partial[blockIdx.x] = dl;
+  write_partial(dl, a.partial);
 }
 
 // ---- CTA-per-row kernel ------------------------------------------------------
 template <class Acc>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_cta(PrArgs<Acc> a) {
   __shared__ double sh[32];
-  const int it = a.ctrl->iter;
-  const bool rb = a.ctrl->read_bf16 != 0, wb = a.ctrl->write_bf16 != 0;
-  const void* cin = (it & 1) ? a.c1 : a.c0;
-  void* cout = (it & 1) ? a.c0 : a.c1;
+  const IterState st = iter_state(a);
   double dl = 0.0;
   for (int64_t i = a.begin + blockIdx.x; i < a.end; i += gridDim.x) {
     const int64_t v = a.list[i];
     const int64_t b = a.off[v], e = a.off[v + 1];
-    double part;
-    if constexpr (std::is_same<Acc, double>::value) {
-      part = gather_lane<PR_THREADS, double, double>(a.idx, reinterpret_cast<const double*>(cin), b, e,
-                                                     threadIdx.x);
-    } else {
-      if (a.kahan) {
-        part = rb ? gather_lane_kahan(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, threadIdx.x,
-                                      PR_THREADS)
-                  : gather_lane_kahan(a.idx, reinterpret_cast<const float*>(cin), b, e, threadIdx.x, PR_THREADS);
-      } else {
-        part = rb ? gather_lane<PR_THREADS, float, __nv_bfloat16>(
-                        a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, threadIdx.x)
-                  : gather_lane<PR_THREADS, float, float>(a.idx, reinterpret_cast<const float*>(cin), b, e,
-                                                          threadIdx.x);
-      }
-    }
+    const double part = lane_sum<PR_THREADS>(a, st.cin, st.rb, b, e, threadIdx.x, a.kahan != 0);
     const double tot = block_sum(part, sh);
-    if (threadIdx.x == 0) dl += update_row(a, v, (Acc)tot, cout, wb);
+    if (threadIdx.x == 0) dl += update_row(a, v, (Acc)tot, st.cout, st.wb);
   }
-  dl = block_sum(dl, sh);
-  if (threadIdx.x == 0) a.partial[blockIdx.x] = dl;
+  write_partial(dl, a.partial);
 }
 
 // ---- hub rows: chunk partials + ordered fix-up --------------------------------
-template <class Acc>
-__global__ void __launch_bounds__(PR_THREADS) k_pull_hub_chunks(PrArgs<Acc> a, const int64_t* __restrict__ cstart,
-                                                                 int64_t nhubs, int64_t chunk,
-                                                                 double* __restrict__ csum) {
+__device__ __forceinline__ int64_t hub_of_chunk(const int64_t* cstart, int64_t nhubs, int64_t cid) {
+  int64_t lo = 0, hi = nhubs - 1;  // largest h with cstart[h] <= cid
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (cstart[mid] <= cid) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Chunk cid of hub h covers arcs [rb + (cid - cstart[h]) * chunk, ...) of the
+// hub's row (SEG: of its segment-s sub-range).
+template <class Acc, bool SEG>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_hub_chunks(PrArgs<Acc> a, SegArgs sg, int s,
+                                                                 const int64_t* __restrict__ cstart, int64_t nhubs,
+                                                                 int64_t chunk, double* __restrict__ csum) {
   __shared__ double sh[32];
-  const int it = a.ctrl->iter;
-  const bool rb = a.ctrl->read_bf16 != 0;
-  const void* cin = (it & 1) ? a.c1 : a.c0;
+  const IterState st = iter_state(a);
   const int64_t total = cstart[nhubs];
   for (int64_t cid = blockIdx.x; cid < total; cid += gridDim.x) {
-    int64_t lo = 0, hi = nhubs - 1;  // largest h with cstart[h] <= cid
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (cstart[mid] <= cid) lo = mid; else hi = mid - 1;
-    }
-    const int64_t v = a.list[a.begin + lo];
-    const int64_t rb0 = a.off[v], re = a.off[v + 1];
-    const int64_t b = rb0 + (cid - cstart[lo]) * chunk;
-    const int64_t e = b + chunk < re ? b + chunk : re;
-    double part;
-    if constexpr (std::is_same<Acc, double>::value) {
-      part = gather_lane<PR_THREADS, double, double>(a.idx, reinterpret_cast<const double*>(cin), b, e,
-                                                     threadIdx.x);
+    const int64_t h = hub_of_chunk(cstart, nhubs, cid);
+    int64_t rb, re;
+    if constexpr (SEG) {
+      const int64_t li = a.begin + h - sg.base;
+      const int64_t r0 = sg.rs[li];
+      rb = r0 + (s ? sg.bnd[li * sg.S + s - 1] : 0);
+      re = r0 + sg.bnd[li * sg.S + s];
     } else {
-      if (a.kahan) {
-        part = rb ? gather_lane_kahan(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, threadIdx.x,
-                                      PR_THREADS)
-                  : gather_lane_kahan(a.idx, reinterpret_cast<const float*>(cin), b, e, threadIdx.x, PR_THREADS);
-      } else {
-        part = rb ? gather_lane<PR_THREADS, float, __nv_bfloat16>(
-                        a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, threadIdx.x)
-                  : gather_lane<PR_THREADS, float, float>(a.idx, reinterpret_cast<const float*>(cin), b, e,
-                                                          threadIdx.x);
-      }
+      const int64_t v = a.list[a.begin + h];
+      rb = a.off[v];
+      re = a.off[v + 1];
     }
+    const int64_t b = rb + (cid - cstart[h]) * chunk;
+    const int64_t e = b + chunk < re ? b + chunk : re;
+    const double part = lane_sum<PR_THREADS>(a, st.cin, st.rb, b, e, threadIdx.x, a.kahan != 0);
     const double tot = block_sum(part, sh);
     if (threadIdx.x == 0) csum[cid] = tot;
   }
 }
 
-template <class Acc>
-__global__ void __launch_bounds__(PR_THREADS) k_hub_fixup(PrArgs<Acc> a, const int64_t* __restrict__ cstart,
-                                                           int64_t nhubs, const double* __restrict__ csum) {
-  __shared__ double sh[32];
-  const bool wb = a.ctrl->write_bf16 != 0;
-  const int it = a.ctrl->iter;
-  void* cout = (it & 1) ? a.c0 : a.c1;
+// One warp per hub adds its chunk sums in order; SEG: into the running row
+// sum, and the last segment applies the update.
+template <class Acc, bool SEG>
+__global__ void __launch_bounds__(PR_THREADS) k_hub_fixup(PrArgs<Acc> a, SegArgs sg, int s,
+                                                           const int64_t* __restrict__ cstart, int64_t nhubs,
+                                                           const double* __restrict__ csum) {
+  const IterState st = iter_state(a);
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   double dl = 0.0;
   for (int64_t h = warp_id; h < nhubs; h += nwarps) {
-    double s = 0.0;
-    for (int64_t k = cstart[h] + lane; k < cstart[h + 1]; k += 32) s += csum[k];
-    s = warp_sum(s);
-    if (lane == 0) dl += update_row(a, a.list[a.begin + h], (Acc)s, cout, wb);
+    double t = 0.0;
+    for (int64_t k = cstart[h] + lane; k < cstart[h + 1]; k += 32) t += csum[k];
+    t = warp_sum(t);
+    if (lane == 0) {
+      if constexpr (SEG) {
+        const int64_t li = a.begin + h - sg.base;
+        const double run = s ? sg.pp[li] + t : t;
+        if (s + 1 < sg.S)
+          sg.pp[li] = run;
+        else
+          dl += update_row(a, a.list[a.begin + h], (Acc)run, st.cout, st.wb);
+      } else {
+        dl += update_row(a, a.list[a.begin + h], (Acc)t, st.cout, st.wb);
+      }
+    }
   }
-  dl = block_sum(dl, sh);
-  if (threadIdx.x == 0) a.partial[blockIdx.x] = dl;
+  if (!SEG || s + 1 == sg.S) write_partial(dl, a.partial);
+}
+
+// ---- segmented group kernel: segment s of each row ----------------------------
+template <int G, class Acc>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_group_seg(PrArgs<Acc> a, SegArgs sg, int s) {
+  const IterState st = iter_state(a);
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & (G - 1);
+  const int grp = (threadIdx.x & 31) / G;
+  const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
+  const bool last = s + 1 == sg.S;
+  double dl = 0.0;
+  for (int64_t wb0 = a.begin + warp_id * RPW; wb0 < a.end; wb0 += nwarps * RPW) {
+    const int64_t i = wb0 + grp;
+    const bool has = i < a.end;
+    const int64_t li = i - sg.base;
+    int64_t b = 0, e = 0, deg = 0;
+    if (has) {
+      const int64_t r0 = __ldcs(sg.rs + li);
+      const int32_t* bd = sg.bnd + li * sg.S;
+      b = r0 + (s ? __ldcs(bd + s - 1) : 0);
+      e = r0 + __ldcs(bd + s);
+      deg = __ldcs(bd + sg.S - 1);
+    }
+    const bool kahan = a.kahan && deg > a.kahan_thr;
+    double t = lane_sum<G>(a, st.cin, st.rb, b, e, lane, kahan);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, G);
+    if (has && lane == 0) {
+      const double run = s ? __ldcs(sg.pp + li) + t : t;
+      if (!last)
+        __stcs(sg.pp + li, run);
+      else
+        dl += update_row(a, __ldcs(a.list + i), (Acc)run, st.cout, st.wb);
+    }
+  }
+  if (last) write_partial(dl, a.partial);
 }
 
 // ---- per-iteration finalize: fixed-order delta reduction and stop test -------
@@ -323,7 +481,10 @@ __global__ void __launch_bounds__(1024) k_finalize(PrCtrl* ctrl, const double* _
     const int stop = conv || (k + 1 >= max_iters);
     ctrl->done = stop;
     ctrl->read_bf16 = ctrl->write_bf16;
-    if (ctrl->ladder && s <= ctrl->ladder_thresh) ctrl->write_bf16 = 0;
+    if (ctrl->ladder && ctrl->write_bf16 && s <= ctrl->ladder_thresh) {
+      ctrl->write_bf16 = 0;
+      ctrl->zero_fill_until = k + 3;  // iterations k+1, k+2 write FP32 into both buffers
+    }
     if (use_handle) cudaGraphSetConditional(handle, stop ? 0u : 1u);
   }
 }
@@ -333,14 +494,18 @@ constexpr int BN_THREADS = 1024;
 constexpr int BN_ITEMS = 4;
 constexpr int BN_TILE = BN_THREADS * BN_ITEMS;
 
-__device__ __forceinline__ int bin_of(int64_t deg, const Tuning& t) {
+struct BinHi {
+  int64_t hi[NBINS - 1];
+};
+
+__device__ __forceinline__ int bin_of(int64_t deg, const BinHi& t) {
   int b = 0;
 #pragma unroll
   for (int q = 0; q < NBINS - 1; ++q) b += deg > t.hi[q] ? 1 : 0;
   return b;
 }
 
-__global__ void __launch_bounds__(BN_THREADS) k_bin_count(const int64_t* __restrict__ off, int64_t n, Tuning t,
+__global__ void __launch_bounds__(BN_THREADS) k_bin_count(const int64_t* __restrict__ off, int64_t n, BinHi t,
                                                            uint32_t* __restrict__ counts, int64_t tiles,
                                                            int64_t* __restrict__ bin_arcs) {
   __shared__ uint32_t h[NBINS];
@@ -369,7 +534,7 @@ __global__ void __launch_bounds__(BN_THREADS) k_bin_count(const int64_t* __restr
 }
 
 // Stable scatter: within a tile, vertex order (round, warp, lane) is ascending v.
-__global__ void __launch_bounds__(BN_THREADS) k_bin_scatter(const int64_t* __restrict__ off, int64_t n, Tuning t,
+__global__ void __launch_bounds__(BN_THREADS) k_bin_scatter(const int64_t* __restrict__ off, int64_t n, BinHi t,
                                                              const int64_t* __restrict__ offs, int64_t tiles,
                                                              int32_t* __restrict__ list) {
   __shared__ uint32_t wc[BN_THREADS / 32][NBINS];
@@ -405,12 +570,13 @@ __global__ void __launch_bounds__(BN_THREADS) k_bin_scatter(const int64_t* __res
   }
 }
 
-// One block: bin boundaries -> meta[0..NBINS], hub chunk starts, meta[NBINS+1] = chunks.
+// One block: bin boundaries -> meta[0..NBINS]; with hub_chunks, hub chunk
+// starts of whole rows and meta[NBINS+1] = their total.
 __global__ void __launch_bounds__(1024) k_bin_finish(const int64_t* __restrict__ offs, int64_t tiles, int64_t n,
                                                       const int64_t* __restrict__ off,
                                                       const int32_t* __restrict__ list, int64_t chunk,
                                                       int64_t* __restrict__ cstart, int64_t* __restrict__ meta,
-                                                      int64_t* __restrict__ bin_rows) {
+                                                      int64_t* __restrict__ bin_rows, int hub_chunks) {
   __shared__ int64_t sh[33];
   __shared__ int64_t starts[NBINS + 1];
   if (threadIdx.x < NBINS) starts[threadIdx.x] = offs[(int64_t)threadIdx.x * tiles];
@@ -418,23 +584,79 @@ __global__ void __launch_bounds__(1024) k_bin_finish(const int64_t* __restrict__
   __syncthreads();
   const int64_t hb = starts[BIN_HUB], nh = n - hb;
   int64_t carry = 0;
-  for (int64_t base = 0; base < nh; base += blockDim.x) {
-    const int64_t h = base + threadIdx.x;
-    int64_t c = 0;
-    if (h < nh) {
-      const int64_t v = list[hb + h];
-      c = (off[v + 1] - off[v] + chunk - 1) / chunk;
+  if (hub_chunks) {
+    for (int64_t base = 0; base < nh; base += blockDim.x) {
+      const int64_t h = base + threadIdx.x;
+      int64_t c = 0;
+      if (h < nh) {
+        const int64_t v = list[hb + h];
+        c = (off[v + 1] - off[v] + chunk - 1) / chunk;
+      }
+      int64_t tot;
+      const int64_t ex = block_exscan_i64(c, sh, &tot);
+      if (h < nh) cstart[h] = carry + ex;
+      carry += tot;
     }
-    int64_t tot;
-    const int64_t ex = block_exscan_i64(c, sh, &tot);
-    if (h < nh) cstart[h] = carry + ex;
-    carry += tot;
+    if (threadIdx.x == 0) cstart[nh] = carry;
   }
   if (threadIdx.x == 0) {
-    cstart[nh] = carry;
     for (int q = 0; q <= NBINS; ++q) meta[q] = starts[q];
     for (int q = 0; q < NBINS; ++q) bin_rows[q] = starts[q + 1] - starts[q];
     meta[NBINS + 1] = carry;
+  }
+}
+
+// Split points of the segmented rows: bnd[li*S + k] = number of row entries
+// below (k+1)*W, i.e. the end of segment k (bnd[li*S + S-1] = degree).
+__global__ void k_seg_setup(const int32_t* __restrict__ list, int64_t base, int64_t rows,
+                            const int64_t* __restrict__ off, const int32_t* __restrict__ idx, int S, int64_t W,
+                            int64_t* __restrict__ rs, int32_t* __restrict__ bnd) {
+  for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < rows;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = list[base + li];
+    const int64_t r0 = off[v], deg = off[v + 1] - r0;
+    rs[li] = r0;
+    int64_t lo = 0;
+    for (int k = 0; k + 1 < S; ++k) {
+      const int64_t key = (int64_t)(k + 1) * W;
+      int64_t l = lo, h = deg;  // first position with idx >= key
+      while (l < h) {
+        const int64_t mid = (l + h) >> 1;
+        if ((int64_t)idx[r0 + mid] < key) l = mid + 1; else h = mid;
+      }
+      bnd[li * S + k] = (int32_t)l;
+      lo = l;
+    }
+    bnd[li * S + S - 1] = (int32_t)deg;
+  }
+}
+
+// Per-segment hub chunk tables: cstart[s*(nh+1) + h]; totals to meta_seg[s].
+__global__ void __launch_bounds__(1024) k_hub_seg_finish(const int32_t* __restrict__ bnd, int64_t hub_li0,
+                                                          int64_t nh, int S, int64_t chunk,
+                                                          int64_t* __restrict__ cstart, int64_t* __restrict__ meta_seg) {
+  __shared__ int64_t sh[33];
+  for (int s = 0; s < S; ++s) {
+    int64_t carry = 0;
+    int64_t* cs = cstart + (int64_t)s * (nh + 1);
+    for (int64_t base = 0; base < nh; base += blockDim.x) {
+      const int64_t h = base + threadIdx.x;
+      int64_t c = 0;
+      if (h < nh) {
+        const int32_t* bd = bnd + (hub_li0 + h) * S;
+        const int64_t len = (int64_t)bd[s] - (s ? (int64_t)bd[s - 1] : 0);
+        c = (len + chunk - 1) / chunk;
+      }
+      int64_t tot;
+      const int64_t ex = block_exscan_i64(c, sh, &tot);
+      if (h < nh) cs[h] = carry + ex;
+      carry += tot;
+    }
+    if (threadIdx.x == 0) {
+      cs[nh] = carry;
+      meta_seg[s] = carry;
+    }
+    __syncthreads();
   }
 }
 
@@ -463,6 +685,7 @@ __global__ void k_ctrl_init(PrCtrl* ctrl, int write_bf16, int ladder, double lad
     ctrl->read_bf16 = write_bf16;
     ctrl->ladder = ladder;
     ctrl->ladder_thresh = ladder_thresh;
+    ctrl->zero_fill_until = 2;
   }
 }
 
@@ -486,26 +709,42 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
 
 // ---- host orchestration ------------------------------------------------------
 
-static Tuning make_tuning(const gap_pr_options& o) {
+constexpr int64_t DEFAULT_SEGMENT_BYTES = 40ll << 20;  // GB300: ~126 MB of L2 over two dies
+constexpr int64_t HUB_CHUNK = 32768;
+constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
+
+static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_bytes) {
   Tuning t;
-  if (o.deterministic) {
-    for (int q = 0; q < NBINS - 1; ++q) t.hi[q] = INT64_MAX;
-    t.hub_chunk = 32768;
+  t.hub_chunk = HUB_CHUNK;
+  t.segments = 1;
+  t.seg_width = n;
+  if (o.deterministic) {  // one thread per row, ascending sources: the oracle's order
+    for (int q = 0; q < NBINS; ++q) t.bin[q] = {INT64_MAX, 1, 0};
     return t;
   }
-  t.hi[BIN_G1] = 4;
-  t.hi[BIN_G4] = 16;
-  t.hi[BIN_G8] = 64;
-  t.hi[BIN_G32] = 2048;
-  t.hi[BIN_CTA] = 32768;
-  t.hub_chunk = 32768;
-  // rows above the compensation threshold must reach a CTA/hub kernel
-  if (o.kahan_hubs && o.hub_threshold > 0) {
-    for (int q = 0; q <= BIN_G32; ++q)
-      if (t.hi[q] > o.hub_threshold) t.hi[q] = o.hub_threshold;
-    for (int q = 1; q <= BIN_G32; ++q)
-      if (t.hi[q] < t.hi[q - 1]) t.hi[q] = t.hi[q - 1];
+  const int64_t seg_bytes = o.segment_bytes == 0 ? DEFAULT_SEGMENT_BYTES : o.segment_bytes;
+  const int64_t cbytes = (int64_t)c_elem_bytes * n;
+  if (seg_bytes > 0 && cbytes > seg_bytes) {
+    t.segments = (int)((cbytes + seg_bytes - 1) / seg_bytes);
+    if (t.segments > 64) t.segments = 64;
+    t.seg_width = (n + t.segments - 1) / t.segments;
   }
+  const bool seg = t.segments > 1;
+  t.bin[BIN_ZERO] = {0, 1, 0};
+  t.bin[BIN_1] = {4, 1, 0};
+  t.bin[BIN_2] = {16, 4, 0};
+  t.bin[BIN_3] = {64, 8, 0};
+  if (seg) {
+    t.bin[BIN_4] = {512, 8, 1};
+    t.bin[BIN_5] = {32768, 32, 1};
+  } else {
+    t.bin[BIN_4] = {2048, 32, 0};
+    t.bin[BIN_5] = {32768, LANES_CTA, 0};
+    // rows above the compensation threshold must reach the CTA / hub kernels
+    if (o.kahan_hubs && o.hub_threshold > 0 && o.hub_threshold < t.bin[BIN_4].hi)
+      t.bin[BIN_4].hi = o.hub_threshold > t.bin[BIN_3].hi ? o.hub_threshold : t.bin[BIN_3].hi;
+  }
+  t.bin[BIN_HUB] = {INT64_MAX, LANES_HUB, seg ? 1 : 0};
   return t;
 }
 
@@ -513,52 +752,56 @@ static Tuning make_tuning(const gap_pr_options& o) {
 struct PhaseTimer {
   bool on = false;
   cudaStream_t s = nullptr;
-  cudaEvent_t ev[GAP_PR_PHASES][2] = {};
-  bool pending[GAP_PR_PHASES] = {};
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ph;
   double ms[GAP_PR_PHASES] = {};
   int32_t launches[GAP_PR_PHASES] = {};
-  gap_status init(bool enable, cudaStream_t stream) {
+  size_t used = 0;
+  void init(bool enable, cudaStream_t stream) {
     on = enable;
     s = stream;
-    if (!on) return GAP_OK;
-    for (int q = 0; q < GAP_PR_PHASES; ++q)
-      for (int k = 0; k < 2; ++k) GAP_CUDA(cudaEventCreate(&ev[q][k]));
-    return GAP_OK;
   }
-  void begin(int q) {
-    if (on) cudaEventRecord(ev[q][0], s);
+  int begin() {
+    if (!on) return -1;
+    if (used + 2 > ev.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ev.push_back(e);
+      }
+      ph.resize(ev.size());
+    }
+    cudaEventRecord(ev[used], s);
+    return (int)used;
   }
-  void end(int q) {
-    if (!on) return;
-    cudaEventRecord(ev[q][1], s);
-    pending[q] = true;
+  void end(int q, int tok) {
+    if (!on || tok < 0) return;
+    cudaEventRecord(ev[tok + 1], s);
+    ph[tok] = q;
+    used = tok + 2;
     ++launches[q];
   }
-  // after a stream synchronize: add the elapsed time of every recorded phase
-  void collect() {
+  void collect() {  // after a stream synchronize
     if (!on) return;
-    for (int q = 0; q < GAP_PR_PHASES; ++q) {
-      if (!pending[q]) continue;
+    for (size_t k = 0; k + 1 < used; k += 2) {
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, ev[q][0], ev[q][1]) == cudaSuccess) ms[q] += t;
-      pending[q] = false;
+      if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) == cudaSuccess) ms[ph[k]] += t;
     }
+    used = 0;
     cudaGetLastError();
   }
   ~PhaseTimer() {
-    if (!on) return;
-    for (int q = 0; q < GAP_PR_PHASES; ++q)
-      for (int k = 0; k < 2; ++k)
-        if (ev[q][k]) cudaEventDestroy(ev[q][k]);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
 };
 
-struct LaunchPlan {
-  int grid[NBINS + 1];   // per bin kernel (+ fix-up)
-  int64_t poff[NBINS + 1];
-  int64_t np = 0;
-  int64_t meta[NBINS + 2];
-  int64_t nhubs = 0, nchunks = 0;
+enum LaunchKind { L_ZERO, L_SHORT, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
+
+struct LaunchRec {
+  LaunchKind kind;
+  int bin, lanes, s, grid, grid2;
+  int64_t poff;   // delta partial slice (-1: this launch updates no rows)
+  int64_t poff2;  // slice of a hub fix-up
 };
 
 template <class Acc>
@@ -567,20 +810,24 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   const int64_t n = g->n;
   const bool bf16 = std::is_same<Acc, float>::value && o.contrib == GAP_CONTRIB_BF16;
   const bool user_dev = is_device_ptr(user_scores);
-  const size_t cbytes = sizeof(Acc) * (size_t)n;
-  const Tuning t = make_tuning(o);
+  const size_t xbytes = sizeof(Acc) * (size_t)n;
+  const Tuning t = make_tuning(o, n, sizeof(Acc));
+  const int S = t.segments;
+  BinHi bh;
+  for (int q = 0; q < NBINS - 1; ++q) bh.hi[q] = t.bin[q].hi;
   const int64_t bn_tiles = (n + BN_TILE - 1) / BN_TILE;
-  const int64_t hub_lo = t.hi[BIN_CTA];
+  const int64_t hub_lo = t.bin[BIN_5].hi;
   const int64_t max_hubs = hub_lo >= g->m ? 1 : g->m / (hub_lo + 1) + 1;
 
   // ---- scratch (inside the trial, §2.3) ----
   Scratch xs, cbuf, list, ctrl, cnt, offs, tmp, cstart, csum, partial, meta;
+  Scratch seg_rs, seg_bnd, seg_pp, seg_cstart, seg_meta;
   Acc* x = user_scores;
   if (!user_dev) {
-    GAP_TRY(xs.get(cbytes, s));
+    GAP_TRY(xs.get(xbytes, s));
     x = xs.as<Acc>();
   }
-  GAP_TRY(cbuf.get(2 * cbytes, s));
+  GAP_TRY(cbuf.get(2 * xbytes, s));
   GAP_TRY(list.get(sizeof(int32_t) * n, s));
   GAP_TRY(ctrl.get(sizeof(PrCtrl), s));
   GAP_TRY(cnt.get(sizeof(uint32_t) * bn_tiles * NBINS, s));
@@ -589,7 +836,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   GAP_TRY(cstart.get(sizeof(int64_t) * (max_hubs + 1), s));
   GAP_TRY(meta.get(sizeof(int64_t) * (NBINS + 2), s));
   void* c0 = cbuf.p;
-  void* c1 = static_cast<char*>(cbuf.p) + cbytes;
+  void* c1 = static_cast<char*>(cbuf.p) + xbytes;
   PrCtrl* dctrl = ctrl.as<PrCtrl>();
 
   const int ladder = bf16 && o.bf16_until_log2_delta != GAP_NO_LADDER;
@@ -597,50 +844,134 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   k_ctrl_init<<<1, 32, 0, s>>>(dctrl, bf16 ? 1 : 0, ladder, thresh);
   GAP_LAUNCH_CHECK();
   PhaseTimer tm;
-  GAP_TRY(tm.init(o.timing != 0, s));
+  tm.init(o.timing != 0, s);
 
-  // ---- degree binning ----
-  tm.begin(GAP_PHASE_BIN);
-  k_bin_count<<<(unsigned)bn_tiles, BN_THREADS, 0, s>>>(g->in_off, n, t, cnt.as<uint32_t>(), bn_tiles,
+  // ---- degree binning (+ segment split points) ----
+  int tok = tm.begin();
+  k_bin_count<<<(unsigned)bn_tiles, BN_THREADS, 0, s>>>(g->in_off, n, bh, cnt.as<uint32_t>(), bn_tiles,
                                                        dctrl->st.bin_arcs);
   GAP_LAUNCH_CHECK();
   GAP_TRY(exclusive_scan_u32(cnt.as<uint32_t>(), offs.as<int64_t>(), bn_tiles * NBINS, tmp.as<int64_t>(), nullptr, s));
-  k_bin_scatter<<<(unsigned)bn_tiles, BN_THREADS, 0, s>>>(g->in_off, n, t, offs.as<int64_t>(), bn_tiles,
+  k_bin_scatter<<<(unsigned)bn_tiles, BN_THREADS, 0, s>>>(g->in_off, n, bh, offs.as<int64_t>(), bn_tiles,
                                                          list.as<int32_t>());
   GAP_LAUNCH_CHECK();
   k_bin_finish<<<1, 1024, 0, s>>>(offs.as<int64_t>(), bn_tiles, n, g->in_off, list.as<int32_t>(), t.hub_chunk,
-                                  cstart.as<int64_t>(), meta.as<int64_t>(), dctrl->st.bin_rows);
+                                  cstart.as<int64_t>(), meta.as<int64_t>(), dctrl->st.bin_rows, S == 1 ? 1 : 0);
   GAP_LAUNCH_CHECK();
-  LaunchPlan p;
-  GAP_CUDA(cudaMemcpyAsync(p.meta, meta.p, sizeof(p.meta), cudaMemcpyDeviceToHost, s));
-  tm.end(GAP_PHASE_BIN);
+  int64_t mt[NBINS + 2];
+  GAP_CUDA(cudaMemcpyAsync(mt, meta.p, sizeof(mt), cudaMemcpyDeviceToHost, s));
   GAP_CUDA(cudaStreamSynchronize(s));
+  const int64_t nhubs = mt[NBINS] - mt[BIN_HUB];
+  int64_t nchunks = mt[NBINS + 1];
+  // segmented rows are the tail of the list (bins are in degree order)
+  int first_seg = NBINS;
+  for (int q = 0; q < NBINS; ++q)
+    if (t.bin[q].seg) {
+      first_seg = q;
+      break;
+    }
+  const int64_t seg_base = first_seg < NBINS ? mt[first_seg] : n;
+  const int64_t seg_rows = n - seg_base;
+  std::vector<int64_t> seg_chunks(S, 0);
+  SegArgs sg{seg_base, S, nullptr, nullptr, nullptr};
+  if (S > 1 && seg_rows > 0) {
+    GAP_TRY(seg_rs.get(sizeof(int64_t) * seg_rows, s));
+    GAP_TRY(seg_bnd.get(sizeof(int32_t) * seg_rows * S, s));
+    GAP_TRY(seg_pp.get(sizeof(double) * seg_rows, s));
+    k_seg_setup<<<stride_grid(seg_rows, 256, 8), 256, 0, s>>>(list.as<int32_t>(), seg_base, seg_rows, g->in_off,
+                                                               g->in_idx, S, t.seg_width, seg_rs.as<int64_t>(),
+                                                               seg_bnd.as<int32_t>());
+    GAP_LAUNCH_CHECK();
+    sg.rs = seg_rs.as<int64_t>();
+    sg.bnd = seg_bnd.as<int32_t>();
+    sg.pp = seg_pp.as<double>();
+    if (nhubs > 0) {
+      GAP_TRY(seg_cstart.get(sizeof(int64_t) * S * (nhubs + 1), s));
+      GAP_TRY(seg_meta.get(sizeof(int64_t) * S, s));
+      k_hub_seg_finish<<<1, 1024, 0, s>>>(seg_bnd.as<int32_t>(), mt[BIN_HUB] - seg_base, nhubs, S, t.hub_chunk,
+                                          seg_cstart.as<int64_t>(), seg_meta.as<int64_t>());
+      GAP_LAUNCH_CHECK();
+      GAP_CUDA(cudaMemcpyAsync(seg_chunks.data(), seg_meta.p, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, s));
+      GAP_CUDA(cudaStreamSynchronize(s));
+      nchunks = 0;
+      for (int k = 0; k < S; ++k) nchunks = seg_chunks[k] > nchunks ? seg_chunks[k] : nchunks;
+    }
+  }
+  tm.end(GAP_PHASE_BIN, tok);
   tm.collect();
-  p.nhubs = p.meta[NBINS] - p.meta[BIN_HUB];
-  p.nchunks = p.meta[NBINS + 1];
-  static const int rows_per_block[BIN_CTA] = {PR_THREADS, PR_THREADS / 4, PR_THREADS / 8, PR_THREADS / 32};
-  for (int q = 0; q < NBINS; ++q) {
-    const int64_t rows = p.meta[q + 1] - p.meta[q];
-    if (q < BIN_CTA) p.grid[q] = rows > 0 ? stride_grid(rows, rows_per_block[q], 8) : 0;
-    else if (q == BIN_CTA) p.grid[q] = rows > 0 ? stride_grid(rows, 1, 8) : 0;
-    else p.grid[q] = p.nchunks > 0 ? stride_grid(p.nchunks, 1, 8) : 0;
+
+  // ---- launch plan of one iteration ----
+  std::vector<LaunchRec> plan;
+  int64_t np = 0;
+  auto rows_of = [&](int q) { return mt[q + 1] - mt[q]; };
+  auto group_grid = [&](int64_t rows, int lanes) { return stride_grid(rows, PR_THREADS / lanes, 8); };
+  for (int q = 0; q < NBINS; ++q) {  // unsegmented bins first
+    const int64_t rows = rows_of(q);
+    if (rows == 0 || t.bin[q].seg) continue;
+    LaunchRec r{};
+    r.bin = q;
+    r.lanes = t.bin[q].lanes;
+    r.poff2 = -1;
+    if (q == BIN_ZERO && !o.deterministic) {
+      r.kind = L_ZERO;
+      r.grid = stride_grid(rows, PR_THREADS, 8);
+    } else if (q == BIN_1 && !o.deterministic) {
+      r.kind = L_SHORT;
+      r.grid = stride_grid(rows, PR_THREADS * SHORT_RPT, 8);
+    } else if (r.lanes == LANES_CTA) {
+      r.kind = L_CTA;
+      r.grid = stride_grid(rows, 1, 8);
+    } else if (r.lanes == LANES_HUB) {
+      r.kind = L_HUB;
+      r.grid = nchunks > 0 ? stride_grid(nchunks, 1, 8) : 0;
+      r.grid2 = (int)((nhubs + 7) / 8);
+    } else {
+      r.kind = L_GROUP;
+      r.grid = group_grid(rows, r.lanes);
+    }
+    r.poff = np;
+    np += r.kind == L_HUB ? r.grid2 : r.grid;
+    plan.push_back(r);
   }
-  p.grid[NBINS] = p.nhubs > 0 ? (int)((p.nhubs + 7) / 8) : 0;  // fix-up: a warp per hub
-  p.np = 0;
-  for (int q = 0; q <= NBINS; ++q) {
-    p.poff[q] = p.np;
-    if (q != BIN_HUB) p.np += p.grid[q];
+  for (int sgi = 0; sgi < S && S > 1; ++sgi) {  // segment passes
+    for (int q = 0; q < NBINS; ++q) {
+      const int64_t rows = rows_of(q);
+      if (rows == 0 || !t.bin[q].seg) continue;
+      LaunchRec r{};
+      r.bin = q;
+      r.lanes = t.bin[q].lanes;
+      r.s = sgi;
+      r.poff = -1;
+      r.poff2 = -1;
+      if (r.lanes == LANES_HUB) {
+        r.kind = L_HUB_SEG;
+        r.grid = seg_chunks[sgi] > 0 ? stride_grid(seg_chunks[sgi], 1, 8) : 0;
+        r.grid2 = (int)((nhubs + 7) / 8);
+        if (sgi + 1 == S) {
+          r.poff2 = np;
+          np += r.grid2;
+        }
+      } else {
+        r.kind = L_GROUP_SEG;
+        r.grid = group_grid(rows, r.lanes);
+        if (sgi + 1 == S) {
+          r.poff = np;
+          np += r.grid;
+        }
+      }
+      plan.push_back(r);
+    }
   }
-  GAP_TRY(partial.get(sizeof(double) * (p.np > 0 ? p.np : 1), s));
-  if (p.np == 0) GAP_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double), s));
-  GAP_TRY(csum.get(sizeof(double) * (p.nchunks > 0 ? p.nchunks : 1), s));
+  GAP_TRY(partial.get(sizeof(double) * (np > 0 ? np : 1), s));
+  if (np == 0) GAP_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double), s));
+  GAP_TRY(csum.get(sizeof(double) * (nchunks > 0 ? nchunks : 1), s));
 
   // ---- x0, c0 ----
   const Acc x0 = (Acc)(1.0 / (double)n);
-  tm.begin(GAP_PHASE_INIT);
+  tok = tm.begin();
   k_init<Acc><<<stride_grid(n, 256, 8), 256, 0, s>>>(n, x0, x, g->outdeg, c0, bf16 ? 1 : 0);
   GAP_LAUNCH_CHECK();
-  tm.end(GAP_PHASE_INIT);
+  tm.end(GAP_PHASE_INIT, tok);
 
   PrArgs<Acc> a;
   a.off = g->in_off;
@@ -654,41 +985,64 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   a.d = (Acc)d;
   a.ctrl = dctrl;
   a.kahan = o.kahan_hubs ? 1 : 0;
+  a.kahan_thr = o.hub_threshold;
+  double* pbase = partial.as<double>();
 
   auto launch_body = [&](cudaStream_t ls, cudaGraphConditionalHandle h, int use_h) -> gap_status {
-    for (int q = 0; q < NBINS; ++q) {
-      if (p.grid[q] == 0) continue;
-      tm.begin(GAP_PHASE_PULL_G1 + q);
+    for (const LaunchRec& r : plan) {
       PrArgs<Acc> b = a;
-      b.begin = p.meta[q];
-      b.end = p.meta[q + 1];
-      b.partial = partial.as<double>() + p.poff[q];
-      switch (q) {
-        case BIN_G1: k_pull_group<1, Acc><<<p.grid[q], PR_THREADS, 0, ls>>>(b); break;
-        case BIN_G4: k_pull_group<4, Acc><<<p.grid[q], PR_THREADS, 0, ls>>>(b); break;
-        case BIN_G8: k_pull_group<8, Acc><<<p.grid[q], PR_THREADS, 0, ls>>>(b); break;
-        case BIN_G32: k_pull_group<32, Acc><<<p.grid[q], PR_THREADS, 0, ls>>>(b); break;
-        case BIN_CTA: k_pull_cta<Acc><<<p.grid[q], PR_THREADS, 0, ls>>>(b); break;
-        case BIN_HUB:
-          k_pull_hub_chunks<Acc><<<p.grid[q], PR_THREADS, 0, ls>>>(b, cstart.as<int64_t>(), p.nhubs, t.hub_chunk,
-                                                                   csum.as<double>());
+      b.begin = mt[r.bin];
+      b.end = mt[r.bin + 1];
+      b.partial = r.poff >= 0 ? pbase + r.poff : pbase;
+      const int phase = GAP_PHASE_PULL0 + r.bin;
+      int tk = tm.begin();
+      switch (r.kind) {
+        case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
+        case L_SHORT: k_pull_short<Acc, SHORT_RPT, 4><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
+        case L_CTA: k_pull_cta<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
+        case L_GROUP:
+          if (r.lanes == 1) k_pull_group<1, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b);
+          else if (r.lanes == 4) k_pull_group<4, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b);
+          else if (r.lanes == 8) k_pull_group<8, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b);
+          else k_pull_group<32, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b);
+          break;
+        case L_GROUP_SEG:
+          if (r.lanes == 8) k_pull_group_seg<8, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b, sg, r.s);
+          else k_pull_group_seg<32, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b, sg, r.s);
+          break;
+        case L_HUB:
+        case L_HUB_SEG: {
+          const bool segd = r.kind == L_HUB_SEG;
+          const int64_t* cs = segd ? seg_cstart.as<int64_t>() + (int64_t)r.s * (nhubs + 1) : cstart.as<int64_t>();
+          if (r.grid > 0) {
+            if (segd)
+              k_pull_hub_chunks<Acc, true><<<r.grid, PR_THREADS, 0, ls>>>(b, sg, r.s, cs, nhubs, t.hub_chunk,
+                                                                          csum.as<double>());
+            else
+              k_pull_hub_chunks<Acc, false><<<r.grid, PR_THREADS, 0, ls>>>(b, sg, 0, cs, nhubs, t.hub_chunk,
+                                                                           csum.as<double>());
+            GAP_LAUNCH_CHECK();
+          }
+          tm.end(phase, tk);
+          tk = tm.begin();
+          PrArgs<Acc> f = b;
+          f.partial = pbase + (segd ? (r.poff2 >= 0 ? r.poff2 : 0) : r.poff);
+          if (segd)
+            k_hub_fixup<Acc, true><<<r.grid2, PR_THREADS, 0, ls>>>(f, sg, r.s, cs, nhubs, csum.as<double>());
+          else
+            k_hub_fixup<Acc, false><<<r.grid2, PR_THREADS, 0, ls>>>(f, sg, 0, cs, nhubs, csum.as<double>());
           GAP_LAUNCH_CHECK();
-          tm.end(GAP_PHASE_PULL_HUB);
-          tm.begin(GAP_PHASE_HUB_FIXUP);
-          b.partial = partial.as<double>() + p.poff[NBINS];
-          k_hub_fixup<Acc><<<p.grid[NBINS], PR_THREADS, 0, ls>>>(b, cstart.as<int64_t>(), p.nhubs,
-                                                               csum.as<double>());
-          GAP_LAUNCH_CHECK();
-          tm.end(GAP_PHASE_HUB_FIXUP);
+          tm.end(GAP_PHASE_HUB_FIXUP, tk);
           continue;
+        }
       }
       GAP_LAUNCH_CHECK();
-      tm.end(GAP_PHASE_PULL_G1 + q);
+      tm.end(phase, tk);
     }
-    tm.begin(GAP_PHASE_FINALIZE);
-    k_finalize<<<1, 1024, 0, ls>>>(dctrl, partial.as<double>(), p.np, tol, max_iters, h, use_h);
+    int tk = tm.begin();
+    k_finalize<<<1, 1024, 0, ls>>>(dctrl, pbase, np, tol, max_iters, h, use_h);
     GAP_LAUNCH_CHECK();
-    tm.end(GAP_PHASE_FINALIZE);
+    tm.end(GAP_PHASE_FINALIZE, tk);
     return GAP_OK;
   };
 
@@ -742,7 +1096,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   }
 
   // ---- output + stats ----
-  tm.begin(GAP_PHASE_OUTPUT);
+  tok = tm.begin();
   {
     const int mg = stride_grid(n, 256, 4);
     Scratch mp;
@@ -752,8 +1106,8 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     k_mass_final<<<1, 1024, 0, s>>>(dctrl, mp.as<double>(), mg);
     GAP_LAUNCH_CHECK();
   }
-  if (!user_dev) GAP_CUDA(cudaMemcpyAsync(user_scores, x, cbytes, cudaMemcpyDefault, s));
-  tm.end(GAP_PHASE_OUTPUT);
+  if (!user_dev) GAP_CUDA(cudaMemcpyAsync(user_scores, x, xbytes, cudaMemcpyDefault, s));
+  tm.end(GAP_PHASE_OUTPUT, tok);
   GAP_CUDA(cudaMemcpyAsync(g->stats_host, &dctrl->st, sizeof(gap_pr_stats_t), cudaMemcpyDeviceToHost, s));
   if (tm.on) {
     GAP_CUDA(cudaStreamSynchronize(s));
@@ -763,10 +1117,18 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       g->stats_host->phase_launches[q] = tm.launches[q];
     }
   }
+  // host-side facts of this run, merged into the stats by gap_pr_stats()
   int per_iter = 1;  // finalize
-  for (int q = 0; q < NBINS; ++q) per_iter += p.grid[q] ? (q == BIN_HUB ? 2 : 1) : 0;
+  for (const LaunchRec& r : plan) per_iter += (r.kind == L_HUB || r.kind == L_HUB_SEG) ? (r.grid > 0 ? 2 : 1) : 1;
   g->launches_per_iter = per_iter;
-  g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/;
+  g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/ + (S > 1 && seg_rows > 0 ? 1 : 0) +
+                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0);
+  g->last_segments = S;
+  for (int q = 0; q < NBINS; ++q) {
+    g->last_bin_hi[q] = t.bin[q].hi;
+    g->last_bin_lanes[q] = t.bin[q].lanes;
+    g->last_bin_seg[q] = t.bin[q].seg;
+  }
   g->last_stream = s;
   g->has_run = 1;
   g->last_tol = tol;
@@ -803,6 +1165,7 @@ void gap_pr_options_default(gap_pr_options* o) {
   o->l2_window = 0;
   o->loop = GAP_LOOP_GRAPH;
   o->timing = 0;
+  o->segment_bytes = 0;
 }
 
 gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters, const gap_pr_options* opt,
@@ -850,6 +1213,12 @@ gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out) {
   GAP_CUDA(cudaStreamSynchronize(g->last_stream));
   *out = *g->stats_host;
   out->kernel_launches = g->launches_fixed + out->iterations * g->launches_per_iter;
+  out->segments = g->last_segments;
+  for (int q = 0; q < GAP_PR_BINS; ++q) {
+    out->bin_max_degree[q] = g->last_bin_hi[q];
+    out->bin_lanes[q] = g->last_bin_lanes[q];
+    out->bin_segmented[q] = g->last_bin_seg[q];
+  }
   if (out->device_error) return out->device_error;
   if (!out->converged && g->last_tol > 0.0) return GAP_WARN_NOT_CONVERGED;
   return GAP_OK;

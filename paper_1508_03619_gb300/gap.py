@@ -35,11 +35,11 @@ GAP_LOOP_GRAPH = 0
 GAP_LOOP_HOST = 1
 GAP_NO_LADDER = -(2 ** 31)
 GAP_PR_HIST = 256
-GAP_PR_PHASES = 11
-GAP_PR_BINS = 6
-PHASE_NAMES = ("bin", "init", "pull_g1", "pull_g4", "pull_g8", "pull_g32", "pull_cta", "pull_hub",
+GAP_PR_PHASES = 12
+GAP_PR_BINS = 7
+PHASE_NAMES = ("bin", "init", "pull0", "pull1", "pull2", "pull3", "pull4", "pull5", "pull6",
                "hub_fixup", "finalize", "output")
-BIN_NAMES = ("g1", "g4", "g8", "g32", "cta", "hub")
+PULL_PHASES = PHASE_NAMES[2:9]
 
 # every symbol include/gap.h declares (checked by the ABI test)
 EXPORTED = (
@@ -55,7 +55,7 @@ class gap_pr_options(ctypes.Structure):
                 ("bf16_until_log2_delta", ctypes.c_int32), ("kahan_hubs", ctypes.c_uint32),
                 ("hub_threshold", ctypes.c_int64), ("deterministic", ctypes.c_uint32),
                 ("l2_window", ctypes.c_uint32), ("loop", ctypes.c_uint32),
-                ("timing", ctypes.c_uint32)]
+                ("timing", ctypes.c_uint32), ("segment_bytes", ctypes.c_int64)]
 
 
 class gap_pr_stats_t(ctypes.Structure):
@@ -64,6 +64,9 @@ class gap_pr_stats_t(ctypes.Structure):
                 ("bf16_iters", ctypes.c_int32), ("device_error", ctypes.c_int32),
                 ("delta_hist", ctypes.c_double * GAP_PR_HIST),
                 ("bin_rows", ctypes.c_int64 * GAP_PR_BINS), ("bin_arcs", ctypes.c_int64 * GAP_PR_BINS),
+                ("bin_max_degree", ctypes.c_int64 * GAP_PR_BINS),
+                ("bin_lanes", ctypes.c_int32 * GAP_PR_BINS),
+                ("bin_segmented", ctypes.c_int32 * GAP_PR_BINS), ("segments", ctypes.c_int32),
                 ("phase_ms", ctypes.c_double * GAP_PR_PHASES),
                 ("phase_launches", ctypes.c_int32 * GAP_PR_PHASES),
                 ("kernel_launches", ctypes.c_int32)]
@@ -73,8 +76,10 @@ class gap_pr_stats_t(ctypes.Structure):
         return {"iterations": self.iterations, "converged": bool(self.converged),
                 "final_delta": self.final_delta, "mass": self.mass, "bf16_iters": self.bf16_iters,
                 "device_error": self.device_error, "deltas": list(self.delta_hist[:k]),
-                "bin_rows": dict(zip(BIN_NAMES, self.bin_rows)),
-                "bin_arcs": dict(zip(BIN_NAMES, self.bin_arcs)),
+                "bins": [{"rows": self.bin_rows[q], "arcs": self.bin_arcs[q],
+                          "max_degree": self.bin_max_degree[q], "lanes": self.bin_lanes[q],
+                          "segmented": bool(self.bin_segmented[q])} for q in range(GAP_PR_BINS)],
+                "segments": self.segments,
                 "phase_ms": dict(zip(PHASE_NAMES, self.phase_ms)),
                 "phase_launches": dict(zip(PHASE_NAMES, self.phase_launches)),
                 "kernel_launches": self.kernel_launches}

@@ -32,6 +32,12 @@ def oracle_graph(n, src, dst, symmetrize=False, dedup=True, drop_self_loops=True
     return oracle.build_csr(n, src, dst, symmetrize, dedup, drop_self_loops)
 
 
+def seg_bytes_for(n):
+    """A segment size that splits the contribution array of n vertices into
+    4 (FP32) or 8 (FP64) source segments, forcing the L2-blocked kernels."""
+    return max(64, n)
+
+
 def run_gpu(g, tol, max_iters, f64=False, host_scores=False, **opts):
     """One trial through gap_pr_run_ex; returns (x as float64 numpy, stats, status)."""
     import torch

@@ -11,7 +11,8 @@ import pytest
 
 import gapgen
 import oracle
-from gpu_helpers import D, FP64_L1, assert_fp32_parity, gpu_graph, oracle_graph, run_gpu
+from gpu_helpers import (D, FP64_L1, assert_fp32_parity, gpu_graph, oracle_graph, run_gpu,
+                         seg_bytes_for)
 from paper_1508_03619_gb300 import gap
 
 pytestmark = pytest.mark.gpu
@@ -48,25 +49,28 @@ def threshold_graph(seed=0x7):
     return n, np.concatenate(src), np.concatenate(dst)
 
 
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_fp32_fixed_iterations(cuda_device, case):
+def test_fp32_fixed_iterations(cuda_device, case, seg):
     name, n, src, dst, sym = case
     off, idx = oracle_graph(n, src, dst, sym)
     xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 20)
     g = gpu_graph(n, src, dst, sym)
-    x, st, status = run_gpu(g, 0.0, 20)
+    x, st, status = run_gpu(g, 0.0, 20, segment_bytes=seg_bytes_for(n) if seg else 0)
     assert status == gap.GAP_OK and st["iterations"] == 20
+    assert st["segments"] == (4 if seg else 1)
     assert_fp32_parity(x, xo)
     g.close()
 
 
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_fp32_tolerance_mode(cuda_device, case):
+def test_fp32_tolerance_mode(cuda_device, case, seg):
     name, n, src, dst, sym = case
     off, idx = oracle_graph(n, src, dst, sym)
     xo, ko, do = oracle.pagerank(off, idx, D, 1e-4, 100)
     g = gpu_graph(n, src, dst, sym)
-    x, st, status = run_gpu(g, 1e-4, 100)
+    x, st, status = run_gpu(g, 1e-4, 100, segment_bytes=seg_bytes_for(n) if seg else 0)
     assert status == gap.GAP_OK and st["converged"]
     assert abs(st["iterations"] - ko) <= 1
     assert oracle.verify(off, idx, x) < 1e-4  # paper §3 verifier
@@ -88,43 +92,57 @@ def test_fp64_deterministic_bitexact(cuda_device):
     g.close()
 
 
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_fp64_binned(cuda_device, case):
+def test_fp64_binned(cuda_device, case, seg):
     name, n, src, dst, sym = case
     off, idx = oracle_graph(n, src, dst, sym)
     xo, ko, _ = oracle.pagerank(off, idx, D, 0.0, 20)
     g = gpu_graph(n, src, dst, sym)
-    x, st, _ = run_gpu(g, 0.0, 20, f64=True)
+    x, st, _ = run_gpu(g, 0.0, 20, f64=True, segment_bytes=seg_bytes_for(n) if seg else 0)
+    assert st["segments"] == (8 if seg else 1)
     assert np.abs(x - xo).sum() <= FP64_L1
     g.close()
 
 
-def test_bin_boundaries_and_hubs(cuda_device):
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
+def test_bin_boundaries_and_hubs(cuda_device, seg):
     n, src, dst = threshold_graph()
     off, idx = oracle_graph(n, src, dst, False)
     xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 12)
     g = gpu_graph(n, src, dst, False)
+    sb = seg_bytes_for(n) if seg else 0
     for kahan in (1, 0):
-        x, st, _ = run_gpu(g, 0.0, 12, kahan_hubs=kahan)
+        x, st, _ = run_gpu(g, 0.0, 12, kahan_hubs=kahan, segment_bytes=sb)
         assert_fp32_parity(x, xo)
         hub_rel = np.abs(x[:20] - xo[:20]) / xo[:20]
-        print(f"kahan={kahan}: max rel error on the 20 boundary/hub rows {hub_rel.max():.3e}")
+        print(f"seg={seg} kahan={kahan}: max rel error on the 20 boundary/hub rows {hub_rel.max():.3e}")
         if kahan:
             assert hub_rel.max() < 1e-5
-    x64, _, _ = run_gpu(g, 0.0, 12, f64=True)
+        rows = sum(b["rows"] for b in st["bins"])
+        arcs = sum(b["arcs"] for b in st["bins"])
+        assert rows == n and arcs == g.m
+        assert st["bins"][6]["rows"] >= 4  # the hub bin holds the rows above 32768
+    x64, _, _ = run_gpu(g, 0.0, 12, f64=True, segment_bytes=sb)
     assert np.abs(x64 - xo).sum() <= FP64_L1
     g.close()
 
 
-def test_loop_modes_agree(cuda_device):
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
+def test_loop_modes_agree(cuda_device, seg):
     n, src, dst, sym = CASES[1][1:]
     g = gpu_graph(n, src, dst, sym)
-    xa, sa, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_GRAPH)
-    xb, sb, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_HOST)
-    assert sa["iterations"] == sb["iterations"]
+    sb = seg_bytes_for(n) if seg else 0
+    xa, sa, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_GRAPH, segment_bytes=sb)
+    xb, sb_, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_HOST, segment_bytes=sb)
+    assert sa["iterations"] == sb_["iterations"]
     assert np.array_equal(xa, xb)
-    xc, sc, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_GRAPH)
+    xc, sc, _ = run_gpu(g, 1e-4, 100, loop=gap.GAP_LOOP_GRAPH, segment_bytes=sb)
     assert np.array_equal(xa, xc)  # run-to-run reproducible
+    xt, stt, _ = run_gpu(g, 1e-4, 100, timing=1, segment_bytes=sb)
+    assert np.array_equal(xa, xt)
+    assert stt["phase_launches"]["finalize"] == stt["iterations"]
+    assert stt["kernel_launches"] > stt["iterations"]
     g.close()
 
 
@@ -137,12 +155,15 @@ def test_host_scores_buffer(cuda_device):
     g.close()
 
 
-def test_bf16_contributions_ladder(cuda_device):
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
+def test_bf16_contributions_ladder(cuda_device, seg):
     n, src, dst, sym = CASES[1][1:]
     off, idx = oracle_graph(n, src, dst, sym)
     xo, ko, _ = oracle.pagerank(off, idx, D, 1e-4, 100)
     g = gpu_graph(n, src, dst, sym)
-    x, st, status = run_gpu(g, 1e-4, 100, contrib=gap.GAP_CONTRIB_BF16, bf16_until_log2_delta=-10)
+    sb = seg_bytes_for(n) if seg else 0
+    x, st, status = run_gpu(g, 1e-4, 100, contrib=gap.GAP_CONTRIB_BF16, bf16_until_log2_delta=-10,
+                            segment_bytes=sb)
     assert status == gap.GAP_OK
     assert st["bf16_iters"] >= 1
     assert st["bf16_iters"] < st["iterations"]
@@ -151,7 +172,7 @@ def test_bf16_contributions_ladder(cuda_device):
     print(f"bf16 ladder: iters {st['iterations']} (bf16 {st['bf16_iters']}), L1 vs FP64 oracle {l1:.3e}")
     assert l1 < 1e-3
     # BF16 throughout: error is reported, not bounded by the FP32 bar
-    x2, st2, _ = run_gpu(g, 1e-4, 100, contrib=gap.GAP_CONTRIB_BF16)
+    x2, st2, _ = run_gpu(g, 1e-4, 100, contrib=gap.GAP_CONTRIB_BF16, segment_bytes=sb)
     assert st2["bf16_iters"] == st2["iterations"]
     print(f"bf16 always: L1 vs FP64 oracle {np.abs(x2 - xo).sum():.3e}")
     g.close()
@@ -185,6 +206,9 @@ def test_kron22_full_config(cuda_device):
     xo, ko, do = oracle.pagerank(off, idx, D, 0.0, 20)
     x, st, _ = run_gpu(g, 0.0, 20)
     l1, rel = assert_fp32_parity(x, xo)
+    xs, sts, _ = run_gpu(g, 0.0, 20, segment_bytes=1 << 20)  # 16 source segments
+    assert sts["segments"] == 16
+    assert_fp32_parity(xs, xo)
     x64, _, _ = run_gpu(g, 0.0, 20, f64=True)
     assert np.abs(x64 - xo).sum() <= FP64_L1
     xt, stt, _ = run_gpu(g, 1e-4, 100)
