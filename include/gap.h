@@ -162,6 +162,9 @@ typedef struct {
                              this, rows above 64 in-edges are pulled one source segment
                              of about this many bytes at a time (0 = library default,
                              tuned per GPU; < 0 disables) */
+  int64_t small_max_degree; /* rows with at most this many in-edges are pulled in vertex
+                               order by the warp-merge kernel (0 = default 64; at most
+                               512) */
 } gap_pr_options;
 
 /* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on

@@ -46,6 +46,7 @@ constexpr int NBINS = GAP_PR_BINS;
 enum { BIN_ZERO = 0, BIN_1, BIN_2, BIN_3, BIN_4, BIN_5, BIN_HUB };
 constexpr int LANES_CTA = 256;
 constexpr int LANES_HUB = 0;
+constexpr int LANES_SMALL = -1;  // vertex-order warp-merge kernel (k_pull_small)
 
 struct BinSpec {
   int64_t hi;   // inclusive upper in-degree
@@ -302,6 +303,88 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_short(PrArgs<Acc> a) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
       if (v[r] >= 0) dl += update_row(a, v[r], s[r], st.cout, st.wb);
+  }
+  write_partial(dl, a.partial);
+}
+
+
+// ---- rows with small in-degree, in vertex order ("warp merge") --------------
+// A warp takes 32 consecutive vertices.  Rows with in-degree <= small_max are
+// owned here (larger rows are skipped; their bins handle them).  The owned
+// rows' arcs form one virtual range of `total` arcs; the warp walks it 32 arcs
+// at a time (UB batches in flight), finds each arc's row by a shuffle binary
+// search over the exclusive degree prefix, gathers, and adds each row's run
+// with a segmented warp scan.  Row sums thus have a fixed order, and offsets,
+// x, out-degrees and c' are read and written fully coalesced.
+template <class Acc, int UB>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_small(PrArgs<Acc> a, int64_t n, int64_t small_max) {
+  const IterState st = iter_state(a);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const int zero_fill = a.ctrl->zero_fill_until;
+  double dl = 0.0;
+  for (int64_t v0 = warp_id * 32; v0 < n; v0 += nwarps * 32) {
+    const int64_t v = v0 + lane;
+    const bool valid = v < n;
+    const int64_t rb = valid ? __ldcs(a.off + v) : 0;
+    const int64_t re = valid ? __ldcs(a.off + v + 1) : 0;
+    const int64_t deg = re - rb;
+    const bool mine = valid && deg <= small_max;
+    const int d = mine ? (int)deg : 0;
+    int incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int excl = incl - d;
+    const int total = __shfl_sync(FULL, incl, 31);
+    Acc acc = Acc(0);
+    for (int base = 0; base < total; base += 32 * UB) {
+      int r[UB];
+      Acc val[UB];
+#pragma unroll
+      for (int q = 0; q < UB; ++q) {
+        const int j = base + q * 32 + lane;
+        int rr = 0;  // largest row with excl <= j
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = rr + step;
+          const int ex = __shfl_sync(FULL, excl, cand & 31);
+          if (cand < 32 && ex <= j) rr = cand;
+        }
+        r[q] = rr;
+        const int64_t rbr = __shfl_sync(FULL, rb, rr);
+        const int exr = __shfl_sync(FULL, excl, rr);
+        const bool act = j < total;
+        const int32_t u = act ? ld_idx(a.idx + rbr + (j - exr)) : 0;
+        if constexpr (std::is_same<Acc, double>::value) {
+          val[q] = act ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u) : 0.0;
+        } else {
+          val[q] = act ? (st.rb ? ld_c_f(reinterpret_cast<const __nv_bfloat16*>(st.cin), u)
+                                : ld_c_f(reinterpret_cast<const float*>(st.cin), u))
+                       : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < UB; ++q) {
+        Acc x = val[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {  // segmented inclusive scan keyed by row
+          const Acc t = __shfl_up_sync(FULL, x, o);
+          const int ro = __shfl_up_sync(FULL, r[q], o);
+          if (lane >= o && ro == r[q]) x = add_rn(x, t);
+        }
+        const int lo = base + q * 32;
+        const bool inter = d > 0 && excl < lo + 32 && incl > lo;
+        const int tl = (incl < lo + 32 ? incl : lo + 32) - 1 - lo;
+        const Acc part = __shfl_sync(FULL, x, inter ? tl : lane);
+        if (inter) acc = add_rn(acc, part);
+      }
+    }
+    if (mine && (d > 0 || st.it < zero_fill)) dl += update_row(a, v, acc, st.cout, st.wb);
   }
   write_partial(dl, a.partial);
 }
@@ -712,6 +795,8 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
 constexpr int64_t DEFAULT_SEGMENT_BYTES = 40ll << 20;  // GB300: ~126 MB of L2 over two dies
 constexpr int64_t HUB_CHUNK = 32768;
 constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
+constexpr int64_t SMALL_MAX = 64;  // rows up to this in-degree go to k_pull_small
+constexpr int SMALL_UB = 4;        // 32-arc batches in flight per warp
 
 static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_bytes) {
   Tuning t;
@@ -730,12 +815,14 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
     t.seg_width = (n + t.segments - 1) / t.segments;
   }
   const bool seg = t.segments > 1;
-  t.bin[BIN_ZERO] = {0, 1, 0};
-  t.bin[BIN_1] = {4, 1, 0};
-  t.bin[BIN_2] = {16, 4, 0};
-  t.bin[BIN_3] = {64, 8, 0};
+  // rows with in-degree <= small (bins 1-3 stay empty): one vertex-order kernel
+  const int64_t small = o.small_max_degree > 0 ? (o.small_max_degree < 512 ? o.small_max_degree : 512) : SMALL_MAX;
+  t.bin[BIN_ZERO] = {small, LANES_SMALL, 0};
+  t.bin[BIN_1] = {small, 1, 0};
+  t.bin[BIN_2] = {small, 4, 0};
+  t.bin[BIN_3] = {small, 8, 0};
   if (seg) {
-    t.bin[BIN_4] = {512, 8, 1};
+    t.bin[BIN_4] = {small > 512 ? small : 512, 8, 1};
     t.bin[BIN_5] = {32768, 32, 1};
   } else {
     t.bin[BIN_4] = {2048, 32, 0};
@@ -795,7 +882,7 @@ struct PhaseTimer {
   }
 };
 
-enum LaunchKind { L_ZERO, L_SHORT, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
+enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -912,7 +999,10 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     r.bin = q;
     r.lanes = t.bin[q].lanes;
     r.poff2 = -1;
-    if (q == BIN_ZERO && !o.deterministic) {
+    if (r.lanes == LANES_SMALL) {
+      r.kind = L_SMALL;
+      r.grid = stride_grid(n, PR_THREADS, 8);
+    } else if (q == BIN_ZERO && !o.deterministic) {
       r.kind = L_ZERO;
       r.grid = stride_grid(rows, PR_THREADS, 8);
     } else if (q == BIN_1 && !o.deterministic) {
@@ -998,6 +1088,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       int tk = tm.begin();
       switch (r.kind) {
         case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
+        case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
         case L_SHORT: k_pull_short<Acc, SHORT_RPT, 4><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_CTA: k_pull_cta<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_GROUP:
@@ -1166,6 +1257,7 @@ void gap_pr_options_default(gap_pr_options* o) {
   o->loop = GAP_LOOP_GRAPH;
   o->timing = 0;
   o->segment_bytes = 0;
+  o->small_max_degree = 0;
 }
 
 gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters, const gap_pr_options* opt,

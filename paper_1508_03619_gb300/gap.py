@@ -55,7 +55,8 @@ class gap_pr_options(ctypes.Structure):
                 ("bf16_until_log2_delta", ctypes.c_int32), ("kahan_hubs", ctypes.c_uint32),
                 ("hub_threshold", ctypes.c_int64), ("deterministic", ctypes.c_uint32),
                 ("l2_window", ctypes.c_uint32), ("loop", ctypes.c_uint32),
-                ("timing", ctypes.c_uint32), ("segment_bytes", ctypes.c_int64)]
+                ("timing", ctypes.c_uint32), ("segment_bytes", ctypes.c_int64),
+                ("small_max_degree", ctypes.c_int64)]
 
 
 class gap_pr_stats_t(ctypes.Structure):
