@@ -240,18 +240,42 @@ def gap_pr_options_default() -> gap_pr_options:
     return o
 
 
+def _check_scores(h, scores, itemsize: int, where: str):
+    """The C ABI cannot see buffer sizes: for tensors and arrays, check here that
+    the output holds n elements of the run's precision (raw integer addresses
+    are passed through unchecked)."""
+    if scores is None or isinstance(scores, int):
+        return
+    n = gap_graph_info(h)[0]
+    if hasattr(scores, "element_size"):
+        size, numel = scores.element_size(), scores.numel()
+        floating = scores.is_floating_point()
+    elif hasattr(scores, "itemsize"):
+        size, numel = scores.itemsize, scores.size
+        floating = scores.dtype.kind == "f"
+    else:
+        return
+    if not floating or size != itemsize:
+        raise ValueError(f"{where}: scores must be float{8 * itemsize}")
+    if numel < n:
+        raise ValueError(f"{where}: scores holds {numel} elements, the graph has {n} vertices")
+
+
 def gap_pr_run(h, damping: float, tol: float, max_iters: int, scores, stream=None):
+    _check_scores(h, scores, 4, "gap_pr_run")
     return _check(load().gap_pr_run(h, damping, tol, max_iters, _ptr(scores), _stream(stream)),
                   "gap_pr_run")
 
 
 def gap_pr_run_f64(h, damping: float, tol: float, max_iters: int, scores, stream=None):
+    _check_scores(h, scores, 8, "gap_pr_run_f64")
     return _check(load().gap_pr_run_f64(h, damping, tol, max_iters, _ptr(scores), _stream(stream)),
                   "gap_pr_run_f64")
 
 
 def gap_pr_run_ex(h, damping: float, tol: float, max_iters: int, options: gap_pr_options, scores,
                   stream=None):
+    _check_scores(h, scores, 8 if options.precision == GAP_PREC_F64 else 4, "gap_pr_run_ex")
     return _check(load().gap_pr_run_ex(h, damping, tol, max_iters, ctypes.byref(options),
                                        _ptr(scores), _stream(stream)), "gap_pr_run_ex")
 

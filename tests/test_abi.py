@@ -93,3 +93,23 @@ def test_run_rejects_null_graph():
 def test_allocator_hook_validation():
     lib = gap.load()
     assert lib.gap_set_allocator(None) == gap.GAP_OK
+
+
+def test_binding_rejects_wrong_score_buffers():
+    """The binding checks tensor/array dtype and length against the graph before
+    any device work (a float32 buffer for an FP64 run would be overrun)."""
+    class FakeHandle:
+        pass
+    import paper_1508_03619_gb300.gap as g
+    orig = g.gap_graph_info
+    g.gap_graph_info = lambda h: (100, 0, 0)
+    try:
+        with pytest.raises(ValueError, match="float64"):
+            g._check_scores(FakeHandle(), np.zeros(100, np.float32), 8, "run")
+        with pytest.raises(ValueError, match="100 vertices"):
+            g._check_scores(FakeHandle(), np.zeros(99, np.float32), 4, "run")
+        with pytest.raises(ValueError, match="float32"):
+            g._check_scores(FakeHandle(), np.zeros(100, np.int32), 4, "run")
+        g._check_scores(FakeHandle(), np.zeros(100, np.float32), 4, "run")
+    finally:
+        g.gap_graph_info = orig
