@@ -164,7 +164,7 @@ typedef struct {
                              tuned per GPU; < 0 disables) */
   int64_t small_max_degree; /* rows with at most this many in-edges are pulled in vertex
                                order by the warp-merge kernel (0 = default 64; at most
-                               512) */
+                               512, and 255 when L2 blocking is active) */
 } gap_pr_options;
 
 /* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on

@@ -389,6 +389,158 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small(PrArgs<Acc> a, int64_
   write_partial(dl, a.partial);
 }
 
+
+// ---- small rows, L2-blocked: segment-major packed arcs ------------------------
+// Per trial the small rows' arcs are copied once into a segment-major array
+// (a timed conversion, as paper §2.3 requires): for segment s, the arcs of
+// tile t (32 consecutive vertices) start at toff[s*T + t], row by row, and
+// cnt8[s*n + v] holds row v's arc count in segment s (<= 255).  A segment
+// pass then streams its arcs contiguously and gathers only from that
+// segment's contributions, which stay in L2.
+
+// cnt8[s][v] and per-tile totals; rows above small_max count zero.
+__global__ void __launch_bounds__(PR_THREADS) k_small_count(const int64_t* __restrict__ off,
+                                                             const int32_t* __restrict__ idx, int64_t n,
+                                                             int64_t small_max, int S, int64_t W,
+                                                             uint8_t* __restrict__ cnt8, uint32_t* __restrict__ ttot,
+                                                             int64_t T) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nr = (n + 31) & ~int64_t(31);
+  for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < nr; v += (int64_t)gridDim.x * PR_THREADS) {
+    const bool valid = v < n;
+    const int64_t rb = valid ? off[v] : 0, re = valid ? off[v + 1] : 0;
+    const bool small = valid && re - rb <= small_max;
+    int64_t j = rb;
+    for (int sg = 0; sg < S; ++sg) {
+      const int64_t hi = (int64_t)(sg + 1) * W;
+      int k = 0;
+      if (small)
+        while (j < re && (int64_t)idx[j] < hi) {
+          ++k;
+          ++j;
+        }
+      if (valid) cnt8[(int64_t)sg * n + v] = (uint8_t)k;
+      const int tot = warp_sum(k);
+      if (lane == 0) ttot[(int64_t)sg * T + (v >> 5)] = (uint32_t)tot;
+    }
+  }
+}
+
+// Copy each small row's arcs to its segment-major positions.
+__global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __restrict__ off,
+                                                            const int32_t* __restrict__ idx, int64_t n,
+                                                            int64_t small_max, int S, const uint8_t* __restrict__ cnt8,
+                                                            const int64_t* __restrict__ toff, int64_t T,
+                                                            int32_t* __restrict__ packed) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nr = (n + 31) & ~int64_t(31);
+  for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < nr; v += (int64_t)gridDim.x * PR_THREADS) {
+    const bool valid = v < n;
+    const int64_t rb = valid ? off[v] : 0, re = valid ? off[v + 1] : 0;
+    const bool small = valid && re - rb <= small_max;
+    int64_t j = rb;
+    for (int sg = 0; sg < S; ++sg) {
+      const int k = valid ? cnt8[(int64_t)sg * n + v] : 0;
+      int incl = k;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (small) {
+        const int64_t pos = toff[(int64_t)sg * T + (v >> 5)] + (incl - k);
+        for (int q = 0; q < k; ++q) packed[pos + q] = idx[j + q];
+        j += k;
+      }
+    }
+  }
+}
+
+// Segment pass s over the small rows: arcs of the tile come from the packed
+// array; the running row sum pp[v] is added segment by segment and the last
+// pass applies the update.
+template <class Acc, int UB>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_small_seg(PrArgs<Acc> a, int64_t n, int64_t small_max, int s,
+                                                                int S, const uint8_t* __restrict__ cnt8,
+                                                                const int64_t* __restrict__ toff, int64_t T,
+                                                                const int32_t* __restrict__ packed,
+                                                                Acc* __restrict__ pp) {
+  const IterState st = iter_state(a);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const bool last = s + 1 == S;
+  const int zero_fill = a.ctrl->zero_fill_until;
+  double dl = 0.0;
+  for (int64_t tile = warp_id; tile < T; tile += nwarps) {
+    const int64_t v = tile * 32 + lane;
+    const bool valid = v < n;
+    const int d = valid ? __ldcs(cnt8 + (int64_t)s * n + v) : 0;
+    int incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int excl = incl - d;
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int32_t* arcs = packed + __ldcs(toff + (int64_t)s * T + tile);
+    Acc acc = Acc(0);
+    for (int base = 0; base < total; base += 32 * UB) {
+      int r[UB];
+      Acc val[UB];
+#pragma unroll
+      for (int q = 0; q < UB; ++q) {
+        const int j = base + q * 32 + lane;
+        int rr = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = rr + step;
+          const int ex = __shfl_sync(FULL, excl, cand & 31);
+          if (cand < 32 && ex <= j) rr = cand;
+        }
+        r[q] = rr;
+        const bool act = j < total;
+        const int32_t u = act ? ld_idx(arcs + j) : 0;
+        if constexpr (std::is_same<Acc, double>::value) {
+          val[q] = act ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u) : 0.0;
+        } else {
+          val[q] = act ? (st.rb ? ld_c_f(reinterpret_cast<const __nv_bfloat16*>(st.cin), u)
+                                : ld_c_f(reinterpret_cast<const float*>(st.cin), u))
+                       : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < UB; ++q) {
+        Acc x = val[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const Acc t = __shfl_up_sync(FULL, x, o);
+          const int ro = __shfl_up_sync(FULL, r[q], o);
+          if (lane >= o && ro == r[q]) x = add_rn(x, t);
+        }
+        const int lo = base + q * 32;
+        const bool inter = d > 0 && excl < lo + 32 && incl > lo;
+        const int tl = (incl < lo + 32 ? incl : lo + 32) - 1 - lo;
+        const Acc part = __shfl_sync(FULL, x, inter ? tl : lane);
+        if (inter) acc = add_rn(acc, part);
+      }
+    }
+    if (!valid) continue;
+    if (!last) {
+      __stcs(pp + v, s ? add_rn(__ldcs(pp + v), acc) : acc);
+    } else {
+      const int64_t deg = __ldcs(a.off + v + 1) - __ldcs(a.off + v);
+      if (deg <= small_max && (deg > 0 || st.it < zero_fill)) {
+        const Acc sum = S > 1 ? add_rn(__ldcs(pp + v), acc) : acc;
+        dl += update_row(a, v, sum, st.cout, st.wb);
+      }
+    }
+  }
+  if (last) write_partial(dl, a.partial);
+}
+
 // ---- group-per-row kernels (G lanes per row) --------------------------------
 template <int G, class Acc>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_group(PrArgs<Acc> a) {
@@ -816,7 +968,8 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
   }
   const bool seg = t.segments > 1;
   // rows with in-degree <= small (bins 1-3 stay empty): one vertex-order kernel
-  const int64_t small = o.small_max_degree > 0 ? (o.small_max_degree < 512 ? o.small_max_degree : 512) : SMALL_MAX;
+  int64_t small = o.small_max_degree > 0 ? (o.small_max_degree < 512 ? o.small_max_degree : 512) : SMALL_MAX;
+  if (seg && small > 255) small = 255;  // packed per-segment counts are bytes
   t.bin[BIN_ZERO] = {small, LANES_SMALL, 0};
   t.bin[BIN_1] = {small, 1, 0};
   t.bin[BIN_2] = {small, 4, 0};
@@ -882,7 +1035,7 @@ struct PhaseTimer {
   }
 };
 
-enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
+enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_SMALL_SEG, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -909,6 +1062,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   // ---- scratch (inside the trial, §2.3) ----
   Scratch xs, cbuf, list, ctrl, cnt, offs, tmp, cstart, csum, partial, meta;
   Scratch seg_rs, seg_bnd, seg_pp, seg_cstart, seg_meta;
+  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_pp;
   Acc* x = user_scores;
   if (!user_dev) {
     GAP_TRY(xs.get(xbytes, s));
@@ -984,6 +1138,31 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       for (int k = 0; k < S; ++k) nchunks = seg_chunks[k] > nchunks ? seg_chunks[k] : nchunks;
     }
   }
+  // small rows, L2-blocked: segment-major packed arcs (timed conversion)
+  const bool small_packed = S > 1 && t.bin[BIN_ZERO].lanes == LANES_SMALL && mt[BIN_4] > 0;
+  const int64_t T = (n + 31) / 32;
+  if (small_packed) {
+    GAP_TRY(sm_cnt.get((size_t)S * n, s));
+    GAP_TRY(sm_ttot.get(sizeof(uint32_t) * S * T, s));
+    GAP_TRY(sm_toff.get(sizeof(int64_t) * S * T, s));
+    GAP_TRY(sm_tmp.get(sizeof(int64_t) * scan_tmp_elems(S * T), s));
+    GAP_TRY(sm_total.get(sizeof(int64_t), s));
+    GAP_TRY(sm_pp.get(sizeof(Acc) * n, s));
+    k_small_count<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
+                                                                         t.seg_width, sm_cnt.as<uint8_t>(),
+                                                                         sm_ttot.as<uint32_t>(), T);
+    GAP_LAUNCH_CHECK();
+    GAP_TRY(exclusive_scan_u32(sm_ttot.as<uint32_t>(), sm_toff.as<int64_t>(), S * T, sm_tmp.as<int64_t>(),
+                               sm_total.as<int64_t>(), s));
+    int64_t small_arcs = 0;
+    GAP_CUDA(cudaMemcpyAsync(&small_arcs, sm_total.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GAP_CUDA(cudaStreamSynchronize(s));
+    GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
+    k_small_pack<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
+                                                                        sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
+                                                                        sm_packed.as<int32_t>());
+    GAP_LAUNCH_CHECK();
+  }
   tm.end(GAP_PHASE_BIN, tok);
   tm.collect();
 
@@ -999,7 +1178,9 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     r.bin = q;
     r.lanes = t.bin[q].lanes;
     r.poff2 = -1;
-    if (r.lanes == LANES_SMALL) {
+    if (r.lanes == LANES_SMALL && small_packed) {
+      continue;  // runs inside the segment passes
+    } else if (r.lanes == LANES_SMALL) {
       r.kind = L_SMALL;
       r.grid = stride_grid(n, PR_THREADS, 8);
     } else if (q == BIN_ZERO && !o.deterministic) {
@@ -1024,6 +1205,21 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     plan.push_back(r);
   }
   for (int sgi = 0; sgi < S && S > 1; ++sgi) {  // segment passes
+    if (small_packed) {
+      LaunchRec r{};
+      r.kind = L_SMALL_SEG;
+      r.bin = BIN_ZERO;
+      r.lanes = LANES_SMALL;
+      r.s = sgi;
+      r.grid = stride_grid(n, PR_THREADS, 8);
+      r.poff = -1;
+      r.poff2 = -1;
+      if (sgi + 1 == S) {
+        r.poff = np;
+        np += r.grid;
+      }
+      plan.push_back(r);
+    }
     for (int q = 0; q < NBINS; ++q) {
       const int64_t rows = rows_of(q);
       if (rows == 0 || !t.bin[q].seg) continue;
@@ -1089,6 +1285,11 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       switch (r.kind) {
         case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
+        case L_SMALL_SEG:
+          k_pull_small_seg<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(
+              b, n, t.bin[BIN_ZERO].hi, r.s, S, sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
+              sm_packed.as<int32_t>(), sm_pp.as<Acc>());
+          break;
         case L_SHORT: k_pull_short<Acc, SHORT_RPT, 4><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_CTA: k_pull_cta<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_GROUP:
@@ -1213,7 +1414,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   for (const LaunchRec& r : plan) per_iter += (r.kind == L_HUB || r.kind == L_HUB_SEG) ? (r.grid > 0 ? 2 : 1) : 1;
   g->launches_per_iter = per_iter;
   g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/ + (S > 1 && seg_rows > 0 ? 1 : 0) +
-                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0);
+                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 5 : 0);
   g->last_segments = S;
   for (int q = 0; q < NBINS; ++q) {
     g->last_bin_hi[q] = t.bin[q].hi;
