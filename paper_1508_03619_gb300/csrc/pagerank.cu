@@ -426,12 +426,19 @@ __global__ void __launch_bounds__(PR_THREADS) k_small_count(const int64_t* __res
   }
 }
 
-// Copy each small row's arcs to its segment-major positions.
+// End of each segment in the packed arrays.
+__global__ void k_seg_ends(const int64_t* __restrict__ toff, int64_t T, int S, const int64_t* __restrict__ total,
+                           int64_t* __restrict__ tend) {
+  for (int sg = threadIdx.x; sg < S; sg += blockDim.x) tend[sg] = sg + 1 < S ? toff[(int64_t)(sg + 1) * T] : *total;
+}
+
+// Copy each small row's arcs to its segment-major positions, with the row id
+// of every arc beside it (COO order: rows ascending within a segment).
 __global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ idx, int64_t n,
                                                             int64_t small_max, int S, const uint8_t* __restrict__ cnt8,
                                                             const int64_t* __restrict__ toff, int64_t T,
-                                                            int32_t* __restrict__ packed) {
+                                                            int32_t* __restrict__ packed, int32_t* __restrict__ prow) {
   const int lane = threadIdx.x & 31;
   const int64_t nr = (n + 31) & ~int64_t(31);
   for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < nr; v += (int64_t)gridDim.x * PR_THREADS) {
@@ -449,60 +456,52 @@ __global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __rest
       }
       if (small) {
         const int64_t pos = toff[(int64_t)sg * T + (v >> 5)] + (incl - k);
-        for (int q = 0; q < k; ++q) packed[pos + q] = idx[j + q];
+        for (int q = 0; q < k; ++q) {
+          packed[pos + q] = idx[j + q];
+          prow[pos + q] = (int32_t)v;
+        }
         j += k;
       }
     }
   }
 }
 
-// Segment pass s over the small rows: arcs of the tile come from the packed
-// array; the running row sum pp[v] is added segment by segment and the last
-// pass applies the update.
-template <class Acc, int UB>
-__global__ void __launch_bounds__(PR_THREADS) k_pull_small_seg(PrArgs<Acc> a, int64_t n, int64_t small_max, int s,
-                                                                int S, const uint8_t* __restrict__ cnt8,
+// Segment pass s over the small rows, COO style: a warp streams chunks of
+// TPC tiles (rows never straddle a chunk), UB batches of 32 arcs in flight,
+// and reduces each row's run with a segmented warp scan; a run that reaches
+// the batch end is carried into the next batch in order, so each row's
+// segment sum has a fixed order.  Completed sums are added to pp[row].
+// tend[s] is the end of segment s in the packed arrays.
+template <class Acc, int UB, int TPC>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, int s,
                                                                 const int64_t* __restrict__ toff, int64_t T,
+                                                                const int64_t* __restrict__ tend,
                                                                 const int32_t* __restrict__ packed,
+                                                                const int32_t* __restrict__ prow,
                                                                 Acc* __restrict__ pp) {
   const IterState st = iter_state(a);
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   const unsigned FULL = 0xffffffffu;
-  const bool last = s + 1 == S;
-  const int zero_fill = a.ctrl->zero_fill_until;
-  double dl = 0.0;
-  for (int64_t tile = warp_id; tile < T; tile += nwarps) {
-    const int64_t v = tile * 32 + lane;
-    const bool valid = v < n;
-    const int d = valid ? __ldcs(cnt8 + (int64_t)s * n + v) : 0;
-    int incl = d;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int excl = incl - d;
-    const int total = __shfl_sync(FULL, incl, 31);
-    const int32_t* arcs = packed + __ldcs(toff + (int64_t)s * T + tile);
-    Acc acc = Acc(0);
-    for (int base = 0; base < total; base += 32 * UB) {
+  const int64_t nchunks = (T + TPC - 1) / TPC;
+  const int64_t* tof = toff + (int64_t)s * T;
+  const int64_t send = tend[s];
+  for (int64_t ch = warp_id; ch < nchunks; ch += nwarps) {
+    const int64_t t0 = ch * TPC, t1 = t0 + TPC;
+    const int64_t a0 = tof[t0];
+    const int64_t a1 = t1 < T ? tof[t1] : send;
+    int carry_r = -1;
+    Acc carry_v = Acc(0);
+    for (int64_t base = a0; base < a1; base += 32 * UB) {
       int r[UB];
       Acc val[UB];
 #pragma unroll
       for (int q = 0; q < UB; ++q) {
-        const int j = base + q * 32 + lane;
-        int rr = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int cand = rr + step;
-          const int ex = __shfl_sync(FULL, excl, cand & 31);
-          if (cand < 32 && ex <= j) rr = cand;
-        }
-        r[q] = rr;
-        const bool act = j < total;
-        const int32_t u = act ? ld_idx(arcs + j) : 0;
+        const int64_t j = base + q * 32 + lane;
+        const bool act = j < a1;
+        r[q] = act ? __ldcs(prow + j) : -2 - lane;  // inactive lanes: unique keys
+        const int32_t u = act ? ld_idx(packed + j) : 0;
         if constexpr (std::is_same<Acc, double>::value) {
           val[q] = act ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u) : 0.0;
         } else {
@@ -513,32 +512,51 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_seg(PrArgs<Acc> a, in
       }
 #pragma unroll
       for (int q = 0; q < UB; ++q) {
+        const int64_t bq = base + q * 32;
+        if (bq >= a1) break;  // warp-uniform
+        const int lastl = a1 - bq >= 32 ? 31 : (int)(a1 - bq - 1);
         Acc x = val[q];
+        if (lane == 0 && carry_r >= 0) {
+          if (r[q] == carry_r)
+            x = add_rn(carry_v, x);  // the carried run continues: its earlier arcs first
+          else
+            pp[carry_r] = add_rn(pp[carry_r], carry_v);  // it ended at the previous batch's end
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const Acc t = __shfl_up_sync(FULL, x, o);
           const int ro = __shfl_up_sync(FULL, r[q], o);
           if (lane >= o && ro == r[q]) x = add_rn(x, t);
         }
-        const int lo = base + q * 32;
-        const bool inter = d > 0 && excl < lo + 32 && incl > lo;
-        const int tl = (incl < lo + 32 ? incl : lo + 32) - 1 - lo;
-        const Acc part = __shfl_sync(FULL, x, inter ? tl : lane);
-        if (inter) acc = add_rn(acc, part);
-      }
-    }
-    if (!valid) continue;
-    if (!last) {
-      __stcs(pp + v, s ? add_rn(__ldcs(pp + v), acc) : acc);
-    } else {
-      const int64_t deg = __ldcs(a.off + v + 1) - __ldcs(a.off + v);
-      if (deg <= small_max && (deg > 0 || st.it < zero_fill)) {
-        const Acc sum = S > 1 ? add_rn(__ldcs(pp + v), acc) : acc;
-        dl += update_row(a, v, sum, st.cout, st.wb);
+        const int rn = __shfl_down_sync(FULL, r[q], 1);
+        const bool batch_end = bq + 32 >= a1;  // no later batch in this chunk
+        const bool run_end = lane < lastl ? rn != r[q] : (lane == lastl && batch_end);
+        if (run_end) pp[r[q]] = add_rn(pp[r[q]], x);
+        carry_r = __shfl_sync(FULL, r[q], lastl);
+        carry_v = __shfl_sync(FULL, x, lastl);
+        if (batch_end) carry_r = -1;
       }
     }
   }
-  if (last) write_partial(dl, a.partial);
+}
+
+// Per iteration, after all segment passes: the small rows' updates in vertex
+// order (coalesced), and pp reset to zero for the next iteration.
+template <class Acc>
+__global__ void __launch_bounds__(PR_THREADS) k_small_update(PrArgs<Acc> a, int64_t n, int64_t small_max,
+                                                              Acc* __restrict__ pp) {
+  const IterState st = iter_state(a);
+  const int zero_fill = a.ctrl->zero_fill_until;
+  double dl = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < n; v += (int64_t)gridDim.x * PR_THREADS) {
+    const int64_t deg = __ldcs(a.off + v + 1) - __ldcs(a.off + v);
+    if (deg > small_max) continue;
+    if (deg == 0 && st.it >= zero_fill) continue;
+    const Acc sum = deg > 0 ? __ldcs(pp + v) : Acc(0);
+    if (deg > 0) __stcs(pp + v, Acc(0));
+    dl += update_row(a, v, sum, st.cout, st.wb);
+  }
+  write_partial(dl, a.partial);
 }
 
 // ---- group-per-row kernels (G lanes per row) --------------------------------
@@ -949,6 +967,7 @@ constexpr int64_t HUB_CHUNK = 32768;
 constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
 constexpr int64_t SMALL_MAX = 64;  // rows up to this in-degree go to k_pull_small
 constexpr int SMALL_UB = 4;        // 32-arc batches in flight per warp
+constexpr int SMALL_TPC = 16;      // 32-vertex tiles per COO chunk
 
 static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_bytes) {
   Tuning t;
@@ -1035,7 +1054,7 @@ struct PhaseTimer {
   }
 };
 
-enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_SMALL_SEG, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
+enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_SMALL_SEG, L_SMALL_UPD, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -1062,7 +1081,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   // ---- scratch (inside the trial, §2.3) ----
   Scratch xs, cbuf, list, ctrl, cnt, offs, tmp, cstart, csum, partial, meta;
   Scratch seg_rs, seg_bnd, seg_pp, seg_cstart, seg_meta;
-  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_pp;
+  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_prow, sm_pp, sm_tend;
   Acc* x = user_scores;
   if (!user_dev) {
     GAP_TRY(xs.get(xbytes, s));
@@ -1158,9 +1177,14 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_CUDA(cudaMemcpyAsync(&small_arcs, sm_total.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GAP_CUDA(cudaStreamSynchronize(s));
     GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
+    GAP_TRY(sm_prow.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
+    GAP_TRY(sm_tend.get(sizeof(int64_t) * S, s));
+    GAP_CUDA(cudaMemsetAsync(sm_pp.p, 0, sizeof(Acc) * n, s));
     k_small_pack<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
                                                                         sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
-                                                                        sm_packed.as<int32_t>());
+                                                                        sm_packed.as<int32_t>(), sm_prow.as<int32_t>());
+    GAP_LAUNCH_CHECK();
+    k_seg_ends<<<1, 64, 0, s>>>(sm_toff.as<int64_t>(), T, S, sm_total.as<int64_t>(), sm_tend.as<int64_t>());
     GAP_LAUNCH_CHECK();
   }
   tm.end(GAP_PHASE_BIN, tok);
@@ -1211,13 +1235,9 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       r.bin = BIN_ZERO;
       r.lanes = LANES_SMALL;
       r.s = sgi;
-      r.grid = stride_grid(n, PR_THREADS, 8);
+      r.grid = stride_grid((T + SMALL_TPC - 1) / SMALL_TPC * 32, PR_THREADS, 8);
       r.poff = -1;
       r.poff2 = -1;
-      if (sgi + 1 == S) {
-        r.poff = np;
-        np += r.grid;
-      }
       plan.push_back(r);
     }
     for (int q = 0; q < NBINS; ++q) {
@@ -1247,6 +1267,17 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       }
       plan.push_back(r);
     }
+  }
+  if (small_packed) {  // the small rows' update after the last segment pass
+    LaunchRec r{};
+    r.kind = L_SMALL_UPD;
+    r.bin = BIN_ZERO;
+    r.lanes = LANES_SMALL;
+    r.grid = stride_grid(n, PR_THREADS, 8);
+    r.poff = np;
+    r.poff2 = -1;
+    np += r.grid;
+    plan.push_back(r);
   }
   GAP_TRY(partial.get(sizeof(double) * (np > 0 ? np : 1), s));
   if (np == 0) GAP_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double), s));
@@ -1286,9 +1317,12 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
         case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
         case L_SMALL_SEG:
-          k_pull_small_seg<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(
-              b, n, t.bin[BIN_ZERO].hi, r.s, S, sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
-              sm_packed.as<int32_t>(), sm_pp.as<Acc>());
+          k_pull_small_coo<Acc, SMALL_UB, SMALL_TPC><<<r.grid, PR_THREADS, 0, ls>>>(
+              b, r.s, sm_toff.as<int64_t>(), T, sm_tend.as<int64_t>(), sm_packed.as<int32_t>(),
+              sm_prow.as<int32_t>(), sm_pp.as<Acc>());
+          break;
+        case L_SMALL_UPD:
+          k_small_update<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[BIN_ZERO].hi, sm_pp.as<Acc>());
           break;
         case L_SHORT: k_pull_short<Acc, SHORT_RPT, 4><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_CTA: k_pull_cta<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
@@ -1414,7 +1448,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   for (const LaunchRec& r : plan) per_iter += (r.kind == L_HUB || r.kind == L_HUB_SEG) ? (r.grid > 0 ? 2 : 1) : 1;
   g->launches_per_iter = per_iter;
   g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/ + (S > 1 && seg_rows > 0 ? 1 : 0) +
-                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 5 : 0);
+                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 7 : 0);
   g->last_segments = S;
   for (int q = 0; q < NBINS; ++q) {
     g->last_bin_hi[q] = t.bin[q].hi;
