@@ -466,16 +466,27 @@ __global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __rest
   }
 }
 
-// Segment pass s over the small rows, COO style: a warp streams chunks of
-// TPC tiles (rows never straddle a chunk), UB batches of 32 arcs in flight,
-// and reduces each row's run with a segmented warp scan; a run that reaches
-// the batch end is carried into the next batch in order, so each row's
-// segment sum has a fixed order.  Completed sums are added to pp[row].
-// tend[s] is the end of segment s in the packed arrays.
-template <class Acc, int UB, int TPC>
+// Segment pass s over the small rows, COO style.  The segment's packed arcs
+// [tof[0], tend[s]) are cut into chunks of about CA arcs whose ends are moved
+// to tile boundaries (a binary search on the tile offsets), so rows never
+// straddle a chunk and every warp streams a similar amount of work.  UB
+// batches of 32 arcs are in flight; each row's run is reduced with a
+// segmented warp scan, and a run that reaches the batch end is carried into
+// the next batch in order, so each row's segment sum has a fixed order.
+// Completed sums are added to pp[row].
+__device__ __forceinline__ int64_t tile_at_or_after(const int64_t* tof, int64_t T, int64_t target) {
+  int64_t lo = 0, hi = T;  // first tile with tof[t] >= target (T if none)
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (tof[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <class Acc, int UB>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, int s,
                                                                 const int64_t* __restrict__ toff, int64_t T,
-                                                                const int64_t* __restrict__ tend,
+                                                                const int64_t* __restrict__ tend, int64_t CA,
                                                                 const int32_t* __restrict__ packed,
                                                                 const int32_t* __restrict__ prow,
                                                                 Acc* __restrict__ pp) {
@@ -484,12 +495,13 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, in
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   const unsigned FULL = 0xffffffffu;
-  const int64_t nchunks = (T + TPC - 1) / TPC;
   const int64_t* tof = toff + (int64_t)s * T;
-  const int64_t send = tend[s];
+  const int64_t sbeg = tof[0], send = tend[s];
+  const int64_t nchunks = (send - sbeg + CA - 1) / CA;
   for (int64_t ch = warp_id; ch < nchunks; ch += nwarps) {
-    const int64_t t0 = ch * TPC, t1 = t0 + TPC;
-    const int64_t a0 = tof[t0];
+    const int64_t t0 = ch == 0 ? 0 : tile_at_or_after(tof, T, sbeg + ch * CA);
+    const int64_t t1 = tile_at_or_after(tof, T, sbeg + (ch + 1) * CA);
+    const int64_t a0 = t0 < T ? tof[t0] : send;
     const int64_t a1 = t1 < T ? tof[t1] : send;
     int carry_r = -1;
     Acc carry_v = Acc(0);
@@ -964,10 +976,12 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
 
 constexpr int64_t DEFAULT_SEGMENT_BYTES = 40ll << 20;  // GB300: ~126 MB of L2 over two dies
 constexpr int64_t HUB_CHUNK = 32768;
+constexpr int64_t HUB_CHUNK_SEG = 4096;
 constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
 constexpr int64_t SMALL_MAX = 64;  // rows up to this in-degree go to k_pull_small
+constexpr int64_t SMALL_MAX_SEG = 255;  // ... and to the packed COO passes when L2-blocked
 constexpr int SMALL_UB = 4;        // 32-arc batches in flight per warp
-constexpr int SMALL_TPC = 16;      // 32-vertex tiles per COO chunk
+constexpr int64_t SMALL_CHUNK_ARCS = 2048;  // arcs per COO chunk (moved to tile boundaries)
 
 static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_bytes) {
   Tuning t;
@@ -987,7 +1001,8 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
   }
   const bool seg = t.segments > 1;
   // rows with in-degree <= small (bins 1-3 stay empty): one vertex-order kernel
-  int64_t small = o.small_max_degree > 0 ? (o.small_max_degree < 512 ? o.small_max_degree : 512) : SMALL_MAX;
+  int64_t small = o.small_max_degree > 0 ? (o.small_max_degree < 512 ? o.small_max_degree : 512)
+                                         : (seg ? SMALL_MAX_SEG : SMALL_MAX);
   if (seg && small > 255) small = 255;  // packed per-segment counts are bytes
   t.bin[BIN_ZERO] = {small, LANES_SMALL, 0};
   t.bin[BIN_1] = {small, 1, 0};
@@ -1004,6 +1019,7 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
       t.bin[BIN_4].hi = o.hub_threshold > t.bin[BIN_3].hi ? o.hub_threshold : t.bin[BIN_3].hi;
   }
   t.bin[BIN_HUB] = {INT64_MAX, LANES_HUB, seg ? 1 : 0};
+  if (seg) t.hub_chunk = HUB_CHUNK_SEG;  // segment sub-rows are S times shorter
   return t;
 }
 
@@ -1160,6 +1176,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   // small rows, L2-blocked: segment-major packed arcs (timed conversion)
   const bool small_packed = S > 1 && t.bin[BIN_ZERO].lanes == LANES_SMALL && mt[BIN_4] > 0;
   const int64_t T = (n + 31) / 32;
+  std::vector<int64_t> seg_small_arcs(S, 0);
   if (small_packed) {
     GAP_TRY(sm_cnt.get((size_t)S * n, s));
     GAP_TRY(sm_ttot.get(sizeof(uint32_t) * S * T, s));
@@ -1186,6 +1203,10 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_LAUNCH_CHECK();
     k_seg_ends<<<1, 64, 0, s>>>(sm_toff.as<int64_t>(), T, S, sm_total.as<int64_t>(), sm_tend.as<int64_t>());
     GAP_LAUNCH_CHECK();
+    std::vector<int64_t> tend_h(S);
+    GAP_CUDA(cudaMemcpyAsync(tend_h.data(), sm_tend.p, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, s));
+    GAP_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < S; ++k) seg_small_arcs[k] = tend_h[k] - (k ? tend_h[k - 1] : 0);
   }
   tm.end(GAP_PHASE_BIN, tok);
   tm.collect();
@@ -1235,7 +1256,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       r.bin = BIN_ZERO;
       r.lanes = LANES_SMALL;
       r.s = sgi;
-      r.grid = stride_grid((T + SMALL_TPC - 1) / SMALL_TPC * 32, PR_THREADS, 8);
+      r.grid = stride_grid(seg_small_arcs[sgi] / SMALL_CHUNK_ARCS * 32 + 32, PR_THREADS, 8);
       r.poff = -1;
       r.poff2 = -1;
       plan.push_back(r);
@@ -1317,8 +1338,8 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
         case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
         case L_SMALL_SEG:
-          k_pull_small_coo<Acc, SMALL_UB, SMALL_TPC><<<r.grid, PR_THREADS, 0, ls>>>(
-              b, r.s, sm_toff.as<int64_t>(), T, sm_tend.as<int64_t>(), sm_packed.as<int32_t>(),
+          k_pull_small_coo<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(
+              b, r.s, sm_toff.as<int64_t>(), T, sm_tend.as<int64_t>(), SMALL_CHUNK_ARCS, sm_packed.as<int32_t>(),
               sm_prow.as<int32_t>(), sm_pp.as<Acc>());
           break;
         case L_SMALL_UPD:
