@@ -466,27 +466,53 @@ __global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __rest
   }
 }
 
-// Segment pass s over the small rows, COO style.  The segment's packed arcs
-// [tof[0], tend[s]) are cut into chunks of about CA arcs whose ends are moved
-// to tile boundaries (a binary search on the tile offsets), so rows never
-// straddle a chunk and every warp streams a similar amount of work.  UB
-// batches of 32 arcs are in flight; each row's run is reduced with a
-// segmented warp scan, and a run that reaches the batch end is carried into
-// the next batch in order, so each row's segment sum has a fixed order.
-// Completed sums are added to pp[row].
-__device__ __forceinline__ int64_t tile_at_or_after(const int64_t* tof, int64_t T, int64_t target) {
-  int64_t lo = 0, hi = T;  // first tile with tof[t] >= target (T if none)
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (tof[mid] < target) lo = mid + 1; else hi = mid;
+// Chunk table of the COO passes: the packed arcs of segment s are cut into
+// chunks of about CA arcs whose ends are moved to tile boundaries, so rows
+// never straddle a chunk.  ctile[cbase[s] + c] is the first tile of chunk c
+// (one extra entry per segment closes the last chunk).
+__global__ void k_coo_chunks(const int64_t* __restrict__ toff, int64_t T, int S, const int64_t* __restrict__ tend,
+                             int64_t CA, const int64_t* __restrict__ cbase, int64_t total_entries,
+                             int64_t* __restrict__ ctile) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total_entries;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int sg = 0;
+    while (sg + 1 < S && cbase[sg + 1] <= e) ++sg;
+    const int64_t c = e - cbase[sg];
+    const int64_t* tof = toff + (int64_t)sg * T;
+    const int64_t sbeg = tof[0], send = tend[sg];
+    const int64_t last = cbase[sg + 1] - cbase[sg] - 1;  // the closing entry
+    int64_t tile;
+    if (c == 0) {
+      tile = 0;
+    } else if (c == last) {
+      tile = T;
+    } else {
+      const int64_t target = sbeg + c * CA;
+      int64_t lo = 0, hi = T;  // first tile with tof >= target
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tof[mid] < target) lo = mid + 1; else hi = mid;
+      }
+      tile = lo;
+    }
+    (void)send;
+    ctile[e] = tile;
   }
-  return lo;
 }
 
-template <class Acc, int UB>
+// Segment pass s over the small rows, COO style.  Each warp streams chunks;
+// each lane takes K consecutive arcs of a batch (32*K arcs), gathers them (K
+// loads in flight) and adds its runs sequentially; runs that are complete
+// inside a lane go straight to pp[row].  Runs crossing lanes are joined by a
+// warp scan keyed by row (rows ascend, so equal keys are adjacent lanes), and
+// a run reaching the batch end is carried into the next batch.  Every row's
+// segment sum is therefore formed in arc order, deterministically.
+template <class Acc, int K>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, int s,
                                                                 const int64_t* __restrict__ toff, int64_t T,
-                                                                const int64_t* __restrict__ tend, int64_t CA,
+                                                                const int64_t* __restrict__ tend,
+                                                                const int64_t* __restrict__ cbase,
+                                                                const int64_t* __restrict__ ctile,
                                                                 const int32_t* __restrict__ packed,
                                                                 const int32_t* __restrict__ prow,
                                                                 Acc* __restrict__ pp) {
@@ -496,58 +522,91 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, in
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t* tof = toff + (int64_t)s * T;
-  const int64_t sbeg = tof[0], send = tend[s];
-  const int64_t nchunks = (send - sbeg + CA - 1) / CA;
+  const int64_t send = tend[s];
+  const int64_t* ct = ctile + cbase[s];
+  const int64_t nchunks = cbase[s + 1] - cbase[s] - 1;
   for (int64_t ch = warp_id; ch < nchunks; ch += nwarps) {
-    const int64_t t0 = ch == 0 ? 0 : tile_at_or_after(tof, T, sbeg + ch * CA);
-    const int64_t t1 = tile_at_or_after(tof, T, sbeg + (ch + 1) * CA);
+    const int64_t t0 = ct[ch], t1 = ct[ch + 1];
     const int64_t a0 = t0 < T ? tof[t0] : send;
     const int64_t a1 = t1 < T ? tof[t1] : send;
     int carry_r = -1;
     Acc carry_v = Acc(0);
-    for (int64_t base = a0; base < a1; base += 32 * UB) {
-      int r[UB];
-      Acc val[UB];
+    for (int64_t base = a0; base < a1; base += 32 * K) {
+      const int64_t lb = base + (int64_t)lane * K;
+      const int nact = a1 - lb >= K ? K : (a1 - lb > 0 ? (int)(a1 - lb) : 0);
+      int rk[K];
+      Acc vk[K];
 #pragma unroll
-      for (int q = 0; q < UB; ++q) {
-        const int64_t j = base + q * 32 + lane;
-        const bool act = j < a1;
-        r[q] = act ? __ldcs(prow + j) : -2 - lane;  // inactive lanes: unique keys
-        const int32_t u = act ? ld_idx(packed + j) : 0;
+      for (int k = 0; k < K; ++k) {
+        const bool act = k < nact;
+        rk[k] = act ? __ldcs(prow + lb + k) : -1;
+        const int32_t u = act ? ld_idx(packed + lb + k) : 0;
         if constexpr (std::is_same<Acc, double>::value) {
-          val[q] = act ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u) : 0.0;
+          vk[k] = act ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u) : 0.0;
         } else {
-          val[q] = act ? (st.rb ? ld_c_f(reinterpret_cast<const __nv_bfloat16*>(st.cin), u)
-                                : ld_c_f(reinterpret_cast<const float*>(st.cin), u))
-                       : 0.f;
+          vk[k] = act ? (st.rb ? ld_c_f(reinterpret_cast<const __nv_bfloat16*>(st.cin), u)
+                               : ld_c_f(reinterpret_cast<const float*>(st.cin), u))
+                      : 0.f;
         }
       }
+      // lane-local runs: head (first row, may continue from earlier lanes),
+      // interior runs (complete here), tail (last row, may continue later)
+      const int rf = nact > 0 ? rk[0] : -2 - lane;  // empty lanes: unique keys
+      int cr = rf;
+      Acc cur = Acc(0), head = Acc(0);
+      bool multi = false;
 #pragma unroll
-      for (int q = 0; q < UB; ++q) {
-        const int64_t bq = base + q * 32;
-        if (bq >= a1) break;  // warp-uniform
-        const int lastl = a1 - bq >= 32 ? 31 : (int)(a1 - bq - 1);
-        Acc x = val[q];
-        if (lane == 0 && carry_r >= 0) {
-          if (r[q] == carry_r)
-            x = add_rn(carry_v, x);  // the carried run continues: its earlier arcs first
-          else
-            pp[carry_r] = add_rn(pp[carry_r], carry_v);  // it ended at the previous batch's end
+      for (int k = 0; k < K; ++k) {
+        if (k < nact) {
+          if (rk[k] != cr) {
+            if (!multi) {
+              head = cur;
+              multi = true;
+            } else {
+              pp[cr] = add_rn(pp[cr], cur);
+            }
+            cr = rk[k];
+            cur = vk[k];
+          } else {
+            cur = add_rn(cur, vk[k]);
+          }
         }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const Acc t = __shfl_up_sync(FULL, x, o);
-          const int ro = __shfl_up_sync(FULL, r[q], o);
-          if (lane >= o && ro == r[q]) x = add_rn(x, t);
-        }
-        const int rn = __shfl_down_sync(FULL, r[q], 1);
-        const bool batch_end = bq + 32 >= a1;  // no later batch in this chunk
-        const bool run_end = lane < lastl ? rn != r[q] : (lane == lastl && batch_end);
-        if (run_end) pp[r[q]] = add_rn(pp[r[q]], x);
-        carry_r = __shfl_sync(FULL, r[q], lastl);
-        carry_v = __shfl_sync(FULL, x, lastl);
-        if (batch_end) carry_r = -1;
       }
+      // carry from the previous batch joins lane 0
+      if (lane == 0 && carry_r >= 0) {
+        if (rf == carry_r) {
+          if (multi) head = add_rn(carry_v, head);
+          else cur = add_rn(carry_v, cur);
+        } else {
+          pp[carry_r] = add_rn(pp[carry_r], carry_v);  // it ended at the previous batch's end
+        }
+      }
+      // inclusive scan of tails keyed by tail row; a multi-row lane starts a key
+      int kk = cr;
+      Acc vv = cur;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ko = __shfl_up_sync(FULL, kk, o);
+        const Acc vo = __shfl_up_sync(FULL, vv, o);
+        if (lane >= o && ko == kk) vv = add_rn(vo, vv);
+      }
+      // exclusive prefix (previous lane's inclusive) completes a multi lane's head
+      const int ke = __shfl_up_sync(FULL, kk, 1);
+      const Acc ve = __shfl_up_sync(FULL, vv, 1);
+      if (multi) {
+        const Acc h = (lane > 0 && ke == rf) ? add_rn(ve, head) : head;
+        pp[rf] = add_rn(pp[rf], h);
+      }
+      // a tail is complete when the next lane starts another row, or at the
+      // chunk's end; the last active lane's tail otherwise carries on
+      const int lastl = a1 - base >= 32 * K ? 31 : (int)((a1 - base - 1) / K);
+      const bool batch_end = base + 32 * K >= a1;
+      const int rn = __shfl_down_sync(FULL, rf, 1);
+      const bool tail_done = lane < lastl ? rn != cr : (lane == lastl && batch_end);
+      if (nact > 0 && tail_done) pp[cr] = add_rn(pp[cr], vv);
+      carry_r = __shfl_sync(FULL, cr, lastl);
+      carry_v = __shfl_sync(FULL, vv, lastl);
+      if (batch_end) carry_r = -1;
     }
   }
 }
@@ -982,6 +1041,7 @@ constexpr int64_t SMALL_MAX = 64;  // rows up to this in-degree go to k_pull_sma
 constexpr int64_t SMALL_MAX_SEG = 255;  // ... and to the packed COO passes when L2-blocked
 constexpr int SMALL_UB = 4;        // 32-arc batches in flight per warp
 constexpr int64_t SMALL_CHUNK_ARCS = 2048;  // arcs per COO chunk (moved to tile boundaries)
+constexpr int SMALL_K = 8;                  // consecutive arcs per lane in a COO batch
 
 static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_bytes) {
   Tuning t;
@@ -1097,7 +1157,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   // ---- scratch (inside the trial, §2.3) ----
   Scratch xs, cbuf, list, ctrl, cnt, offs, tmp, cstart, csum, partial, meta;
   Scratch seg_rs, seg_bnd, seg_pp, seg_cstart, seg_meta;
-  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_prow, sm_pp, sm_tend;
+  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_prow, sm_pp, sm_tend, sm_cbase, sm_ctile;
   Acc* x = user_scores;
   if (!user_dev) {
     GAP_TRY(xs.get(xbytes, s));
@@ -1207,6 +1267,16 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_CUDA(cudaMemcpyAsync(tend_h.data(), sm_tend.p, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, s));
     GAP_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < S; ++k) seg_small_arcs[k] = tend_h[k] - (k ? tend_h[k - 1] : 0);
+    std::vector<int64_t> cb(S + 1, 0);
+    for (int k = 0; k < S; ++k) cb[k + 1] = cb[k] + (seg_small_arcs[k] + SMALL_CHUNK_ARCS - 1) / SMALL_CHUNK_ARCS + 1;
+    GAP_TRY(sm_cbase.get(sizeof(int64_t) * (S + 1), s));
+    GAP_TRY(sm_ctile.get(sizeof(int64_t) * cb[S], s));
+    GAP_CUDA(cudaMemcpyAsync(sm_cbase.p, cb.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    k_coo_chunks<<<stride_grid(cb[S], 256, 4), 256, 0, s>>>(sm_toff.as<int64_t>(), T, S, sm_tend.as<int64_t>(),
+                                                             SMALL_CHUNK_ARCS, sm_cbase.as<int64_t>(), cb[S],
+                                                             sm_ctile.as<int64_t>());
+    GAP_LAUNCH_CHECK();
+    GAP_CUDA(cudaStreamSynchronize(s));  // cb (host) must outlive the copy
   }
   tm.end(GAP_PHASE_BIN, tok);
   tm.collect();
@@ -1338,9 +1408,9 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
         case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
         case L_SMALL_SEG:
-          k_pull_small_coo<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(
-              b, r.s, sm_toff.as<int64_t>(), T, sm_tend.as<int64_t>(), SMALL_CHUNK_ARCS, sm_packed.as<int32_t>(),
-              sm_prow.as<int32_t>(), sm_pp.as<Acc>());
+          k_pull_small_coo<Acc, SMALL_K><<<r.grid, PR_THREADS, 0, ls>>>(
+              b, r.s, sm_toff.as<int64_t>(), T, sm_tend.as<int64_t>(), sm_cbase.as<int64_t>(), sm_ctile.as<int64_t>(),
+              sm_packed.as<int32_t>(), sm_prow.as<int32_t>(), sm_pp.as<Acc>());
           break;
         case L_SMALL_UPD:
           k_small_update<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[BIN_ZERO].hi, sm_pp.as<Acc>());
@@ -1469,7 +1539,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   for (const LaunchRec& r : plan) per_iter += (r.kind == L_HUB || r.kind == L_HUB_SEG) ? (r.grid > 0 ? 2 : 1) : 1;
   g->launches_per_iter = per_iter;
   g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/ + (S > 1 && seg_rows > 0 ? 1 : 0) +
-                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 7 : 0);
+                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 8 : 0);
   g->last_segments = S;
   for (int q = 0; q < NBINS; ++q) {
     g->last_bin_hi[q] = t.bin[q].hi;
