@@ -466,68 +466,44 @@ __global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __rest
   }
 }
 
-// Chunk table of the COO passes: the packed arcs of segment s are cut into
-// chunks of about CA arcs whose ends are moved to tile boundaries, so rows
-// never straddle a chunk.  ctile[cbase[s] + c] is the first tile of chunk c
-// (one extra entry per segment closes the last chunk).
-__global__ void k_coo_chunks(const int64_t* __restrict__ toff, int64_t T, int S, const int64_t* __restrict__ tend,
-                             int64_t CA, const int64_t* __restrict__ cbase, int64_t total_entries,
-                             int64_t* __restrict__ ctile) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total_entries;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int sg = 0;
-    while (sg + 1 < S && cbase[sg + 1] <= e) ++sg;
-    const int64_t c = e - cbase[sg];
-    const int64_t* tof = toff + (int64_t)sg * T;
-    const int64_t sbeg = tof[0], send = tend[sg];
-    const int64_t last = cbase[sg + 1] - cbase[sg] - 1;  // the closing entry
-    int64_t tile;
-    if (c == 0) {
-      tile = 0;
-    } else if (c == last) {
-      tile = T;
-    } else {
-      const int64_t target = sbeg + c * CA;
-      int64_t lo = 0, hi = T;  // first tile with tof >= target
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (tof[mid] < target) lo = mid + 1; else hi = mid;
-      }
-      tile = lo;
-    }
-    (void)send;
-    ctile[e] = tile;
-  }
-}
-
-// Segment pass s over the small rows, COO style.  Each warp streams chunks;
-// each lane takes K consecutive arcs of a batch (32*K arcs), gathers them (K
-// loads in flight) and adds its runs sequentially; runs that are complete
-// inside a lane go straight to pp[row].  Runs crossing lanes are joined by a
-// warp scan keyed by row (rows ascend, so equal keys are adjacent lanes), and
-// a run reaching the batch end is carried into the next batch.  Every row's
-// segment sum is therefore formed in arc order, deterministically.
-template <class Acc, int K>
-__global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, int s,
-                                                                const int64_t* __restrict__ toff, int64_t T,
+// Segment pass s over the small rows, COO style.  A warp takes a chunk of
+// TPC tiles (32*TPC consecutive vertices; rows never straddle a chunk) and
+// streams the chunk's packed arcs in batches: each lane takes K consecutive
+// arcs, gathers them (K loads in flight) and adds its runs sequentially; runs
+// crossing lanes are joined by a warp scan keyed by row (rows ascend, so
+// equal keys are adjacent lanes), and a run reaching the batch end is carried
+// into the next batch.  Every row's segment sum is thus formed in arc order,
+// deterministically, and lands once in a per-warp shared-memory slot.  At the
+// chunk's end the slots are flushed with coalesced accesses: pass 0 writes
+// pp, later passes add to it, and the last pass applies the rows' updates.
+template <class Acc, int K, int TPC>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, int64_t n, int64_t small_max, int s,
+                                                                int S, const int64_t* __restrict__ toff, int64_t T,
                                                                 const int64_t* __restrict__ tend,
-                                                                const int64_t* __restrict__ cbase,
-                                                                const int64_t* __restrict__ ctile,
                                                                 const int32_t* __restrict__ packed,
                                                                 const int32_t* __restrict__ prow,
                                                                 Acc* __restrict__ pp) {
+  constexpr int ROWS = TPC * 32;
+  __shared__ Acc sacc_all[PR_THREADS / 32][ROWS];
   const IterState st = iter_state(a);
   const int lane = threadIdx.x & 31;
+  Acc* sacc = sacc_all[threadIdx.x >> 5];
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t* tof = toff + (int64_t)s * T;
   const int64_t send = tend[s];
-  const int64_t* ct = ctile + cbase[s];
-  const int64_t nchunks = cbase[s + 1] - cbase[s] - 1;
+  const int64_t nchunks = (T + TPC - 1) / TPC;
+  const bool last = s + 1 == S;
+  const int zero_fill = a.ctrl->zero_fill_until;
+  double dl = 0.0;
   for (int64_t ch = warp_id; ch < nchunks; ch += nwarps) {
-    const int64_t t0 = ct[ch], t1 = ct[ch + 1];
-    const int64_t a0 = t0 < T ? tof[t0] : send;
+    const int64_t t0 = ch * TPC, t1 = t0 + TPC < T ? t0 + TPC : T;
+    const int64_t r0 = t0 * 32;
+    const int span = (int)((t1 - t0) * 32);
+    for (int i = lane; i < span; i += 32) sacc[i] = Acc(0);
+    __syncwarp();
+    const int64_t a0 = tof[t0];
     const int64_t a1 = t1 < T ? tof[t1] : send;
     int carry_r = -1;
     Acc carry_v = Acc(0);
@@ -563,7 +539,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, in
               head = cur;
               multi = true;
             } else {
-              pp[cr] = add_rn(pp[cr], cur);
+              sacc[cr - r0] = cur;
             }
             cr = rk[k];
             cur = vk[k];
@@ -572,13 +548,12 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, in
           }
         }
       }
-      // carry from the previous batch joins lane 0
-      if (lane == 0 && carry_r >= 0) {
+      if (lane == 0 && carry_r >= 0) {  // the run carried from the previous batch
         if (rf == carry_r) {
           if (multi) head = add_rn(carry_v, head);
           else cur = add_rn(carry_v, cur);
         } else {
-          pp[carry_r] = add_rn(pp[carry_r], carry_v);  // it ended at the previous batch's end
+          sacc[carry_r - r0] = carry_v;  // it ended at the previous batch's end
         }
       }
       // inclusive scan of tails keyed by tail row; a multi-row lane starts a key
@@ -590,44 +565,36 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, in
         const Acc vo = __shfl_up_sync(FULL, vv, o);
         if (lane >= o && ko == kk) vv = add_rn(vo, vv);
       }
-      // exclusive prefix (previous lane's inclusive) completes a multi lane's head
       const int ke = __shfl_up_sync(FULL, kk, 1);
       const Acc ve = __shfl_up_sync(FULL, vv, 1);
-      if (multi) {
-        const Acc h = (lane > 0 && ke == rf) ? add_rn(ve, head) : head;
-        pp[rf] = add_rn(pp[rf], h);
-      }
-      // a tail is complete when the next lane starts another row, or at the
-      // chunk's end; the last active lane's tail otherwise carries on
+      if (multi) sacc[rf - r0] = (lane > 0 && ke == rf) ? add_rn(ve, head) : head;
       const int lastl = a1 - base >= 32 * K ? 31 : (int)((a1 - base - 1) / K);
       const bool batch_end = base + 32 * K >= a1;
       const int rn = __shfl_down_sync(FULL, rf, 1);
       const bool tail_done = lane < lastl ? rn != cr : (lane == lastl && batch_end);
-      if (nact > 0 && tail_done) pp[cr] = add_rn(pp[cr], vv);
+      if (nact > 0 && tail_done) sacc[cr - r0] = vv;
       carry_r = __shfl_sync(FULL, cr, lastl);
       carry_v = __shfl_sync(FULL, vv, lastl);
       if (batch_end) carry_r = -1;
     }
+    __syncwarp();
+    for (int i = lane; i < span; i += 32) {
+      const int64_t v = r0 + i;
+      if (v >= n) break;
+      const Acc part = sacc[i];
+      if (!last) {
+        __stcs(pp + v, s ? add_rn(__ldcs(pp + v), part) : part);
+      } else {
+        const int64_t deg = __ldcs(a.off + v + 1) - __ldcs(a.off + v);
+        if (deg <= small_max && (deg > 0 || st.it < zero_fill)) {
+          const Acc sum = S > 1 ? add_rn(__ldcs(pp + v), part) : part;
+          dl += update_row(a, v, sum, st.cout, st.wb);
+        }
+      }
+    }
+    __syncwarp();
   }
-}
-
-// Per iteration, after all segment passes: the small rows' updates in vertex
-// order (coalesced), and pp reset to zero for the next iteration.
-template <class Acc>
-__global__ void __launch_bounds__(PR_THREADS) k_small_update(PrArgs<Acc> a, int64_t n, int64_t small_max,
-                                                              Acc* __restrict__ pp) {
-  const IterState st = iter_state(a);
-  const int zero_fill = a.ctrl->zero_fill_until;
-  double dl = 0.0;
-  for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < n; v += (int64_t)gridDim.x * PR_THREADS) {
-    const int64_t deg = __ldcs(a.off + v + 1) - __ldcs(a.off + v);
-    if (deg > small_max) continue;
-    if (deg == 0 && st.it >= zero_fill) continue;
-    const Acc sum = deg > 0 ? __ldcs(pp + v) : Acc(0);
-    if (deg > 0) __stcs(pp + v, Acc(0));
-    dl += update_row(a, v, sum, st.cout, st.wb);
-  }
-  write_partial(dl, a.partial);
+  if (last) write_partial(dl, a.partial);
 }
 
 // ---- group-per-row kernels (G lanes per row) --------------------------------
@@ -1040,8 +1007,8 @@ constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
 constexpr int64_t SMALL_MAX = 64;  // rows up to this in-degree go to k_pull_small
 constexpr int64_t SMALL_MAX_SEG = 255;  // ... and to the packed COO passes when L2-blocked
 constexpr int SMALL_UB = 4;        // 32-arc batches in flight per warp
-constexpr int64_t SMALL_CHUNK_ARCS = 2048;  // arcs per COO chunk (moved to tile boundaries)
-constexpr int SMALL_K = 8;                  // consecutive arcs per lane in a COO batch
+constexpr int SMALL_TPC = 32;  // 32-vertex tiles per COO chunk (rows staged in shared memory)
+constexpr int SMALL_K = 8;     // consecutive arcs per lane in a COO batch
 
 static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_bytes) {
   Tuning t;
@@ -1130,7 +1097,7 @@ struct PhaseTimer {
   }
 };
 
-enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_SMALL_SEG, L_SMALL_UPD, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
+enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_SMALL_SEG, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -1157,7 +1124,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   // ---- scratch (inside the trial, §2.3) ----
   Scratch xs, cbuf, list, ctrl, cnt, offs, tmp, cstart, csum, partial, meta;
   Scratch seg_rs, seg_bnd, seg_pp, seg_cstart, seg_meta;
-  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_prow, sm_pp, sm_tend, sm_cbase, sm_ctile;
+  Scratch sm_cnt, sm_ttot, sm_toff, sm_tmp, sm_total, sm_packed, sm_prow, sm_pp, sm_tend;
   Acc* x = user_scores;
   if (!user_dev) {
     GAP_TRY(xs.get(xbytes, s));
@@ -1256,7 +1223,6 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
     GAP_TRY(sm_prow.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
     GAP_TRY(sm_tend.get(sizeof(int64_t) * S, s));
-    GAP_CUDA(cudaMemsetAsync(sm_pp.p, 0, sizeof(Acc) * n, s));
     k_small_pack<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
                                                                         sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
                                                                         sm_packed.as<int32_t>(), sm_prow.as<int32_t>());
@@ -1267,16 +1233,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_CUDA(cudaMemcpyAsync(tend_h.data(), sm_tend.p, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, s));
     GAP_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < S; ++k) seg_small_arcs[k] = tend_h[k] - (k ? tend_h[k - 1] : 0);
-    std::vector<int64_t> cb(S + 1, 0);
-    for (int k = 0; k < S; ++k) cb[k + 1] = cb[k] + (seg_small_arcs[k] + SMALL_CHUNK_ARCS - 1) / SMALL_CHUNK_ARCS + 1;
-    GAP_TRY(sm_cbase.get(sizeof(int64_t) * (S + 1), s));
-    GAP_TRY(sm_ctile.get(sizeof(int64_t) * cb[S], s));
-    GAP_CUDA(cudaMemcpyAsync(sm_cbase.p, cb.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
-    k_coo_chunks<<<stride_grid(cb[S], 256, 4), 256, 0, s>>>(sm_toff.as<int64_t>(), T, S, sm_tend.as<int64_t>(),
-                                                             SMALL_CHUNK_ARCS, sm_cbase.as<int64_t>(), cb[S],
-                                                             sm_ctile.as<int64_t>());
-    GAP_LAUNCH_CHECK();
-    GAP_CUDA(cudaStreamSynchronize(s));  // cb (host) must outlive the copy
+
   }
   tm.end(GAP_PHASE_BIN, tok);
   tm.collect();
@@ -1326,9 +1283,13 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       r.bin = BIN_ZERO;
       r.lanes = LANES_SMALL;
       r.s = sgi;
-      r.grid = stride_grid(seg_small_arcs[sgi] / SMALL_CHUNK_ARCS * 32 + 32, PR_THREADS, 8);
+      r.grid = stride_grid((T + SMALL_TPC - 1) / SMALL_TPC * 32, PR_THREADS, 8);
       r.poff = -1;
       r.poff2 = -1;
+      if (sgi + 1 == S) {
+        r.poff = np;
+        np += r.grid;
+      }
       plan.push_back(r);
     }
     for (int q = 0; q < NBINS; ++q) {
@@ -1358,17 +1319,6 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       }
       plan.push_back(r);
     }
-  }
-  if (small_packed) {  // the small rows' update after the last segment pass
-    LaunchRec r{};
-    r.kind = L_SMALL_UPD;
-    r.bin = BIN_ZERO;
-    r.lanes = LANES_SMALL;
-    r.grid = stride_grid(n, PR_THREADS, 8);
-    r.poff = np;
-    r.poff2 = -1;
-    np += r.grid;
-    plan.push_back(r);
   }
   GAP_TRY(partial.get(sizeof(double) * (np > 0 ? np : 1), s));
   if (np == 0) GAP_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double), s));
@@ -1408,12 +1358,10 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
         case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
         case L_SMALL_SEG:
-          k_pull_small_coo<Acc, SMALL_K><<<r.grid, PR_THREADS, 0, ls>>>(
-              b, r.s, sm_toff.as<int64_t>(), T, sm_tend.as<int64_t>(), sm_cbase.as<int64_t>(), sm_ctile.as<int64_t>(),
-              sm_packed.as<int32_t>(), sm_prow.as<int32_t>(), sm_pp.as<Acc>());
-          break;
-        case L_SMALL_UPD:
-          k_small_update<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[BIN_ZERO].hi, sm_pp.as<Acc>());
+          k_pull_small_coo<Acc, SMALL_K, std::is_same<Acc, double>::value ? SMALL_TPC / 2 : SMALL_TPC>
+              <<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[BIN_ZERO].hi, r.s, S, sm_toff.as<int64_t>(), T,
+                                              sm_tend.as<int64_t>(), sm_packed.as<int32_t>(),
+                                              sm_prow.as<int32_t>(), sm_pp.as<Acc>());
           break;
         case L_SHORT: k_pull_short<Acc, SHORT_RPT, 4><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_CTA: k_pull_cta<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
@@ -1539,7 +1487,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   for (const LaunchRec& r : plan) per_iter += (r.kind == L_HUB || r.kind == L_HUB_SEG) ? (r.grid > 0 ? 2 : 1) : 1;
   g->launches_per_iter = per_iter;
   g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/ + (S > 1 && seg_rows > 0 ? 1 : 0) +
-                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 8 : 0);
+                      (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 6 : 0);
   g->last_segments = S;
   for (int q = 0; q < NBINS; ++q) {
     g->last_bin_hi[q] = t.bin[q].hi;
