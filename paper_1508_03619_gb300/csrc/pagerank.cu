@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __rest
 // chunk's end the slots are flushed with coalesced accesses: pass 0 writes
 // pp, later passes add to it, and the last pass applies the rows' updates.
 template <class Acc, int K, int TPC>
-__global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, int64_t n, int64_t small_max, int s,
+__global__ void __launch_bounds__(PR_THREADS, 4) k_pull_small_coo(PrArgs<Acc> a, int64_t n, int64_t small_max, int s,
                                                                 int S, const int64_t* __restrict__ toff, int64_t T,
                                                                 const int64_t* __restrict__ tend,
                                                                 const int32_t* __restrict__ packed,
@@ -578,17 +578,56 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small_coo(PrArgs<Acc> a, in
       if (batch_end) carry_r = -1;
     }
     __syncwarp();
-    for (int i = lane; i < span; i += 32) {
-      const int64_t v = r0 + i;
-      if (v >= n) break;
-      const Acc part = sacc[i];
+    // flush, FU rows per lane per round with every load issued up front
+    constexpr int FU = 4;
+    for (int ib = 0; ib < span; ib += 32 * FU) {
+      int64_t v[FU];
+      bool ok[FU];
+      Acc prev[FU];
+#pragma unroll
+      for (int u = 0; u < FU; ++u) {
+        const int i = ib + u * 32 + lane;
+        v[u] = r0 + i;
+        ok[u] = i < span && v[u] < n;
+        prev[u] = (ok[u] && s > 0) ? __ldcs(pp + v[u]) : Acc(0);
+      }
       if (!last) {
-        __stcs(pp + v, s ? add_rn(__ldcs(pp + v), part) : part);
+#pragma unroll
+        for (int u = 0; u < FU; ++u)
+          if (ok[u]) __stcs(pp + v[u], s ? add_rn(prev[u], sacc[ib + u * 32 + lane]) : sacc[ib + u * 32 + lane]);
       } else {
-        const int64_t deg = __ldcs(a.off + v + 1) - __ldcs(a.off + v);
-        if (deg <= small_max && (deg > 0 || st.it < zero_fill)) {
-          const Acc sum = S > 1 ? add_rn(__ldcs(pp + v), part) : part;
-          dl += update_row(a, v, sum, st.cout, st.wb);
+        int64_t ob[FU], oe[FU];
+        Acc xo[FU];
+        int32_t od[FU];
+#pragma unroll
+        for (int u = 0; u < FU; ++u) {
+          ob[u] = ok[u] ? __ldcs(a.off + v[u]) : 0;
+          oe[u] = ok[u] ? __ldcs(a.off + v[u] + 1) : 0;
+          xo[u] = ok[u] ? __ldcs(a.x + v[u]) : Acc(0);
+          od[u] = ok[u] ? __ldcs(a.outdeg + v[u]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < FU; ++u) {
+          const int64_t deg = oe[u] - ob[u];
+          if (!ok[u] || deg > small_max || (deg == 0 && st.it >= zero_fill)) continue;
+          const Acc sum = add_rn(prev[u], sacc[ib + u * 32 + lane]);
+          Acc xn;
+          if constexpr (std::is_same<Acc, double>::value)
+            xn = __dadd_rn(a.base, __dmul_rn(a.d, sum));
+          else
+            xn = __fadd_rn(a.base, __fmul_rn(a.d, sum));
+          __stcs(a.x + v[u], xn);
+          const Acc cv = od[u] > 0 ? xn / (Acc)od[u] : Acc(0);
+          if constexpr (std::is_same<Acc, double>::value) {
+            reinterpret_cast<double*>(st.cout)[v[u]] = cv;
+          } else {
+            if (st.wb)
+              reinterpret_cast<__nv_bfloat16*>(st.cout)[v[u]] = __float2bfloat16_rn(cv);
+            else
+              reinterpret_cast<float*>(st.cout)[v[u]] = cv;
+          }
+          const double dd = (double)xn - (double)xo[u];
+          dl += dd < 0 ? -dd : dd;
         }
       }
     }
