@@ -159,9 +159,10 @@ typedef struct {
   uint32_t timing;        /* 1: time every kernel with CUDA events (forces the host
                              loop); per-phase times land in gap_pr_stats_t */
   int64_t segment_bytes;  /* L2 blocking: when the contribution array is larger than
-                             this, rows above 64 in-edges are pulled one source segment
-                             of about this many bytes at a time (0 = library default,
-                             tuned per GPU; < 0 disables) */
+                             this, rows are pulled one source segment at a time; a
+                             segment spans a power-of-two number of vertices whose
+                             contributions take at most this many bytes (0 = library
+                             default, tuned per GPU; < 0 disables) */
   int64_t small_max_degree; /* rows with at most this many in-edges are pulled in vertex
                                order by the warp-merge kernel (0 = default 64; at most
                                512, and 255 when L2 blocking is active) */
@@ -179,13 +180,14 @@ GAP_API gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int
 #define GAP_PR_HIST 256
 /* Phases timed with options.timing (index into phase_ms / phase_launches).
  * Pull phases are per degree bin (see gap_pr_stats_t.bin_*). */
-#define GAP_PHASE_BIN 0      /* degree binning (and segment split points) */
+#define GAP_PHASE_BIN 0      /* degree binning */
 #define GAP_PHASE_INIT 1     /* x0 and first contributions */
 #define GAP_PHASE_PULL0 2    /* gather + update of bin 0 .. bin 6: phases 2 .. 8 */
 #define GAP_PHASE_HUB_FIXUP 9
 #define GAP_PHASE_FINALIZE 10 /* delta reduction and stop test */
 #define GAP_PHASE_OUTPUT 11   /* mass reduction and output copy */
-#define GAP_PR_PHASES 12
+#define GAP_PHASE_PREP 12     /* L2 blocking set-up: split points, hub tables, packing */
+#define GAP_PR_PHASES 13
 #define GAP_PR_BINS 7
 typedef struct {
   int32_t iterations;   /* iterations performed */

@@ -398,31 +398,58 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small(PrArgs<Acc> a, int64_
 // pass then streams its arcs contiguously and gathers only from that
 // segment's contributions, which stay in L2.
 
-// cnt8[s][v] and per-tile totals; rows above small_max count zero.
+// cnt8[s][v] and per-tile totals; rows above small_max count zero.  Segment
+// widths are powers of two (s = u >> wbits).  Each thread reads its row in
+// unrolled chunks and counts runs of equal segment (the row is sorted);
+// cnt8 must be zero beforehand.  Per-tile totals come from a warp-local
+// shared-memory histogram.
+constexpr int COUNT_MAX_S = 64;
 __global__ void __launch_bounds__(PR_THREADS) k_small_count(const int64_t* __restrict__ off,
                                                              const int32_t* __restrict__ idx, int64_t n,
-                                                             int64_t small_max, int S, int64_t W,
+                                                             int64_t small_max, int S, int wbits,
                                                              uint8_t* __restrict__ cnt8, uint32_t* __restrict__ ttot,
                                                              int64_t T) {
-  const int lane = threadIdx.x & 31;
+  __shared__ uint32_t hist[PR_THREADS / 32][COUNT_MAX_S];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = lane; q < COUNT_MAX_S; q += 32) hist[warp][q] = 0;
+  __syncwarp();
   const int64_t nr = (n + 31) & ~int64_t(31);
   for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < nr; v += (int64_t)gridDim.x * PR_THREADS) {
     const bool valid = v < n;
     const int64_t rb = valid ? off[v] : 0, re = valid ? off[v + 1] : 0;
-    const bool small = valid && re - rb <= small_max;
-    int64_t j = rb;
-    for (int sg = 0; sg < S; ++sg) {
-      const int64_t hi = (int64_t)(sg + 1) * W;
-      int k = 0;
-      if (small)
-        while (j < re && (int64_t)idx[j] < hi) {
-          ++k;
-          ++j;
+    if (valid && re - rb <= small_max && re > rb) {
+      int cs = -1, k = 0;
+      for (int64_t j0 = rb; j0 < re; j0 += 8) {
+        int su[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) su[q] = j0 + q < re ? (int)(idx[j0 + q] >> wbits) : -1;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (su[q] < 0) break;
+          if (su[q] != cs) {
+            if (k) {
+              cnt8[(int64_t)cs * n + v] = (uint8_t)k;
+              atomicAdd(&hist[warp][cs], (uint32_t)k);
+            }
+            cs = su[q];
+            k = 1;
+          } else {
+            ++k;
+          }
         }
-      if (valid) cnt8[(int64_t)sg * n + v] = (uint8_t)k;
-      const int tot = warp_sum(k);
-      if (lane == 0) ttot[(int64_t)sg * T + (v >> 5)] = (uint32_t)tot;
+      }
+      if (k) {
+        cnt8[(int64_t)cs * n + v] = (uint8_t)k;
+        atomicAdd(&hist[warp][cs], (uint32_t)k);
+      }
     }
+    __syncwarp();
+    const int64_t tile = v >> 5;
+    for (int q = lane; q < S; q += 32) {
+      ttot[(int64_t)q * T + tile] = hist[warp][q];
+      hist[warp][q] = 0;
+    }
+    __syncwarp();
   }
 }
 
@@ -1039,7 +1066,7 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
 
 // ---- host orchestration ------------------------------------------------------
 
-constexpr int64_t DEFAULT_SEGMENT_BYTES = 40ll << 20;  // GB300: ~126 MB of L2 over two dies
+constexpr int64_t DEFAULT_SEGMENT_BYTES = 32ll << 20;  // GB300: ~126 MB of L2 over two dies
 constexpr int64_t HUB_CHUNK = 32768;
 constexpr int64_t HUB_CHUNK_SEG = 4096;
 constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
@@ -1061,9 +1088,16 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
   const int64_t seg_bytes = o.segment_bytes == 0 ? DEFAULT_SEGMENT_BYTES : o.segment_bytes;
   const int64_t cbytes = (int64_t)c_elem_bytes * n;
   if (seg_bytes > 0 && cbytes > seg_bytes) {
-    t.segments = (int)((cbytes + seg_bytes - 1) / seg_bytes);
-    if (t.segments > 64) t.segments = 64;
-    t.seg_width = (n + t.segments - 1) / t.segments;
+    // largest power-of-two vertex span whose contributions fit in seg_bytes
+    int64_t w = 1;
+    while (w * 2 * (int64_t)c_elem_bytes <= seg_bytes) w *= 2;
+    while ((n + w - 1) / w > 64) w *= 2;
+    t.seg_width = w;
+    t.segments = (int)((n + w - 1) / w);
+    if (t.segments < 2) {
+      t.segments = 1;
+      t.seg_width = n;
+    }
   }
   const bool seg = t.segments > 1;
   // rows with in-degree <= small (bins 1-3 stay empty): one vertex-order kernel
@@ -1126,6 +1160,7 @@ struct PhaseTimer {
     if (!on) return;
     for (size_t k = 0; k + 1 < used; k += 2) {
       float t = 0.f;
+      cudaEventSynchronize(ev[k + 1]);
       if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) == cudaSuccess) ms[ph[k]] += t;
     }
     used = 0;
@@ -1250,8 +1285,11 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_TRY(sm_tmp.get(sizeof(int64_t) * scan_tmp_elems(S * T), s));
     GAP_TRY(sm_total.get(sizeof(int64_t), s));
     GAP_TRY(sm_pp.get(sizeof(Acc) * n, s));
+    int wbits = 0;
+    while ((int64_t(1) << wbits) < t.seg_width) ++wbits;
+    GAP_CUDA(cudaMemsetAsync(sm_cnt.p, 0, (size_t)S * n, s));
     k_small_count<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
-                                                                         t.seg_width, sm_cnt.as<uint8_t>(),
+                                                                         wbits, sm_cnt.as<uint8_t>(),
                                                                          sm_ttot.as<uint32_t>(), T);
     GAP_LAUNCH_CHECK();
     GAP_TRY(exclusive_scan_u32(sm_ttot.as<uint32_t>(), sm_toff.as<int64_t>(), S * T, sm_tmp.as<int64_t>(),
@@ -1274,7 +1312,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     for (int k = 0; k < S; ++k) seg_small_arcs[k] = tend_h[k] - (k ? tend_h[k - 1] : 0);
 
   }
-  tm.end(GAP_PHASE_BIN, tok);
+  tm.end(GAP_PHASE_PREP, tok);
   tm.collect();
 
   // ---- launch plan of one iteration ----

@@ -35,10 +35,10 @@ GAP_LOOP_GRAPH = 0
 GAP_LOOP_HOST = 1
 GAP_NO_LADDER = -(2 ** 31)
 GAP_PR_HIST = 256
-GAP_PR_PHASES = 12
+GAP_PR_PHASES = 13
 GAP_PR_BINS = 7
 PHASE_NAMES = ("bin", "init", "pull0", "pull1", "pull2", "pull3", "pull4", "pull5", "pull6",
-               "hub_fixup", "finalize", "output")
+               "hub_fixup", "finalize", "output", "prep")
 PULL_PHASES = PHASE_NAMES[2:9]
 
 # every symbol include/gap.h declares (checked by the ABI test)

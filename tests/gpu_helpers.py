@@ -34,7 +34,8 @@ def oracle_graph(n, src, dst, symmetrize=False, dedup=True, drop_self_loops=True
 
 def seg_bytes_for(n):
     """A segment size that splits the contribution array of n vertices into
-    4 (FP32) or 8 (FP64) source segments, forcing the L2-blocked kernels."""
+    about 4 (FP32) or 8 (FP64) power-of-two source segments, forcing the
+    L2-blocked kernels."""
     return max(64, n)
 
 
