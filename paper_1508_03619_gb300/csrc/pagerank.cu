@@ -398,56 +398,133 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small(PrArgs<Acc> a, int64_
 // pass then streams its arcs contiguously and gathers only from that
 // segment's contributions, which stay in L2.
 
-// cnt8[s][v] and per-tile totals; rows above small_max count zero.  Segment
-// widths are powers of two (s = u >> wbits).  Each thread reads its row in
-// unrolled chunks and counts runs of equal segment (the row is sorted);
-// cnt8 must be zero beforehand.  Per-tile totals come from a warp-local
-// shared-memory histogram.
-constexpr int COUNT_MAX_S = 64;
-__global__ void __launch_bounds__(PR_THREADS) k_small_count(const int64_t* __restrict__ off,
-                                                             const int32_t* __restrict__ idx, int64_t n,
-                                                             int64_t small_max, int S, int wbits,
-                                                             uint8_t* __restrict__ cnt8, uint32_t* __restrict__ ttot,
-                                                             int64_t T) {
-  __shared__ uint32_t hist[PR_THREADS / 32][COUNT_MAX_S];
+// Small-row packing, warp per tile (32 consecutive vertices).  The tile's
+// small rows' arcs form one virtual range (exclusive degree prefix `excl`);
+// each lane walks it 32 arcs apart (coalesced reads of the CSC), finding an
+// arc's row by a shuffle binary search.  Segment widths are powers of two
+// (s = u >> wbits).  Per-warp shared tables are indexed [row*S + s].
+constexpr int PACK_WARPS = 4;
+constexpr int PACK_THREADS = PACK_WARPS * 32;
+
+struct TileRows {
+  int64_t rb;  // this lane's row start
+  int excl, total;
+};
+
+__device__ __forceinline__ TileRows tile_rows(const int64_t* __restrict__ off, int64_t n, int64_t v,
+                                              int64_t small_max) {
+  TileRows t;
+  const bool valid = v < n;
+  t.rb = valid ? off[v] : 0;
+  const int64_t re = valid ? off[v + 1] : 0;
+  const int d = (valid && re - t.rb <= small_max) ? (int)(re - t.rb) : 0;
+  int incl = d;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  t.excl = incl - d;
+  t.total = __shfl_sync(0xffffffffu, incl, 31);
+  return t;
+}
+
+// Row of virtual arc jv (largest lane r with excl_r <= jv), its CSC position
+// and the row's virtual start.  All lanes of the warp must call it.
+__device__ __forceinline__ int arc_row(const TileRows& t, int jv, int64_t* pos, int* row_excl) {
+  int rr = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = rr + step;
+    const int ex = __shfl_sync(0xffffffffu, t.excl, cand & 31);
+    if (cand < 32 && ex <= jv) rr = cand;
+  }
+  const int64_t rb = __shfl_sync(0xffffffffu, t.rb, rr);
+  const int ex = __shfl_sync(0xffffffffu, t.excl, rr);
+  *pos = rb + (jv - ex);
+  *row_excl = ex;
+  return rr;
+}
+
+// cnt8[s][v] = arcs of small row v in segment s; ttot[s][tile] = tile totals.
+__global__ void __launch_bounds__(PACK_THREADS) k_small_count(const int64_t* __restrict__ off,
+                                                               const int32_t* __restrict__ idx, int64_t n,
+                                                               int64_t small_max, int S, int wbits,
+                                                               uint8_t* __restrict__ cnt8, uint32_t* __restrict__ ttot,
+                                                               int64_t T) {
+  extern __shared__ uint32_t pack_sh[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = lane; q < COUNT_MAX_S; q += 32) hist[warp][q] = 0;
-  __syncwarp();
-  const int64_t nr = (n + 31) & ~int64_t(31);
-  for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < nr; v += (int64_t)gridDim.x * PR_THREADS) {
-    const bool valid = v < n;
-    const int64_t rb = valid ? off[v] : 0, re = valid ? off[v + 1] : 0;
-    if (valid && re - rb <= small_max && re > rb) {
-      int cs = -1, k = 0;
-      for (int64_t j0 = rb; j0 < re; j0 += 8) {
-        int su[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) su[q] = j0 + q < re ? (int)(idx[j0 + q] >> wbits) : -1;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (su[q] < 0) break;
-          if (su[q] != cs) {
-            if (k) {
-              cnt8[(int64_t)cs * n + v] = (uint8_t)k;
-              atomicAdd(&hist[warp][cs], (uint32_t)k);
-            }
-            cs = su[q];
-            k = 1;
-          } else {
-            ++k;
-          }
-        }
-      }
-      if (k) {
-        cnt8[(int64_t)cs * n + v] = (uint8_t)k;
-        atomicAdd(&hist[warp][cs], (uint32_t)k);
-      }
+  uint32_t* h = pack_sh + warp * 32 * S;
+  const int64_t gw = ((int64_t)blockIdx.x * PACK_THREADS + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * PACK_THREADS) >> 5;
+  for (int64_t tile = gw; tile < T; tile += nw) {
+    for (int q = lane; q < 32 * S; q += 32) h[q] = 0;
+    __syncwarp();
+    const int64_t v = tile * 32 + lane;
+    const TileRows tr = tile_rows(off, n, v, small_max);
+    for (int jb = 0; jb < tr.total; jb += 32) {
+      const int jv = jb + lane;
+      int64_t pos;
+      int ex;
+      const int r = arc_row(tr, jv, &pos, &ex);
+      if (jv < tr.total) atomicAdd(&h[r * S + (idx[pos] >> wbits)], 1u);
     }
     __syncwarp();
-    const int64_t tile = v >> 5;
-    for (int q = lane; q < S; q += 32) {
-      ttot[(int64_t)q * T + tile] = hist[warp][q];
-      hist[warp][q] = 0;
+    for (int sg = 0; sg < S; ++sg) {
+      const uint32_t c = h[lane * S + sg];
+      if (v < n) cnt8[(int64_t)sg * n + v] = (uint8_t)c;
+      const uint32_t tot = warp_sum(c);
+      if (lane == 0) ttot[(int64_t)sg * T + tile] = tot;
+    }
+    __syncwarp();
+  }
+}
+
+// Copy each small row's arcs to its segment-major positions, with the row id
+// of every arc beside it (COO order: rows ascending within a segment).
+__global__ void __launch_bounds__(PACK_THREADS) k_small_pack(const int64_t* __restrict__ off,
+                                                              const int32_t* __restrict__ idx, int64_t n,
+                                                              int64_t small_max, int S, int wbits,
+                                                              const uint8_t* __restrict__ cnt8,
+                                                              const int64_t* __restrict__ toff, int64_t T,
+                                                              int32_t* __restrict__ packed, int32_t* __restrict__ prow) {
+  extern __shared__ uint32_t pack_sh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* tp = pack_sh + warp * 64 * S;  // in-tile prefix of row r in segment s
+  uint32_t* rs = tp + 32 * S;              // start of segment s within row r
+  const int64_t gw = ((int64_t)blockIdx.x * PACK_THREADS + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * PACK_THREADS) >> 5;
+  for (int64_t tile = gw; tile < T; tile += nw) {
+    const int64_t v = tile * 32 + lane;
+    uint32_t run = 0;
+    for (int sg = 0; sg < S; ++sg) {
+      const uint32_t c = v < n ? cnt8[(int64_t)sg * n + v] : 0;
+      rs[lane * S + sg] = run;
+      run += c;
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      tp[lane * S + sg] = incl - c;
+    }
+    __syncwarp();
+    const TileRows tr = tile_rows(off, n, v, small_max);
+    for (int jb = 0; jb < tr.total; jb += 32) {
+      const int jv = jb + lane;
+      int64_t pos;
+      int ex;
+      const int r = arc_row(tr, jv, &pos, &ex);
+      if (jv < tr.total) {
+        const int32_t u = idx[pos];
+        const int sg = u >> wbits;
+        const int64_t k = (int64_t)(jv - ex) - rs[r * S + sg];
+        const int64_t dst = toff[(int64_t)sg * T + tile] + tp[r * S + sg] + k;
+        packed[dst] = u;
+        prow[dst] = (int32_t)(tile * 32 + r);
+      }
     }
     __syncwarp();
   }
@@ -459,39 +536,6 @@ __global__ void k_seg_ends(const int64_t* __restrict__ toff, int64_t T, int S, c
   for (int sg = threadIdx.x; sg < S; sg += blockDim.x) tend[sg] = sg + 1 < S ? toff[(int64_t)(sg + 1) * T] : *total;
 }
 
-// Copy each small row's arcs to its segment-major positions, with the row id
-// of every arc beside it (COO order: rows ascending within a segment).
-__global__ void __launch_bounds__(PR_THREADS) k_small_pack(const int64_t* __restrict__ off,
-                                                            const int32_t* __restrict__ idx, int64_t n,
-                                                            int64_t small_max, int S, const uint8_t* __restrict__ cnt8,
-                                                            const int64_t* __restrict__ toff, int64_t T,
-                                                            int32_t* __restrict__ packed, int32_t* __restrict__ prow) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nr = (n + 31) & ~int64_t(31);
-  for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < nr; v += (int64_t)gridDim.x * PR_THREADS) {
-    const bool valid = v < n;
-    const int64_t rb = valid ? off[v] : 0, re = valid ? off[v + 1] : 0;
-    const bool small = valid && re - rb <= small_max;
-    int64_t j = rb;
-    for (int sg = 0; sg < S; ++sg) {
-      const int k = valid ? cnt8[(int64_t)sg * n + v] : 0;
-      int incl = k;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (small) {
-        const int64_t pos = toff[(int64_t)sg * T + (v >> 5)] + (incl - k);
-        for (int q = 0; q < k; ++q) {
-          packed[pos + q] = idx[j + q];
-          prow[pos + q] = (int32_t)v;
-        }
-        j += k;
-      }
-    }
-  }
-}
 
 // Segment pass s over the small rows, COO style.  A warp takes a chunk of
 // TPC tiles (32*TPC consecutive vertices; rows never straddle a chunk) and
@@ -1287,10 +1331,12 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_TRY(sm_pp.get(sizeof(Acc) * n, s));
     int wbits = 0;
     while ((int64_t(1) << wbits) < t.seg_width) ++wbits;
-    GAP_CUDA(cudaMemsetAsync(sm_cnt.p, 0, (size_t)S * n, s));
-    k_small_count<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
-                                                                         wbits, sm_cnt.as<uint8_t>(),
-                                                                         sm_ttot.as<uint32_t>(), T);
+    const size_t count_smem = sizeof(uint32_t) * PACK_WARPS * 32 * S;
+    const size_t pack_smem = 2 * count_smem;
+    GAP_CUDA(cudaFuncSetAttribute(k_small_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem));
+    GAP_CUDA(cudaFuncSetAttribute(k_small_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pack_smem));
+    k_small_count<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, count_smem, s>>>(
+        g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S, wbits, sm_cnt.as<uint8_t>(), sm_ttot.as<uint32_t>(), T);
     GAP_LAUNCH_CHECK();
     GAP_TRY(exclusive_scan_u32(sm_ttot.as<uint32_t>(), sm_toff.as<int64_t>(), S * T, sm_tmp.as<int64_t>(),
                                sm_total.as<int64_t>(), s));
@@ -1300,9 +1346,9 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
     GAP_TRY(sm_prow.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
     GAP_TRY(sm_tend.get(sizeof(int64_t) * S, s));
-    k_small_pack<<<stride_grid(n, PR_THREADS, 8), PR_THREADS, 0, s>>>(g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S,
-                                                                        sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
-                                                                        sm_packed.as<int32_t>(), sm_prow.as<int32_t>());
+    k_small_pack<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, pack_smem, s>>>(
+        g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S, wbits, sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
+        sm_packed.as<int32_t>(), sm_prow.as<int32_t>());
     GAP_LAUNCH_CHECK();
     k_seg_ends<<<1, 64, 0, s>>>(sm_toff.as<int64_t>(), T, S, sm_total.as<int64_t>(), sm_tend.as<int64_t>());
     GAP_LAUNCH_CHECK();
