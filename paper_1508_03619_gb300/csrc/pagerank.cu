@@ -468,7 +468,9 @@ __global__ void __launch_bounds__(PACK_THREADS) k_small_count(const int64_t* __r
       int64_t pos;
       int ex;
       const int r = arc_row(tr, jv, &pos, &ex);
-      if (jv < tr.total) atomicAdd(&h[r * S + (idx[pos] >> wbits)], 1u);
+      const int key = jv < tr.total ? r * S + (idx[pos] >> wbits) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);  // one add per distinct key
+      if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) h[key] += __popc(peers);
     }
     __syncwarp();
     for (int sg = 0; sg < S; ++sg) {
@@ -491,27 +493,27 @@ __global__ void __launch_bounds__(PACK_THREADS) k_small_pack(const int64_t* __re
                                                               int32_t* __restrict__ packed, int32_t* __restrict__ prow) {
   extern __shared__ uint32_t pack_sh[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* tp = pack_sh + warp * 64 * S;  // in-tile prefix of row r in segment s
-  uint32_t* rs = tp + 32 * S;              // start of segment s within row r
+  // base[r*S + s] = destination of virtual arc 0 of row r in segment s, so an
+  // arc's destination is base + jv (jv = its virtual index in the tile)
+  int64_t* base = reinterpret_cast<int64_t*>(pack_sh) + warp * 32 * S;
   const int64_t gw = ((int64_t)blockIdx.x * PACK_THREADS + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * PACK_THREADS) >> 5;
   for (int64_t tile = gw; tile < T; tile += nw) {
     const int64_t v = tile * 32 + lane;
-    uint32_t run = 0;
+    const TileRows tr = tile_rows(off, n, v, small_max);
+    uint32_t run = 0;  // start of segment s within this lane's row
     for (int sg = 0; sg < S; ++sg) {
       const uint32_t c = v < n ? cnt8[(int64_t)sg * n + v] : 0;
-      rs[lane * S + sg] = run;
-      run += c;
       uint32_t incl = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      tp[lane * S + sg] = incl - c;
+      base[lane * S + sg] = toff[(int64_t)sg * T + tile] + (int64_t)(incl - c) - (int64_t)run - tr.excl;
+      run += c;
     }
     __syncwarp();
-    const TileRows tr = tile_rows(off, n, v, small_max);
     for (int jb = 0; jb < tr.total; jb += 32) {
       const int jv = jb + lane;
       int64_t pos;
@@ -519,9 +521,7 @@ __global__ void __launch_bounds__(PACK_THREADS) k_small_pack(const int64_t* __re
       const int r = arc_row(tr, jv, &pos, &ex);
       if (jv < tr.total) {
         const int32_t u = idx[pos];
-        const int sg = u >> wbits;
-        const int64_t k = (int64_t)(jv - ex) - rs[r * S + sg];
-        const int64_t dst = toff[(int64_t)sg * T + tile] + tp[r * S + sg] + k;
+        const int64_t dst = base[r * S + (u >> wbits)] + jv;
         packed[dst] = u;
         prow[dst] = (int32_t)(tile * 32 + r);
       }
