@@ -492,6 +492,10 @@ static gap_status build_from_device_edges(int64_t n, int64_t m, const int32_t* d
     graph_free(g);
     return st;
   }
+  // hand the builder's sort scratch back (trials keep their own scratch warm)
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  cudaGetLastError();
   *out = g;
   return GAP_OK;
 }

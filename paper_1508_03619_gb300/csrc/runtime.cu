@@ -30,8 +30,26 @@ gap_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
 
 static gap_allocator g_alloc = {nullptr, nullptr, nullptr};
 
+// The default stream-ordered pool returns freed memory to the driver at every
+// synchronization (release threshold 0), so each trial would map its scratch
+// afresh.  Keep freed scratch in the pool instead, like a host allocator
+// that keeps its heap; this is process-local state of this device's pool.
+static void keep_pool_warm() {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev == done_dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done_dev = dev;
+}
+
 void* scratch_alloc(size_t bytes, cudaStream_t s) {
   if (g_alloc.alloc) return g_alloc.alloc(bytes, (void*)s, g_alloc.ctx);
+  keep_pool_warm();
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
     cudaGetLastError();
