@@ -484,49 +484,56 @@ __global__ void __launch_bounds__(PACK_THREADS) k_small_count(const int64_t* __r
 }
 
 // Copy each small row's arcs to its segment-major positions, with the row id
-// of every arc beside it (COO order: rows ascending within a segment).
+// of every arc beside it (COO order: rows ascending within a segment).  Per
+// tile and segment, the destination range is contiguous, so the warp walks
+// it in order (coalesced writes); lane w finds its row by a shuffle binary
+// search over the in-tile prefix and reads the arc from that row's run (the
+// tile's few KB of CSC stay in L1 across the segments).
 __global__ void __launch_bounds__(PACK_THREADS) k_small_pack(const int64_t* __restrict__ off,
                                                               const int32_t* __restrict__ idx, int64_t n,
                                                               int64_t small_max, int S, int wbits,
                                                               const uint8_t* __restrict__ cnt8,
                                                               const int64_t* __restrict__ toff, int64_t T,
                                                               int32_t* __restrict__ packed, int32_t* __restrict__ prow) {
-  extern __shared__ uint32_t pack_sh[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // base[r*S + s] = destination of virtual arc 0 of row r in segment s, so an
-  // arc's destination is base + jv (jv = its virtual index in the tile)
-  int64_t* base = reinterpret_cast<int64_t*>(pack_sh) + warp * 32 * S;
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
   const int64_t gw = ((int64_t)blockIdx.x * PACK_THREADS + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * PACK_THREADS) >> 5;
   for (int64_t tile = gw; tile < T; tile += nw) {
     const int64_t v = tile * 32 + lane;
-    const TileRows tr = tile_rows(off, n, v, small_max);
-    uint32_t run = 0;  // start of segment s within this lane's row
+    const bool valid = v < n;
+    const int64_t rb = valid ? off[v] : 0;
+    const int64_t re = valid ? off[v + 1] : 0;
+    const bool small = valid && re - rb <= small_max;
+    int64_t run = rb;  // CSC position where this lane's row enters segment sg
     for (int sg = 0; sg < S; ++sg) {
-      const uint32_t c = v < n ? cnt8[(int64_t)sg * n + v] : 0;
-      uint32_t incl = c;
+      const int c = small ? (int)cnt8[(int64_t)sg * n + v] : 0;
+      int incl = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        const int y = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += y;
       }
-      base[lane * S + sg] = toff[(int64_t)sg * T + tile] + (int64_t)(incl - c) - (int64_t)run - tr.excl;
+      const int excl = incl - c;
+      const int total = __shfl_sync(FULL, incl, 31);
+      const int64_t dst0 = toff[(int64_t)sg * T + tile];
+      for (int wb = 0; wb < total; wb += 32) {
+        const int w = wb + lane;
+        int rr = 0;  // largest row with excl <= w
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = rr + step;
+          const int ex = __shfl_sync(FULL, excl, cand & 31);
+          if (cand < 32 && ex <= w) rr = cand;
+        }
+        const int64_t src = __shfl_sync(FULL, run, rr) + (w - __shfl_sync(FULL, excl, rr));
+        if (w < total) {
+          packed[dst0 + w] = idx[src];
+          prow[dst0 + w] = (int32_t)(tile * 32 + rr);
+        }
+      }
       run += c;
     }
-    __syncwarp();
-    for (int jb = 0; jb < tr.total; jb += 32) {
-      const int jv = jb + lane;
-      int64_t pos;
-      int ex;
-      const int r = arc_row(tr, jv, &pos, &ex);
-      if (jv < tr.total) {
-        const int32_t u = idx[pos];
-        const int64_t dst = base[r * S + (u >> wbits)] + jv;
-        packed[dst] = u;
-        prow[dst] = (int32_t)(tile * 32 + r);
-      }
-    }
-    __syncwarp();
   }
 }
 
@@ -909,6 +916,8 @@ __device__ __forceinline__ int bin_of(int64_t deg, const BinHi& t) {
 __global__ void __launch_bounds__(BN_THREADS) k_bin_count(const int64_t* __restrict__ off, int64_t n, BinHi t,
                                                            uint32_t* __restrict__ counts, int64_t tiles,
                                                            int64_t* __restrict__ bin_arcs) {
+  // warp-aggregated: one shared add per warp and bin (ballot + popcount, and a
+  // warp sum of the degrees), then one global add per block and bin
   __shared__ uint32_t h[NBINS];
   __shared__ unsigned long long ha[NBINS];
   if (threadIdx.x < NBINS) {
@@ -916,15 +925,27 @@ __global__ void __launch_bounds__(BN_THREADS) k_bin_count(const int64_t* __restr
     ha[threadIdx.x] = 0;
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * BN_TILE;
+  uint32_t my_cnt[NBINS] = {};
+  unsigned long long my_arcs[NBINS] = {};
 #pragma unroll
   for (int r = 0; r < BN_ITEMS; ++r) {
     const int64_t v = base + (int64_t)r * BN_THREADS + threadIdx.x;
-    if (v < n) {
-      const int64_t deg = off[v + 1] - off[v];
-      const int q = bin_of(deg, t);
-      atomicAdd(&h[q], 1u);
-      if (deg) atomicAdd(&ha[q], (unsigned long long)deg);
+    const int64_t deg = v < n ? off[v + 1] - off[v] : 0;
+    const int q = v < n ? bin_of(deg, t) : -1;
+#pragma unroll
+    for (int b = 0; b < NBINS; ++b) {
+      my_cnt[b] += __popc(__ballot_sync(0xffffffffu, q == b));
+      my_arcs[b] += q == b ? (unsigned long long)deg : 0ull;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NBINS; ++b) {
+    const unsigned long long a = warp_sum(my_arcs[b]);
+    if (lane == 0) {
+      if (my_cnt[b]) atomicAdd(&h[b], my_cnt[b]);
+      if (a) atomicAdd(&ha[b], a);
     }
   }
   __syncthreads();
@@ -1332,9 +1353,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     int wbits = 0;
     while ((int64_t(1) << wbits) < t.seg_width) ++wbits;
     const size_t count_smem = sizeof(uint32_t) * PACK_WARPS * 32 * S;
-    const size_t pack_smem = 2 * count_smem;
     GAP_CUDA(cudaFuncSetAttribute(k_small_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem));
-    GAP_CUDA(cudaFuncSetAttribute(k_small_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pack_smem));
     k_small_count<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, count_smem, s>>>(
         g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S, wbits, sm_cnt.as<uint8_t>(), sm_ttot.as<uint32_t>(), T);
     GAP_LAUNCH_CHECK();
@@ -1346,7 +1365,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
     GAP_TRY(sm_prow.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
     GAP_TRY(sm_tend.get(sizeof(int64_t) * S, s));
-    k_small_pack<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, pack_smem, s>>>(
+    k_small_pack<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, 0, s>>>(
         g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S, wbits, sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,
         sm_packed.as<int32_t>(), sm_prow.as<int32_t>());
     GAP_LAUNCH_CHECK();
