@@ -34,9 +34,9 @@ TOL = 1e-4
 MAX_ITERS = 100
 FALLBACK_HBM_GBS = 6800.0
 
-# ncu DRAM bytes per launch for the dominant kernel, from the committed profile
-# summary (profiles/); None until captured for the current kernel.
-NCU_TRAFFIC = {}
+# ncu DRAM bytes (read + write) per launch, from one capture of the launch list
+# (profiles/pull_segmented_kron26.md); only kernels unchanged since then.
+NCU_TRAFFIC = {"k_pull_group_seg<32>": 0.8855e9}
 
 
 def parse():

@@ -1302,7 +1302,10 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   GAP_LAUNCH_CHECK();
   int64_t mt[NBINS + 2];
   GAP_CUDA(cudaMemcpyAsync(mt, meta.p, sizeof(mt), cudaMemcpyDeviceToHost, s));
+  tm.end(GAP_PHASE_BIN, tok);
   GAP_CUDA(cudaStreamSynchronize(s));
+  tm.collect();
+  tok = tm.begin();
   const int64_t nhubs = mt[NBINS] - mt[BIN_HUB];
   int64_t nchunks = mt[NBINS + 1];
   // segmented rows are the tail of the list (bins are in degree order)
