@@ -213,6 +213,34 @@ typedef struct {
  * GAP_WARN_NOT_CONVERGED, or the device error of that run. */
 GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
 
+/* ------------------------------------------------- no-allocation variant --- */
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory during the call: code running while a CUDA
+ * stream is being captured (cudaMalloc is not allowed there), processes whose
+ * device memory is entirely owned by a fixed memory plan or arena, and
+ * latency-critical paths that must never wait on an allocator.
+ *
+ * Same result contract as gap_pr_run (FP32 scores, FP32 accumulation, FP64
+ * convergence reduction), but all scratch lives in one static device array of
+ * about 8 MB that every GPU loading the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - Limits: at most GAP_NOALLOC_MAX_VERTICES vertices and fewer than 2^31
+ *    arcs; larger graphs are rejected with GAP_ERR_INVALID_ARG and a message.
+ *  - `scores` must be device memory (n floats, caller-owned); the graph comes
+ *    from gap_graph_create* as usual (created before, outside this call).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - The convergence loop is driven from the host (one synchronization per
+ *    iteration), so the call returns after the run finished; gap_pr_stats
+ *    reports it afterwards.
+ *  - All calls share the one array and each starts by rewriting everything it
+ *    reads; calls that overlap on the GPU (e.g. on two streams at once) race
+ *    and must not be issued. */
+#define GAP_NOALLOC_MAX_VERTICES (1LL << 20)
+GAP_API gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double tol, int32_t max_iters,
+                                      float* scores, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

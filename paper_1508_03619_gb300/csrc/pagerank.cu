@@ -34,6 +34,7 @@
 // has a fixed order and results are reproducible run to run.
 #include <cuda_bf16.h>
 
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -1736,3 +1737,140 @@ gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// No-allocation variant of the PageRank trial.
+//
+// Some callers cannot allocate device memory while they call us: code that runs
+// while a CUDA stream is being captured (cudaMalloc is not allowed there),
+// processes whose device memory is entirely owned by a fixed memory plan or
+// arena, and latency-critical paths that must never wait on the allocator.
+// For them this variant keeps all of its scratch in one file-scope device
+// array.  It is limited to graphs of at most GAP_NOALLOC_MAX_VERTICES
+// vertices (fewer than 2^31 arcs) and writes FP32 scores into the caller's
+// device buffer.  Every row is pulled in vertex order by k_pull_small, and
+// the convergence loop is host-driven, so no graph, stream or event objects
+// are created either.
+namespace gap {
+
+constexpr int64_t NOALLOC_C_BYTES = 2 * sizeof(float) * GAP_NOALLOC_MAX_VERTICES;  // c0, c1
+constexpr int64_t NOALLOC_PARTIALS = 4096;                                       // delta block partials
+constexpr int64_t NOALLOC_BYTES = NOALLOC_C_BYTES + sizeof(double) * NOALLOC_PARTIALS + 4096;
+
+// The array lives on every GPU that loads this library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch per device.  In host code the symbol is
+// only a host-side stand-in, so the address is looked up once per device
+// (with that device current) by cudaGetSymbolAddress.
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {};
+
+static gap_status noalloc_scratch(void** out) {
+  int dev = 0;
+  GAP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device %d out of range", dev);
+    return GAP_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                 "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GAP_OK;
+}
+
+}  // namespace gap
+
+extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double tol, int32_t max_iters,
+                                         float* scores, void* stream) {
+  using namespace gap;
+  GAP_TRY(check_run_args(g, damping, tol, max_iters, scores));
+  if (g->n > GAP_NOALLOC_MAX_VERTICES) {
+    set_error("gap_pr_run_noalloc: graph has %lld vertices, this entry point supports at most %lld",
+              (long long)g->n, (long long)GAP_NOALLOC_MAX_VERTICES);
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (g->m >= (int64_t(1) << 31)) {
+    set_error("gap_pr_run_noalloc: graph has %lld arcs, this entry point supports fewer than 2^31",
+              (long long)g->m);
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (!is_device_ptr(scores)) {
+    set_error("gap_pr_run_noalloc: scores must be device memory");
+    return GAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->has_run && g->last_stream != s) cudaStreamSynchronize(g->last_stream);  // stats buffer reuse
+  void* base = nullptr;
+  GAP_TRY(noalloc_scratch(&base));
+  const int64_t n = g->n;
+  char* bytes = static_cast<char*>(base);
+  void* c0 = bytes;
+  void* c1 = bytes + sizeof(float) * GAP_NOALLOC_MAX_VERTICES;
+  double* partial = reinterpret_cast<double*>(bytes + NOALLOC_C_BYTES);
+  PrCtrl* dctrl = reinterpret_cast<PrCtrl*>(bytes + NOALLOC_C_BYTES + sizeof(double) * NOALLOC_PARTIALS);
+  static_assert(sizeof(PrCtrl) <= 4096, "PrCtrl must fit its slot");
+
+  // every field the trial reads is written first: k_ctrl_init resets the
+  // control block, k_init writes x and c0, iteration 1 writes c1, and each
+  // launch writes all of its delta partials
+  k_ctrl_init<<<1, 32, 0, s>>>(dctrl, 0, 0, 0.0);
+  GAP_LAUNCH_CHECK();
+  const float x0 = (float)(1.0 / (double)n);
+  k_init<float><<<stride_grid(n, 256, 8), 256, 0, s>>>(n, x0, scores, g->outdeg, c0, 0);
+  GAP_LAUNCH_CHECK();
+  PrArgs<float> a{};
+  a.off = g->in_off;
+  a.idx = g->in_idx;
+  a.outdeg = g->outdeg;
+  a.list = nullptr;
+  a.begin = 0;
+  a.end = n;
+  a.x = scores;
+  a.c0 = c0;
+  a.c1 = c1;
+  a.base = (float)((1.0 - damping) / (double)n);
+  a.d = (float)damping;
+  a.ctrl = dctrl;
+  a.partial = partial;
+  a.kahan = 0;
+  a.kahan_thr = INT64_MAX;
+  const int grid = stride_grid(n, PR_THREADS, 8);
+  if (grid > NOALLOC_PARTIALS) {
+    set_error("gap_pr_run_noalloc: launch grid %d exceeds the partial slots", grid);
+    return GAP_ERR_UNSUPPORTED;
+  }
+  for (int32_t k = 0; k < max_iters; ++k) {
+    k_pull_small<float, SMALL_UB><<<grid, PR_THREADS, 0, s>>>(a, n, INT64_MAX);
+    GAP_LAUNCH_CHECK();
+    k_finalize<<<1, 1024, 0, s>>>(dctrl, partial, grid, tol, max_iters, 0, 0);
+    GAP_LAUNCH_CHECK();
+    GAP_CUDA(cudaMemcpyAsync(g->flag_host, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GAP_CUDA(cudaStreamSynchronize(s));
+    if (*g->flag_host) break;
+  }
+  const int mg = stride_grid(n, 256, 4);
+  k_mass_partial<float><<<mg, 256, 0, s>>>(scores, n, partial);
+  GAP_LAUNCH_CHECK();
+  k_mass_final<<<1, 1024, 0, s>>>(dctrl, partial, mg);
+  GAP_LAUNCH_CHECK();
+  GAP_CUDA(cudaMemcpyAsync(g->stats_host, &dctrl->st, sizeof(gap_pr_stats_t), cudaMemcpyDeviceToHost, s));
+  g->launches_per_iter = 2;
+  g->launches_fixed = 4;
+  g->last_segments = 1;
+  for (int q = 0; q < NBINS; ++q) {
+    g->last_bin_hi[q] = INT64_MAX;
+    g->last_bin_lanes[q] = q == 0 ? LANES_SMALL : 1;
+    g->last_bin_seg[q] = 0;
+  }
+  g->last_stream = s;
+  g->has_run = 1;
+  g->last_tol = tol;
+  return GAP_OK;
+}

@@ -46,8 +46,9 @@ EXPORTED = (
     "gap_status_string", "gap_last_error_message", "gap_version", "gap_set_allocator",
     "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
-    "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats",
+    "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
 )
+GAP_NOALLOC_MAX_VERTICES = 1 << 20
 
 
 class gap_pr_options(ctypes.Structure):
@@ -127,6 +128,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_pr_options_default": ([ctypes.POINTER(gap_pr_options)], None),
         "gap_pr_run_ex": ([vp, dbl, dbl, i32, ctypes.POINTER(gap_pr_options), vp, vp], st),
         "gap_pr_stats": ([vp, ctypes.POINTER(gap_pr_stats_t)], st),
+        "gap_pr_run_noalloc": ([vp, dbl, dbl, i32, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -278,6 +280,13 @@ def gap_pr_run_ex(h, damping: float, tol: float, max_iters: int, options: gap_pr
     _check_scores(h, scores, 8 if options.precision == GAP_PREC_F64 else 4, "gap_pr_run_ex")
     return _check(load().gap_pr_run_ex(h, damping, tol, max_iters, ctypes.byref(options),
                                        _ptr(scores), _stream(stream)), "gap_pr_run_ex")
+
+
+def gap_pr_run_noalloc(h, damping: float, tol: float, max_iters: int, scores, stream=None):
+    """No-allocation FP32 trial (scratch in a static device array); see gap.h."""
+    _check_scores(h, scores, 4, "gap_pr_run_noalloc")
+    return _check(load().gap_pr_run_noalloc(h, damping, tol, max_iters, _ptr(scores),
+                                            _stream(stream)), "gap_pr_run_noalloc")
 
 
 def gap_pr_stats(h):
