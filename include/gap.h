@@ -213,6 +213,23 @@ typedef struct {
  * GAP_WARN_NOT_CONVERGED, or the device error of that run. */
 GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
 
+/* ------------------------------------------- personalized PageRank batch --- */
+/* Personalized PageRank (the serving workload; not in the paper): the §2.1
+ * equation with the teleport term (1-d)/|V| replaced by (1-d)/|S_j| on the
+ * seed set S_j of query j (repeated seeds count once), start x0 = 1/|S_j| on
+ * the seeds.  q queries: query j's seeds are seeds[seed_offsets[j] ..
+ * seed_offsets[j+1]-1] (host or device arrays; offsets int64[q+1], offsets[0]
+ * = 0).  Queries run as one multi-vector pull SpMM of up to 128 columns at a
+ * time; each query stops on its own (delta < tol or max_iters) and its result
+ * does not depend on the other queries in the batch.  scores: q x n FP32,
+ * query-major (query j's scores at scores + j*n), host or device.  stats
+ * (optional, q entries) receives per-query iterations, convergence and deltas.
+ * Blocks until done.  Errors: INVALID_ARG (bad offsets, seed outside [0,n),
+ * a query without seeds), OOM, CUDA. */
+GAP_API gap_status gap_ppr_batch(gap_graph_t* g, int32_t q, const int64_t* seed_offsets, const int32_t* seeds,
+                                 double damping, double tol, int32_t max_iters, float* scores,
+                                 gap_pr_stats_t* stats, void* stream);
+
 /* ------------------------------------------------- no-allocation variant --- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory during the call: code running while a CUDA

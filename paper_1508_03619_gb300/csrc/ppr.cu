@@ -1,0 +1,426 @@
+// ppr.cu — personalized PageRank for many queries at once, as a multi-vector
+// pull SpMM over the in-direction CSR (the serving workload; the paper's §2.1
+// PageRank equation with the teleport (1-d)/|V| replaced by (1-d)/|S_j| on the
+// seed set S_j of query column j).
+//
+// Layout: KP query columns (KP a power of two, 4..128), row-major [n][KP]
+// arrays for the contributions C (ping-pong) and the scores X, so every arc
+// gathers one coalesced KP-wide row C[u][*].  A per-vertex bitmask says which
+// columns have the vertex as a seed.
+//
+// Column independence: the arithmetic of column j — the sum over a row's arcs
+// in ascending order, x' = b + d*s, c' = x'/outdeg, and |x' - x| reduced over
+// fixed 256-row blocks in a fixed order — does not depend on KP, on the slot
+// j occupies, or on the other columns, so a query's result and its iteration
+// count are the same alone and in any mix.  A column that met its tolerance
+// (or max_iters) stops updating at once, like a run of its own would.
+#include <algorithm>
+#include <vector>
+
+#include "graph.cuh"
+#include "ppr.cuh"
+
+namespace gap {
+
+constexpr int PPR_ROWS = 32;        // rows per CTA round (one per row slot)
+constexpr int PPR_SUB = 8;          // rounds per delta block
+constexpr int PPR_BLOCK_ROWS = PPR_ROWS * PPR_SUB;  // 256 rows per delta partial
+constexpr int PPR_KMAX = 128;
+
+struct PprArgs {
+  const int64_t* __restrict__ off;
+  const int32_t* __restrict__ idx;
+  const int32_t* __restrict__ outdeg;
+  int64_t n;
+  int KP;
+  const float* cin;
+  float* cout;
+  float* x;
+  const uint32_t* __restrict__ seedmask;  // [n][KP/32 rounded up]
+  int mask_words;
+  const float* __restrict__ base;         // [KP] (1-d)/|S_j|
+  const int32_t* __restrict__ active;     // [KP] 1: column updates this iteration
+  float d;
+  double* partial;                        // [nblocks][KP]
+};
+
+// One CTA = 32 row slots x LR lanes; lane g of a row covers columns 4g..4g+3.
+template <int LR>
+__global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
+  __shared__ double sh[PPR_ROWS][PPR_KMAX];
+  const int g = threadIdx.x % LR;
+  const int r = threadIdx.x / LR;
+  const int col0 = 4 * g;
+  const int64_t nblocks = (a.n + PPR_BLOCK_ROWS - 1) / PPR_BLOCK_ROWS;
+  int act[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) act[q] = a.active[col0 + q];
+  float bq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bq[q] = a.base[col0 + q];
+  for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    double dacc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int sub = 0; sub < PPR_SUB; ++sub) {
+      const int64_t v = blk * PPR_BLOCK_ROWS + sub * PPR_ROWS + r;
+      if (v >= a.n) break;
+      const int64_t b = a.off[v], e = a.off[v + 1];
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int64_t j = b;
+      for (; j + 3 < e; j += 4) {
+        const int32_t u0 = __ldcs(a.idx + j), u1 = __ldcs(a.idx + j + 1), u2 = __ldcs(a.idx + j + 2),
+                      u3 = __ldcs(a.idx + j + 3);
+        const float4 c0 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u0 * a.KP + col0));
+        const float4 c1 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u1 * a.KP + col0));
+        const float4 c2 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u2 * a.KP + col0));
+        const float4 c3 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u3 * a.KP + col0));
+        s0 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s0, c0.x), c1.x), c2.x), c3.x);
+        s1 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s1, c0.y), c1.y), c2.y), c3.y);
+        s2 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s2, c0.z), c1.z), c2.z), c3.z);
+        s3 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s3, c0.w), c1.w), c2.w), c3.w);
+      }
+      for (; j < e; ++j) {
+        const float4 c = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)__ldcs(a.idx + j) * a.KP + col0));
+        s0 = __fadd_rn(s0, c.x);
+        s1 = __fadd_rn(s1, c.y);
+        s2 = __fadd_rn(s2, c.z);
+        s3 = __fadd_rn(s3, c.w);
+      }
+      const float sum[4] = {s0, s1, s2, s3};
+      const uint32_t mw = a.seedmask[v * a.mask_words + (col0 >> 5)];
+      const int deg = a.outdeg[v];
+      float* xr = a.x + v * a.KP + col0;
+      float* cr = a.cout + v * a.KP + col0;
+      const float4 xo4 = *reinterpret_cast<const float4*>(xr);
+      const float xo[4] = {xo4.x, xo4.y, xo4.z, xo4.w};
+      float xn[4], cn[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (act[q]) {
+          const float bb = (mw >> ((col0 + q) & 31)) & 1u ? bq[q] : 0.f;
+          xn[q] = __fadd_rn(bb, __fmul_rn(a.d, sum[q]));
+          const double dd = (double)xn[q] - (double)xo[q];
+          dacc[q] += dd < 0 ? -dd : dd;
+        } else {
+          xn[q] = xo[q];  // frozen column: keep its scores
+        }
+        cn[q] = deg > 0 ? xn[q] / (float)deg : 0.f;
+      }
+      *reinterpret_cast<float4*>(xr) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+      *reinterpret_cast<float4*>(cr) = make_float4(cn[0], cn[1], cn[2], cn[3]);
+    }
+    // per-column sum over the 32 row slots, in slot order
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sh[r][col0 + q] = dacc[q];
+    __syncthreads();
+    for (int c = threadIdx.x; c < a.KP; c += blockDim.x) {
+      double t = 0.0;
+      for (int rr = 0; rr < PPR_ROWS; ++rr) t += sh[rr][c];
+      a.partial[blk * a.KP + c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Two-level fixed-order reduction of the per-block partials: out[grp][c] =
+// sum of partial[grp*FAN + i][c] for i ascending.
+constexpr int PPR_FAN = 256;
+__global__ void k_ppr_reduce(const double* __restrict__ partial, int64_t nblocks, int KP, double* __restrict__ out) {
+  const int64_t grp = blockIdx.x;
+  for (int c = threadIdx.x; c < KP; c += blockDim.x) {
+    double t = 0.0;
+    const int64_t b0 = grp * PPR_FAN, b1 = std::min<int64_t>(b0 + PPR_FAN, nblocks);
+    for (int64_t bb = b0; bb < b1; ++bb) t += partial[bb * KP + c];
+    out[grp * KP + c] = t;
+  }
+}
+
+// Per column: delta, history, stop test; active flags for the next iteration.
+__global__ void k_ppr_finalize(PprCtrl* ctrl, const double* __restrict__ part2, int64_t ngrp, int KP, double tol,
+                               int32_t max_iters, cudaGraphConditionalHandle handle, int use_handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < KP; c += blockDim.x) {
+    PprColumn& col = ctrl->col[c];
+    if (!col.active) continue;
+    double t = 0.0;
+    for (int64_t gI = 0; gI < ngrp; ++gI) t += part2[gI * KP + c];
+    const int k = col.iterations;
+    if (k < GAP_PPR_HIST) col.delta_hist[k] = t;
+    col.final_delta = t;
+    col.iterations = k + 1;
+    col.converged = t < tol;
+    if (col.converged || col.iterations >= max_iters) {
+      col.active = 0;
+    } else {
+      atomicOr(&any, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctrl->step += 1;
+    ctrl->any_active = any;
+    if (use_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+  }
+  for (int c = threadIdx.x; c < KP; c += blockDim.x) ctrl->active[c] = ctrl->col[c].active;
+}
+
+// Column setup: x = t (1/|S| on the seeds), c = x/outdeg, seed bits, teleport.
+__global__ void k_ppr_clear_column(float* x, float* c0, float* c1, uint32_t* seedmask, int64_t n, int KP,
+                                   int mask_words, int col) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    x[v * KP + col] = 0.f;
+    c0[v * KP + col] = 0.f;
+    c1[v * KP + col] = 0.f;
+    atomicAnd(&seedmask[v * mask_words + (col >> 5)], ~(1u << (col & 31)));  // only this column's bit
+  }
+}
+
+__global__ void k_ppr_seed_column(float* x, float* c0, float* c1, uint32_t* seedmask, const int32_t* outdeg,
+                                  const int32_t* seeds, int32_t nseeds, float tval, int KP, int mask_words, int col) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nseeds; i += gridDim.x * blockDim.x) {
+    const int64_t v = seeds[i];
+    x[v * KP + col] = tval;
+    const int deg = outdeg[v];
+    const float cv = deg > 0 ? tval / (float)deg : 0.f;
+    c0[v * KP + col] = cv;
+    c1[v * KP + col] = cv;
+    atomicOr(&seedmask[v * mask_words + (col >> 5)], 1u << (col & 31));
+  }
+}
+
+// Gather column `col` of x into a contiguous n-vector.
+__global__ void k_ppr_extract(const float* __restrict__ x, int64_t n, int KP, int col, float* __restrict__ out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = x[v * KP + col];
+}
+
+__global__ void k_ppr_ctrl_column(PprCtrl* ctrl, int col, int active, float base) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    PprColumn& c = ctrl->col[col];
+    memset(&c, 0, sizeof(PprColumn));
+    c.active = active;
+    ctrl->active[col] = active;
+    ctrl->base[col] = base;
+    if (active) ctrl->any_active = 1;
+  }
+}
+
+__global__ void k_ppr_ctrl_init(PprCtrl* ctrl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) memset(ctrl, 0, sizeof(PprCtrl));
+}
+
+// ---- host side ----------------------------------------------------------------
+
+gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStream_t s) {
+  e->g = g;
+  e->KP = kp;
+  e->mask_words = (kp + 31) / 32;
+  e->d = d;
+  e->nblocks = (g->n + PPR_BLOCK_ROWS - 1) / PPR_BLOCK_ROWS;
+  e->ngrp = (e->nblocks + PPR_FAN - 1) / PPR_FAN;
+  const size_t cells = (size_t)g->n * kp;
+  GAP_TRY(e->xbuf.get(sizeof(float) * cells, s));
+  GAP_TRY(e->cbuf.get(2 * sizeof(float) * cells, s));
+  GAP_TRY(e->mask.get(sizeof(uint32_t) * g->n * e->mask_words, s));
+  GAP_TRY(e->part.get(sizeof(double) * e->nblocks * kp, s));
+  GAP_TRY(e->part2.get(sizeof(double) * e->ngrp * kp, s));
+  GAP_TRY(e->ctrl.get(sizeof(PprCtrl), s));
+  GAP_CUDA(cudaMemsetAsync(e->xbuf.p, 0, sizeof(float) * cells, s));
+  GAP_CUDA(cudaMemsetAsync(e->cbuf.p, 0, 2 * sizeof(float) * cells, s));
+  GAP_CUDA(cudaMemsetAsync(e->mask.p, 0, sizeof(uint32_t) * g->n * e->mask_words, s));
+  k_ppr_ctrl_init<<<1, 32, 0, s>>>(e->ctrl.as<PprCtrl>());
+  GAP_LAUNCH_CHECK();
+  return GAP_OK;
+}
+
+float* ppr_c(PprEngine* e, int which) {
+  return e->cbuf.as<float>() + (size_t)which * e->g->n * e->KP;
+}
+
+gap_status ppr_engine_set_column(PprEngine* e, int col, const int32_t* d_seeds, int32_t nseeds, int32_t distinct,
+                                 cudaStream_t s) {
+  const int64_t n = e->g->n;
+  float* x = e->xbuf.as<float>();
+  k_ppr_clear_column<<<stride_grid(n, 256, 4), 256, 0, s>>>(x, ppr_c(e, 0), ppr_c(e, 1), e->mask.as<uint32_t>(), n,
+                                                            e->KP, e->mask_words, col);
+  GAP_LAUNCH_CHECK();
+  const bool active = nseeds > 0;
+  const float tval = active ? (float)(1.0 / (double)distinct) : 0.f;
+  const float base = active ? (float)((1.0 - e->d) / (double)distinct) : 0.f;
+  if (active) {
+    k_ppr_seed_column<<<std::max(1, std::min(64, (nseeds + 255) / 256)), 256, 0, s>>>(
+        x, ppr_c(e, 0), ppr_c(e, 1), e->mask.as<uint32_t>(), e->g->outdeg, d_seeds, nseeds, tval, e->KP,
+        e->mask_words, col);
+    GAP_LAUNCH_CHECK();
+  }
+  k_ppr_ctrl_column<<<1, 32, 0, s>>>(e->ctrl.as<PprCtrl>(), col, active ? 1 : 0, base);
+  GAP_LAUNCH_CHECK();
+  return GAP_OK;
+}
+
+// One iteration over all KP columns (frozen columns only refresh c').
+gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStream_t s,
+                           cudaGraphConditionalHandle h, int use_h) {
+  PprArgs a;
+  a.off = e->g->in_off;
+  a.idx = e->g->in_idx;
+  a.outdeg = e->g->outdeg;
+  a.n = e->g->n;
+  a.KP = e->KP;
+  const int par = e->parity;
+  a.cin = ppr_c(e, par);
+  a.cout = ppr_c(e, par ^ 1);
+  a.x = e->xbuf.as<float>();
+  a.seedmask = e->mask.as<uint32_t>();
+  a.mask_words = e->mask_words;
+  PprCtrl* ctrl = e->ctrl.as<PprCtrl>();
+  a.base = ctrl->base;
+  a.active = ctrl->active;
+  a.d = (float)e->d;
+  a.partial = e->part.as<double>();
+  const int LR = e->KP / 4;
+  const int threads = PPR_ROWS * LR;
+  const int grid = (int)std::min<int64_t>(e->nblocks, (int64_t)device_info().sms * std::max(1, 2048 / threads));
+  switch (LR) {
+    case 1: k_ppr_spmm<1><<<grid, threads, 0, s>>>(a); break;
+    case 2: k_ppr_spmm<2><<<grid, threads, 0, s>>>(a); break;
+    case 4: k_ppr_spmm<4><<<grid, threads, 0, s>>>(a); break;
+    case 8: k_ppr_spmm<8><<<grid, threads, 0, s>>>(a); break;
+    case 16: k_ppr_spmm<16><<<grid, threads, 0, s>>>(a); break;
+    case 32: k_ppr_spmm<32><<<grid, threads, 0, s>>>(a); break;
+    default: set_error("bad column width %d", e->KP); return GAP_ERR_INVALID_ARG;
+  }
+  GAP_LAUNCH_CHECK();
+  k_ppr_reduce<<<(unsigned)e->ngrp, 128, 0, s>>>(e->part.as<double>(), e->nblocks, e->KP, e->part2.as<double>());
+  GAP_LAUNCH_CHECK();
+  k_ppr_finalize<<<1, 128, 0, s>>>(ctrl, e->part2.as<double>(), e->ngrp, e->KP, tol, max_iters, h, use_h);
+  GAP_LAUNCH_CHECK();
+  e->parity ^= 1;
+  return GAP_OK;
+}
+
+gap_status ppr_engine_extract(PprEngine* e, int col, float* out, cudaStream_t s) {
+  k_ppr_extract<<<stride_grid(e->g->n, 256, 4), 256, 0, s>>>(e->xbuf.as<float>(), e->g->n, e->KP, col, out);
+  GAP_LAUNCH_CHECK();
+  return GAP_OK;
+}
+
+int ppr_width_for(int q) {
+  int kp = 4;
+  while (kp < q && kp < PPR_KMAX) kp *= 2;
+  return kp;
+}
+
+}  // namespace gap
+
+using namespace gap;
+
+extern "C" gap_status gap_ppr_batch(gap_graph_t* g, int32_t q, const int64_t* seed_offsets, const int32_t* seeds,
+                                    double damping, double tol, int32_t max_iters, float* scores,
+                                    gap_pr_stats_t* stats, void* stream) {
+  clear_error();
+  if (!g || q < 0 || (q > 0 && (!seed_offsets || !scores))) {
+    set_error("gap_ppr_batch: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (!(damping >= 0.0 && damping <= 1.0) || !(tol >= 0.0) || max_iters < 0) {
+    set_error("gap_ppr_batch: bad damping/tol/max_iters");
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (q == 0) return GAP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = g->n;
+  // host copies of the seed lists (validated; distinct seeds counted)
+  std::vector<int64_t> so(q + 1);
+  GAP_CUDA(cudaMemcpy(so.data(), seed_offsets, sizeof(int64_t) * (q + 1), cudaMemcpyDefault));
+  if (so[0] != 0) {
+    set_error("gap_ppr_batch: seed_offsets[0] must be 0");
+    return GAP_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < q; ++i)
+    if (so[i + 1] < so[i]) {
+      set_error("gap_ppr_batch: seed_offsets not monotone");
+      return GAP_ERR_INVALID_ARG;
+    }
+  const int64_t total = so[q];
+  std::vector<int32_t> sd(total > 0 ? total : 1);
+  if (total > 0) GAP_CUDA(cudaMemcpy(sd.data(), seeds, sizeof(int32_t) * total, cudaMemcpyDefault));
+  std::vector<int32_t> distinct(q, 0);
+  for (int i = 0; i < q; ++i) {
+    std::vector<int32_t> t(sd.begin() + so[i], sd.begin() + so[i + 1]);
+    for (int32_t v : t)
+      if (v < 0 || v >= n) {
+        set_error("gap_ppr_batch: seed %d outside [0, %lld)", v, (long long)n);
+        return GAP_ERR_INVALID_ARG;
+      }
+    std::sort(t.begin(), t.end());
+    distinct[i] = (int32_t)(std::unique(t.begin(), t.end()) - t.begin());
+    if (distinct[i] == 0) {
+      set_error("gap_ppr_batch: query %d has no seeds", i);
+      return GAP_ERR_INVALID_ARG;
+    }
+  }
+  Scratch dseeds;
+  GAP_TRY(dseeds.get(sizeof(int32_t) * (total > 0 ? total : 1), s));
+  GAP_CUDA(cudaMemcpyAsync(dseeds.p, sd.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, s));
+  const bool out_dev = is_device_ptr(scores);
+  for (int q0 = 0; q0 < q; q0 += PPR_KMAX) {
+    const int cnt = std::min(PPR_KMAX, q - q0);
+    PprEngine e;
+    GAP_TRY(ppr_engine_init(&e, g, ppr_width_for(cnt), damping, s));
+    for (int i = 0; i < cnt; ++i)
+      GAP_TRY(ppr_engine_set_column(&e, i, dseeds.as<int32_t>() + so[q0 + i], (int32_t)(so[q0 + i + 1] - so[q0 + i]),
+                                    distinct[q0 + i], s));
+    PprCtrl* hctrl = nullptr;
+    GAP_CUDA(cudaMallocHost(&hctrl, sizeof(PprCtrl)));
+    gap_status st = GAP_OK;
+    for (int32_t k = 0; k < max_iters && st == GAP_OK; ++k) {
+      st = ppr_engine_step(&e, tol, max_iters, s, 0, 0);
+      if (st != GAP_OK) break;
+      if (cudaMemcpyAsync(&hctrl->any_active, &e.ctrl.as<PprCtrl>()->any_active, sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError(), "ppr loop", __FILE__, __LINE__);
+        break;
+      }
+      if (!hctrl->any_active) break;
+    }
+    if (st == GAP_OK) {
+      Scratch col;
+      if (!out_dev) st = col.get(sizeof(float) * n, s);
+      for (int i = 0; i < cnt && st == GAP_OK; ++i) {
+        float* dst = out_dev ? scores + (size_t)(q0 + i) * n : col.as<float>();
+        st = ppr_engine_extract(&e, i, dst, s);
+        if (st == GAP_OK && !out_dev) {
+          if (cudaMemcpyAsync(scores + (size_t)(q0 + i) * n, dst, sizeof(float) * n, cudaMemcpyDefault, s) !=
+              cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "ppr output copy", __FILE__, __LINE__);
+          if (st == GAP_OK && cudaStreamSynchronize(s) != cudaSuccess) st = GAP_ERR_CUDA;
+        }
+      }
+      if (st == GAP_OK && stats) {
+        if (cudaMemcpyAsync(hctrl, e.ctrl.p, sizeof(PprCtrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          st = GAP_ERR_CUDA;
+        } else {
+          for (int i = 0; i < cnt; ++i) {
+            gap_pr_stats_t& o = stats[q0 + i];
+            memset(&o, 0, sizeof(o));
+            const PprColumn& c = hctrl->col[i];
+            o.iterations = c.iterations;
+            o.converged = c.converged;
+            o.final_delta = c.final_delta;
+            const int kk = std::min(c.iterations, GAP_PPR_HIST);
+            for (int t = 0; t < kk && t < GAP_PR_HIST; ++t) o.delta_hist[t] = c.delta_hist[t];
+          }
+        }
+      }
+    }
+    cudaFreeHost(hctrl);
+    cudaStreamSynchronize(s);
+    if (st != GAP_OK) return st;
+  }
+  GAP_CUDA(cudaStreamSynchronize(s));
+  return GAP_OK;
+}

@@ -1,0 +1,49 @@
+// ppr.cuh — the multi-column personalized-PageRank engine shared by the batch
+// entry point (ppr.cu) and the continuous-batching server (server.cu).
+#pragma once
+
+#include "graph.cuh"
+
+namespace gap {
+
+constexpr int GAP_PPR_HIST = 64;
+constexpr int PPR_COLS_MAX = 128;
+
+struct PprColumn {
+  int32_t active;      // updates in the next iteration
+  int32_t iterations;  // iterations this column has run
+  int32_t converged;
+  int32_t pad;
+  double final_delta;
+  double delta_hist[GAP_PPR_HIST];
+};
+
+struct PprCtrl {
+  int32_t step;        // iterations run by the engine
+  int32_t any_active;  // some column still iterating
+  int32_t active[PPR_COLS_MAX];
+  float base[PPR_COLS_MAX];  // (1-d)/|S_j|
+  PprColumn col[PPR_COLS_MAX];
+};
+
+// Device state of KP query columns over one graph (all scratch owned here).
+struct PprEngine {
+  gap_graph* g = nullptr;
+  int KP = 0;
+  int mask_words = 1;
+  double d = 0.85;
+  int64_t nblocks = 0, ngrp = 0;
+  int parity = 0;
+  Scratch xbuf, cbuf, mask, part, part2, ctrl;
+};
+
+gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStream_t s);
+// (Re)start column `col` with the given device seed list (nseeds > 0) or clear it (nseeds == 0).
+gap_status ppr_engine_set_column(PprEngine* e, int col, const int32_t* d_seeds, int32_t nseeds, int32_t distinct,
+                                 cudaStream_t s);
+gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStream_t s,
+                           cudaGraphConditionalHandle h, int use_h);
+gap_status ppr_engine_extract(PprEngine* e, int col, float* out, cudaStream_t s);
+int ppr_width_for(int q);
+
+}  // namespace gap

@@ -47,6 +47,7 @@ EXPORTED = (
     "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
+    "gap_ppr_batch",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_pr_run_ex": ([vp, dbl, dbl, i32, ctypes.POINTER(gap_pr_options), vp, vp], st),
         "gap_pr_stats": ([vp, ctypes.POINTER(gap_pr_stats_t)], st),
         "gap_pr_run_noalloc": ([vp, dbl, dbl, i32, vp, vp], st),
+        "gap_ppr_batch": ([vp, i32, vp, vp, dbl, dbl, i32, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -287,6 +289,22 @@ def gap_pr_run_noalloc(h, damping: float, tol: float, max_iters: int, scores, st
     _check_scores(h, scores, 4, "gap_pr_run_noalloc")
     return _check(load().gap_pr_run_noalloc(h, damping, tol, max_iters, _ptr(scores),
                                             _stream(stream)), "gap_pr_run_noalloc")
+
+
+def gap_ppr_batch(h, seed_offsets, seeds, damping: float, tol: float, max_iters: int, scores,
+                  stats=True, stream=None):
+    """Personalized PageRank for q = len(seed_offsets)-1 queries (see gap.h).
+    Returns the list of per-query stats dicts when `stats`."""
+    q = len(seed_offsets) - 1
+    n = gap_graph_info(h)[0]
+    _check_scores(h, scores, 4, "gap_ppr_batch")
+    numel = scores.numel() if hasattr(scores, "numel") else getattr(scores, "size", None)
+    if numel is not None and numel < q * n:
+        raise ValueError(f"gap_ppr_batch: scores holds {numel} floats, need {q * n}")
+    st = (gap_pr_stats_t * max(q, 1))() if stats else None
+    _check(load().gap_ppr_batch(h, q, _ptr(seed_offsets), _ptr(seeds), damping, tol, max_iters,
+                                _ptr(scores), st, _stream(stream)), "gap_ppr_batch")
+    return [st[i].to_dict() for i in range(q)] if stats else None
 
 
 def gap_pr_stats(h):
