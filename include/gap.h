@@ -230,6 +230,41 @@ GAP_API gap_status gap_ppr_batch(gap_graph_t* g, int32_t q, const int64_t* seed_
                                  double damping, double tol, int32_t max_iters, float* scores,
                                  gap_pr_stats_t* stats, void* stream);
 
+/* -------------------------------------- continuous-batching PPR serving --- */
+/* A server runs personalized-PageRank queries over one device-resident graph as
+ * they arrive: a worker thread iterates a multi-column PPR engine (same
+ * arithmetic as gap_ppr_batch), admits waiting queries into free columns
+ * between iterations, and retires each column as soon as its own delta meets
+ * tol (or max_iters), copying its scores out.  The column count is the
+ * largest power of two <= max_cols (<= 128) whose buffers fit in the free HBM
+ * minus hbm_reserve; creation fails with GAP_ERR_OOM if even 4 columns do not
+ * fit.  A query's result does not depend on the other queries in flight. */
+typedef struct gap_ppr_server gap_ppr_server_t;
+typedef struct {
+  int32_t iterations;
+  int32_t converged;
+  double final_delta;
+  double latency_ms; /* submit to scores written, host clock */
+  int32_t column;    /* column it ran in */
+  int32_t pad;
+} gap_ppr_query_info_t;
+
+GAP_API gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_reserve, double damping,
+                                         double tol, int32_t max_iters, gap_ppr_server_t** out);
+/* Queue a query: seeds (host, 1..4096 ids in [0,n), copied), out = n FP32
+ * scores (host or device, caller-owned, written when the query completes). */
+GAP_API gap_status gap_ppr_submit(gap_ppr_server_t* s, const int32_t* seeds, int32_t nseeds, float* out,
+                                  int64_t* ticket);
+/* Non-blocking: *done = 1 once out holds the scores (info filled then). */
+GAP_API gap_status gap_ppr_poll(gap_ppr_server_t* s, int64_t ticket, int32_t* done, gap_ppr_query_info_t* info);
+/* Block until the query completed. */
+GAP_API gap_status gap_ppr_wait(gap_ppr_server_t* s, int64_t ticket, gap_ppr_query_info_t* info);
+/* Columns, completed queries, engine iterations so far, queries waiting. */
+GAP_API gap_status gap_ppr_server_info(gap_ppr_server_t* s, int32_t* columns, int64_t* completed, int64_t* steps,
+                                       int32_t* waiting);
+/* Stop the worker (queries not yet completed are abandoned) and free everything. */
+GAP_API void gap_ppr_server_destroy(gap_ppr_server_t* s);
+
 /* ------------------------------------------------- no-allocation variant --- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory during the call: code running while a CUDA

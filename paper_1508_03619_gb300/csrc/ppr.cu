@@ -239,12 +239,14 @@ float* ppr_c(PprEngine* e, int which) {
 }
 
 gap_status ppr_engine_set_column(PprEngine* e, int col, const int32_t* d_seeds, int32_t nseeds, int32_t distinct,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool clear) {
   const int64_t n = e->g->n;
   float* x = e->xbuf.as<float>();
-  k_ppr_clear_column<<<stride_grid(n, 256, 4), 256, 0, s>>>(x, ppr_c(e, 0), ppr_c(e, 1), e->mask.as<uint32_t>(), n,
-                                                            e->KP, e->mask_words, col);
-  GAP_LAUNCH_CHECK();
+  if (clear) {
+    k_ppr_clear_column<<<stride_grid(n, 256, 4), 256, 0, s>>>(x, ppr_c(e, 0), ppr_c(e, 1), e->mask.as<uint32_t>(), n,
+                                                              e->KP, e->mask_words, col);
+    GAP_LAUNCH_CHECK();
+  }
   const bool active = nseeds > 0;
   const float tval = active ? (float)(1.0 / (double)distinct) : 0.f;
   const float base = active ? (float)((1.0 - e->d) / (double)distinct) : 0.f;

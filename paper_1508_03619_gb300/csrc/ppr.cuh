@@ -40,7 +40,7 @@ struct PprEngine {
 gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStream_t s);
 // (Re)start column `col` with the given device seed list (nseeds > 0) or clear it (nseeds == 0).
 gap_status ppr_engine_set_column(PprEngine* e, int col, const int32_t* d_seeds, int32_t nseeds, int32_t distinct,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool clear = true);
 gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStream_t s,
                            cudaGraphConditionalHandle h, int use_h);
 gap_status ppr_engine_extract(PprEngine* e, int col, float* out, cudaStream_t s);

@@ -1,0 +1,357 @@
+// server.cu — continuous-batching personalized-PageRank server over a
+// device-resident graph.  Queries arrive at any time (gap_ppr_submit); a
+// worker thread runs the multi-column PPR engine one iteration at a time,
+// admits waiting queries into free columns between iterations, and retires
+// each column as soon as its own delta meets the tolerance (or max_iters),
+// copying its scores out.  The number of columns is chosen at creation from
+// the free HBM (minus a caller-given reserve).  Because a column's arithmetic
+// does not depend on its slot or on the other columns (see ppr.cu), a query's
+// result is the same whether it ran alone or in a busy mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "graph.cuh"
+#include "ppr.cuh"
+
+namespace gap {
+
+constexpr int32_t SERVER_MAX_SEEDS = 4096;
+
+struct Request {
+  int64_t ticket = 0;
+  std::vector<int32_t> seeds;
+  int32_t distinct = 0;
+  float* out = nullptr;
+  bool out_dev = false;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  int32_t done = 0;
+  gap_ppr_query_info_t info{};
+};
+
+// Clear the listed columns (x and both contribution buffers) and their seed bits.
+__global__ void k_srv_clear(float* x, float* c0, float* c1, uint32_t* mask, int64_t n, int KP, int mask_words,
+                            const int32_t* cols, int ncols) {
+  const int64_t total = n * ncols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t / ncols;
+    const int c = cols[t % ncols];
+    const int64_t cell = v * KP + c;
+    x[cell] = 0.f;
+    c0[cell] = 0.f;
+    c1[cell] = 0.f;
+    atomicAnd(&mask[v * mask_words + (c >> 5)], ~(1u << (c & 31)));
+  }
+}
+
+}  // namespace gap
+
+struct gap_ppr_server {
+  gap_graph* g = nullptr;
+  double d = 0.85, tol = 1e-4;
+  int32_t max_iters = 100;
+  int32_t cols = 0;
+  gap::PprEngine eng;
+  cudaStream_t s = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  gap_status worker_status = GAP_OK;
+  std::deque<gap::Request*> pending;
+  std::unordered_map<int64_t, gap::Request*> all;
+  std::vector<gap::Request*> slot;  // per column, or nullptr
+  int64_t next_ticket = 1;
+  int64_t completed = 0, steps = 0;
+  int32_t* seed_dev = nullptr;       // per column SERVER_MAX_SEEDS seeds
+  int32_t* cols_dev = nullptr;       // columns to clear
+  float* stage = nullptr;            // n floats for host outputs
+  gap::PprCtrl* hctrl = nullptr;     // pinned mirror of the control block
+};
+
+namespace gap {
+
+static gap_status srv_admit(gap_ppr_server* S) {
+  // caller holds S->mu; fills free columns with waiting queries
+  std::vector<int32_t> newcols;
+  std::vector<Request*> newreq;
+  for (int c = 0; c < S->cols && !S->pending.empty(); ++c) {
+    if (S->slot[c]) continue;
+    Request* r = S->pending.front();
+    S->pending.pop_front();
+    S->slot[c] = r;
+    newcols.push_back(c);
+    newreq.push_back(r);
+  }
+  if (newcols.empty()) return GAP_OK;
+  GAP_CUDA(cudaMemcpyAsync(S->cols_dev, newcols.data(), sizeof(int32_t) * newcols.size(), cudaMemcpyHostToDevice, S->s));
+  const int64_t n = S->g->n;
+  k_srv_clear<<<stride_grid(n * (int64_t)newcols.size(), 256, 8), 256, 0, S->s>>>(
+      S->eng.xbuf.as<float>(), S->eng.cbuf.as<float>(), S->eng.cbuf.as<float>() + (size_t)n * S->eng.KP,
+      S->eng.mask.as<uint32_t>(), n, S->eng.KP, S->eng.mask_words, S->cols_dev, (int)newcols.size());
+  GAP_LAUNCH_CHECK();
+  for (size_t i = 0; i < newcols.size(); ++i) {
+    Request* r = newreq[i];
+    int32_t* sd = S->seed_dev + (size_t)newcols[i] * SERVER_MAX_SEEDS;
+    GAP_CUDA(cudaMemcpyAsync(sd, r->seeds.data(), sizeof(int32_t) * r->seeds.size(), cudaMemcpyHostToDevice, S->s));
+    GAP_TRY(ppr_engine_set_column(&S->eng, newcols[i], sd, (int32_t)r->seeds.size(), r->distinct, S->s,
+                                  /*clear=*/false));
+  }
+  // host seed vectors must stay alive until the copies ran
+  GAP_CUDA(cudaStreamSynchronize(S->s));
+  return GAP_OK;
+}
+
+static gap_status srv_retire(gap_ppr_server* S) {
+  // after a step: columns that stopped are copied out and freed
+  GAP_CUDA(cudaMemcpyAsync(S->hctrl, S->eng.ctrl.p, sizeof(PprCtrl), cudaMemcpyDeviceToHost, S->s));
+  GAP_CUDA(cudaStreamSynchronize(S->s));
+  const int64_t n = S->g->n;
+  for (int c = 0; c < S->cols; ++c) {
+    Request* r = S->slot[c];
+    if (!r || S->hctrl->col[c].active) continue;
+    float* dst = r->out_dev ? r->out : S->stage;
+    GAP_TRY(ppr_engine_extract(&S->eng, c, dst, S->s));
+    if (!r->out_dev) GAP_CUDA(cudaMemcpyAsync(r->out, S->stage, sizeof(float) * n, cudaMemcpyDefault, S->s));
+    GAP_CUDA(cudaStreamSynchronize(S->s));
+    const PprColumn& col = S->hctrl->col[c];
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->t_done = std::chrono::steady_clock::now();
+    r->info.iterations = col.iterations;
+    r->info.converged = col.converged;
+    r->info.final_delta = col.final_delta;
+    r->info.latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    r->info.column = c;
+    r->done = 1;
+    S->slot[c] = nullptr;
+    ++S->completed;
+  }
+  S->cv_done.notify_all();
+  return GAP_OK;
+}
+
+static void srv_loop(gap_ppr_server* S) {
+  cudaSetDevice(S->g->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      auto busy = [&] {
+        for (Request* r : S->slot)
+          if (r) return true;
+        return false;
+      };
+      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || busy(); });
+      if (S->stop) return;
+      gap_status st = srv_admit(S);
+      if (st != GAP_OK) {
+        S->worker_status = st;
+        S->stop = true;
+        S->cv_done.notify_all();
+        return;
+      }
+    }
+    gap_status st = ppr_engine_step(&S->eng, S->tol, S->max_iters, S->s, 0, 0);
+    if (st == GAP_OK) st = srv_retire(S);
+    if (st != GAP_OK) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->worker_status = st;
+      S->stop = true;
+      S->cv_done.notify_all();
+      return;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    ++S->steps;
+  }
+}
+
+static void srv_free(gap_ppr_server* S) {
+  if (S->s) cudaStreamSynchronize(S->s);
+  cudaFree(S->seed_dev);
+  cudaFree(S->cols_dev);
+  cudaFree(S->stage);
+  if (S->hctrl) cudaFreeHost(S->hctrl);
+  for (auto& kv : S->all) delete kv.second;
+  S->all.clear();
+  // the engine's scratch is released on its stream by its destructors
+  S->eng.xbuf.release();
+  S->eng.cbuf.release();
+  S->eng.mask.release();
+  S->eng.part.release();
+  S->eng.part2.release();
+  S->eng.ctrl.release();
+  if (S->s) {
+    cudaStreamSynchronize(S->s);
+    cudaStreamDestroy(S->s);
+  }
+  delete S;
+}
+
+}  // namespace gap
+
+using namespace gap;
+
+extern "C" {
+
+gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_reserve, double damping, double tol,
+                                 int32_t max_iters, gap_ppr_server_t** out) {
+  clear_error();
+  if (!g || !out || max_cols < 1 || max_cols > PPR_COLS_MAX || !(damping >= 0 && damping <= 1) || !(tol >= 0) ||
+      max_iters < 1) {
+    set_error("gap_ppr_server_create: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  GAP_CUDA(cudaSetDevice(g->device));
+  // admission by free HBM: the widest power-of-two column count that fits
+  size_t free_b = 0, total_b = 0;
+  GAP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  int kp = ppr_width_for(max_cols);
+  auto need = [&](int k) {
+    const double cells = (double)g->n * k;
+    return cells * 12.0 + (double)g->n * 4.0 * ((k + 31) / 32) + (double)g->n * 4.0 + (double)k * SERVER_MAX_SEEDS * 4.0 +
+           (double)((g->n + 255) / 256) * k * 8.0 + (64 << 20);
+  };
+  while (kp > 4 && need(kp) + (double)hbm_reserve > (double)free_b) kp /= 2;
+  if (need(kp) + (double)hbm_reserve > (double)free_b) {
+    set_error("gap_ppr_server_create: not enough free HBM (%zu free, %zu reserved)", free_b, hbm_reserve);
+    return GAP_ERR_OOM;
+  }
+  gap_ppr_server* S = new gap_ppr_server();
+  S->g = g;
+  S->d = damping;
+  S->tol = tol;
+  S->max_iters = max_iters;
+  S->cols = std::min<int32_t>(max_cols, kp);
+  gap_status st = GAP_OK;
+  do {
+    if (cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking) != cudaSuccess) { st = GAP_ERR_CUDA; break; }
+    if ((st = ppr_engine_init(&S->eng, g, kp, damping, S->s)) != GAP_OK) break;
+    if (cudaMalloc(&S->seed_dev, sizeof(int32_t) * SERVER_MAX_SEEDS * kp) != cudaSuccess ||
+        cudaMalloc(&S->cols_dev, sizeof(int32_t) * kp) != cudaSuccess ||
+        cudaMalloc(&S->stage, sizeof(float) * g->n) != cudaSuccess ||
+        cudaMallocHost(&S->hctrl, sizeof(PprCtrl)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("gap_ppr_server_create: allocation failed");
+      st = GAP_ERR_OOM;
+      break;
+    }
+    if (cudaStreamSynchronize(S->s) != cudaSuccess) { st = GAP_ERR_CUDA; break; }
+  } while (0);
+  if (st != GAP_OK) {
+    srv_free(S);
+    return st;
+  }
+  S->slot.assign(S->cols, nullptr);
+  S->worker = std::thread(srv_loop, S);
+  *out = S;
+  return GAP_OK;
+}
+
+gap_status gap_ppr_server_info(gap_ppr_server_t* S, int32_t* columns, int64_t* completed, int64_t* steps,
+                               int32_t* waiting) {
+  clear_error();
+  if (!S) {
+    set_error("server is NULL");
+    return GAP_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (columns) *columns = S->cols;
+  if (completed) *completed = S->completed;
+  if (steps) *steps = S->steps;
+  if (waiting) *waiting = (int32_t)S->pending.size();
+  return S->worker_status;
+}
+
+gap_status gap_ppr_submit(gap_ppr_server_t* S, const int32_t* seeds, int32_t nseeds, float* out, int64_t* ticket) {
+  clear_error();
+  if (!S || !seeds || !out || !ticket || nseeds < 1 || nseeds > SERVER_MAX_SEEDS) {
+    set_error("gap_ppr_submit: bad argument (1 <= nseeds <= %d)", SERVER_MAX_SEEDS);
+    return GAP_ERR_INVALID_ARG;
+  }
+  Request* r = new Request();
+  r->seeds.assign(seeds, seeds + nseeds);
+  for (int32_t v : r->seeds)
+    if (v < 0 || v >= S->g->n) {
+      delete r;
+      set_error("gap_ppr_submit: seed %d outside [0, %lld)", v, (long long)S->g->n);
+      return GAP_ERR_INVALID_ARG;
+    }
+  std::vector<int32_t> t = r->seeds;
+  std::sort(t.begin(), t.end());
+  r->distinct = (int32_t)(std::unique(t.begin(), t.end()) - t.begin());
+  r->out = out;
+  r->out_dev = is_device_ptr(out);
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->worker_status != GAP_OK) {
+      delete r;
+      set_error("gap_ppr_submit: the server stopped after an error");
+      return S->worker_status;
+    }
+    r->ticket = S->next_ticket++;
+    S->all[r->ticket] = r;
+    S->pending.push_back(r);
+  }
+  S->cv_work.notify_one();
+  *ticket = r->ticket;
+  return GAP_OK;
+}
+
+static gap_status lookup(gap_ppr_server_t* S, int64_t ticket, Request** r) {
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) {
+    set_error("unknown ticket %lld", (long long)ticket);
+    return GAP_ERR_INVALID_ARG;
+  }
+  *r = it->second;
+  return GAP_OK;
+}
+
+gap_status gap_ppr_poll(gap_ppr_server_t* S, int64_t ticket, int32_t* done, gap_ppr_query_info_t* info) {
+  clear_error();
+  if (!S || !done) {
+    set_error("gap_ppr_poll: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  Request* r = nullptr;
+  GAP_TRY(lookup(S, ticket, &r));
+  *done = r->done;
+  if (r->done && info) *info = r->info;
+  if (!r->done && S->worker_status != GAP_OK) return S->worker_status;
+  return GAP_OK;
+}
+
+gap_status gap_ppr_wait(gap_ppr_server_t* S, int64_t ticket, gap_ppr_query_info_t* info) {
+  clear_error();
+  if (!S) {
+    set_error("gap_ppr_wait: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  Request* r = nullptr;
+  GAP_TRY(lookup(S, ticket, &r));
+  S->cv_done.wait(lk, [&] { return r->done || S->worker_status != GAP_OK; });
+  if (!r->done) return S->worker_status;
+  if (info) *info = r->info;
+  return GAP_OK;
+}
+
+void gap_ppr_server_destroy(gap_ppr_server_t* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  srv_free(S);
+}
+
+}  // extern "C"

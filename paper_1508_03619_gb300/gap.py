@@ -47,7 +47,8 @@ EXPORTED = (
     "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
-    "gap_ppr_batch",
+    "gap_ppr_batch", "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
+    "gap_ppr_server_info", "gap_ppr_server_destroy",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 
@@ -86,6 +87,16 @@ class gap_pr_stats_t(ctypes.Structure):
                 "phase_ms": dict(zip(PHASE_NAMES, self.phase_ms)),
                 "phase_launches": dict(zip(PHASE_NAMES, self.phase_launches)),
                 "kernel_launches": self.kernel_launches}
+
+
+class gap_ppr_query_info_t(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("final_delta", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("column", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {"iterations": self.iterations, "converged": bool(self.converged),
+                "final_delta": self.final_delta, "latency_ms": self.latency_ms, "column": self.column}
 
 
 class GapError(RuntimeError):
@@ -131,6 +142,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_pr_stats": ([vp, ctypes.POINTER(gap_pr_stats_t)], st),
         "gap_pr_run_noalloc": ([vp, dbl, dbl, i32, vp, vp], st),
         "gap_ppr_batch": ([vp, i32, vp, vp, dbl, dbl, i32, vp, vp, vp], st),
+        "gap_ppr_server_create": ([vp, i32, ctypes.c_size_t, dbl, dbl, i32, ctypes.POINTER(vp)], st),
+        "gap_ppr_submit": ([vp, vp, i32, vp, ctypes.POINTER(i64)], st),
+        "gap_ppr_poll": ([vp, i64, ctypes.POINTER(i32), ctypes.POINTER(gap_ppr_query_info_t)], st),
+        "gap_ppr_wait": ([vp, i64, ctypes.POINTER(gap_ppr_query_info_t)], st),
+        "gap_ppr_server_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                 ctypes.POINTER(i32)], st),
+        "gap_ppr_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -305,6 +323,58 @@ def gap_ppr_batch(h, seed_offsets, seeds, damping: float, tol: float, max_iters:
     _check(load().gap_ppr_batch(h, q, _ptr(seed_offsets), _ptr(seeds), damping, tol, max_iters,
                                 _ptr(scores), st, _stream(stream)), "gap_ppr_batch")
     return [st[i].to_dict() for i in range(q)] if stats else None
+
+
+class PprServer:
+    """Continuous-batching PPR server (gap_ppr_server_*)."""
+
+    def __init__(self, graph_handle, max_cols=128, hbm_reserve=0, damping=0.85, tol=1e-4,
+                 max_iters=100):
+        self.handle = ctypes.c_void_p()
+        _check(load().gap_ppr_server_create(graph_handle, max_cols, hbm_reserve, damping, tol,
+                                            max_iters, ctypes.byref(self.handle)),
+               "gap_ppr_server_create")
+        self._keep = {}
+
+    def submit(self, seeds, out):
+        import numpy as np
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+        t = ctypes.c_int64()
+        _check(load().gap_ppr_submit(self.handle, _ptr(seeds), len(seeds), _ptr(out), ctypes.byref(t)),
+               "gap_ppr_submit")
+        self._keep[t.value] = out  # the output buffer must outlive the query
+        return t.value
+
+    def poll(self, ticket):
+        done = ctypes.c_int32()
+        info = gap_ppr_query_info_t()
+        _check(load().gap_ppr_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(info)),
+               "gap_ppr_poll")
+        return (info.to_dict() if done.value else None)
+
+    def wait(self, ticket):
+        info = gap_ppr_query_info_t()
+        _check(load().gap_ppr_wait(self.handle, ticket, ctypes.byref(info)), "gap_ppr_wait")
+        self._keep.pop(ticket, None)
+        return info.to_dict()
+
+    def info(self):
+        c, done, steps, w = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(load().gap_ppr_server_info(self.handle, ctypes.byref(c), ctypes.byref(done),
+                                          ctypes.byref(steps), ctypes.byref(w)), "gap_ppr_server_info")
+        return {"columns": c.value, "completed": done.value, "steps": steps.value, "waiting": w.value}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().gap_ppr_server_destroy(self.handle)
+        self.handle = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gap_pr_stats(h):

@@ -90,6 +90,14 @@ def test_run_rejects_null_graph():
     assert gap.load().gap_pr_stats(None, ctypes.byref(st)) == gap.GAP_ERR_INVALID_ARG
 
 
+def test_server_create_rejects_null_graph():
+    out = ctypes.c_void_p()
+    assert gap.load().gap_ppr_server_create(None, 8, 0, 0.85, 1e-4, 100, ctypes.byref(out)) == \
+        gap.GAP_ERR_INVALID_ARG
+    assert gap.load().gap_ppr_batch(None, 1, None, None, 0.85, 1e-4, 10, None, None, None) == \
+        gap.GAP_ERR_INVALID_ARG
+
+
 def test_allocator_hook_validation():
     lib = gap.load()
     assert lib.gap_set_allocator(None) == gap.GAP_OK

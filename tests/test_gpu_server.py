@@ -1,0 +1,72 @@
+"""Continuous-batching PPR server: queries admitted as columns free up give
+exactly the result of the same query run alone (column independence), with
+host or device output buffers and staggered arrivals."""
+import time
+
+import numpy as np
+import pytest
+
+import gapgen
+from gpu_helpers import D, gpu_graph, oracle_graph
+from paper_1508_03619_gb300 import gap
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(g, seeds, tol=1e-4, iters=100):
+    import torch
+    out = torch.empty(g.n, dtype=torch.float32, device="cuda:0")
+    st = gap.gap_ppr_batch(g.handle, np.array([0, len(seeds)], np.int64), np.asarray(seeds, np.int32), D,
+                           tol, iters, out)
+    return out.cpu().numpy(), st[0]
+
+
+def test_server_mix_equals_alone(cuda_device):
+    import torch
+    n = 1 << 13
+    src, dst = gapgen.kron(13, 16, 0x61)
+    off, idx = oracle_graph(n, src, dst, True)
+    cand = np.flatnonzero(np.diff(off) > 0)
+    rng = np.random.default_rng(4)
+    g = gpu_graph(n, src, dst, True)
+    srv = gap.PprServer(g.handle, max_cols=8, damping=D, tol=1e-4, max_iters=100)
+    try:
+        assert srv.info()["columns"] == 8
+        queries, outs, tickets = [], [], []
+        for i in range(24):
+            seeds = rng.choice(cand, size=int(rng.integers(1, 65))).astype(np.int32)
+            out = np.zeros(n, np.float32) if i % 2 == 0 else torch.zeros(n, dtype=torch.float32, device="cuda:0")
+            queries.append(seeds)
+            outs.append(out)
+            tickets.append(srv.submit(seeds, out))
+            if i in (5, 13):
+                time.sleep(0.02)  # arrivals while others are on the GPU
+        infos = [srv.wait(t) for t in tickets]
+        for seeds, out, info in zip(queries, outs, infos):
+            got = out if isinstance(out, np.ndarray) else out.cpu().numpy()
+            ref, st = alone(g, seeds)
+            assert info["iterations"] == st["iterations"] and info["converged"]
+            assert np.array_equal(got, ref)
+            assert info["latency_ms"] > 0 and 0 <= info["column"] < 8
+        s = srv.info()
+        assert s["completed"] == 24 and s["waiting"] == 0 and s["steps"] > 0
+    finally:
+        srv.close()
+        g.close()
+
+
+def test_server_bad_input_and_destroy_with_pending(cuda_device):
+    n = 500
+    src, dst = gapgen.urand(n, 4000, 0x62)
+    g = gpu_graph(n, src, dst)
+    srv = gap.PprServer(g.handle, max_cols=4, damping=D, tol=0.0, max_iters=50)
+    try:
+        with pytest.raises(gap.GapError) as e:
+            srv.submit(np.array([n], np.int32), np.zeros(n, np.float32))
+        assert e.value.status == gap.GAP_ERR_INVALID_ARG
+        outs = [np.zeros(n, np.float32) for _ in range(10)]
+        for o in outs:
+            srv.submit(np.array([1, 2], np.int32), o)
+    finally:
+        srv.close()  # abandons what is still queued; must not hang
+        g.close()
