@@ -213,6 +213,29 @@ typedef struct {
  * GAP_WARN_NOT_CONVERGED, or the device error of that run. */
 GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
 
+/* ---------------------------------------------------- batch of graphs --- */
+/* PageRank (§2.1) on `count` independent graphs of any sizes in one
+ * persistent, cooperative kernel launched from a CUDA graph.  Each graph i
+ * uses its own n_i in the (1-d)/n_i term and x0 = 1/n_i, and stops on its own
+ * (its FP64 L1 delta < tol, or max_iters); graphs that stopped cost nothing in
+ * later iterations.  FP32 scores with FP32 accumulation in vertex order per
+ * row; contributions x/outdeg (0 for dangling vertices), as gap_pr_run.
+ *  - graphs: count handles, all on the current device; scores: count device
+ *    pointers, scores[i] holding graphs[i]'s n_i floats (caller-owned; the
+ *    arrays must not overlap).
+ *  - stats (optional, count entries): iterations, converged, final_delta,
+ *    mass, delta_hist per graph; segments = 1 and bin fields zero.
+ *  - Scratch (2 n_i floats per graph, one double per 32 vertices) comes from
+ *    the library's stream-ordered pool and is released before return.
+ *  - Blocks until the batch is done (it synchronizes `stream`).
+ *  - The kernel's grid barriers wait at most 2 s each; a wait that gives up
+ *    returns GAP_ERR_TIMEOUT (the context stays usable).
+ * Errors: INVALID_ARG (count < 0, NULL handle or scores, a graph on another
+ * device, host scores, damping outside [0,1], tol < 0, max_iters < 0),
+ * UNSUPPORTED (the kernel cannot be resident), OOM, CUDA, TIMEOUT. */
+GAP_API gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
+                                    int32_t max_iters, float* const* scores, gap_pr_stats_t* stats, void* stream);
+
 /* ------------------------------------------- personalized PageRank batch --- */
 /* Personalized PageRank (the serving workload; not in the paper): the §2.1
  * equation with the teleport term (1-d)/|V| replaced by (1-d)/|S_j| on the

@@ -47,7 +47,7 @@ EXPORTED = (
     "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
-    "gap_ppr_batch", "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
+    "gap_pr_run_batch", "gap_ppr_batch", "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
     "gap_ppr_server_info", "gap_ppr_server_destroy",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
@@ -141,6 +141,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_pr_run_ex": ([vp, dbl, dbl, i32, ctypes.POINTER(gap_pr_options), vp, vp], st),
         "gap_pr_stats": ([vp, ctypes.POINTER(gap_pr_stats_t)], st),
         "gap_pr_run_noalloc": ([vp, dbl, dbl, i32, vp, vp], st),
+        "gap_pr_run_batch": ([vp, i32, dbl, dbl, i32, vp, vp, vp], st),
         "gap_ppr_batch": ([vp, i32, vp, vp, dbl, dbl, i32, vp, vp, vp], st),
         "gap_ppr_server_create": ([vp, i32, ctypes.c_size_t, dbl, dbl, i32, ctypes.POINTER(vp)], st),
         "gap_ppr_submit": ([vp, vp, i32, vp, ctypes.POINTER(i64)], st),
@@ -307,6 +308,25 @@ def gap_pr_run_noalloc(h, damping: float, tol: float, max_iters: int, scores, st
     _check_scores(h, scores, 4, "gap_pr_run_noalloc")
     return _check(load().gap_pr_run_noalloc(h, damping, tol, max_iters, _ptr(scores),
                                             _stream(stream)), "gap_pr_run_noalloc")
+
+
+def gap_pr_run_batch(handles, scores, damping: float, tol: float, max_iters: int, stats=True,
+                     stream=None):
+    """PageRank on len(handles) graphs in one persistent launch (see gap.h);
+    scores[i] is a float32 device tensor of graph i's n floats.  Returns the
+    per-graph stats dicts when `stats`."""
+    count = len(handles)
+    if len(scores) != count:
+        raise ValueError(f"gap_pr_run_batch: {count} graphs but {len(scores)} score arrays")
+    for i, (h, sc) in enumerate(zip(handles, scores)):
+        _check_scores(h, sc, 4, f"gap_pr_run_batch[{i}]")
+    hs = (ctypes.c_void_p * max(count, 1))(*[h if isinstance(h, ctypes.c_void_p) else _ptr(h)
+                                              for h in handles])
+    ps = (ctypes.c_void_p * max(count, 1))(*[_ptr(sc) for sc in scores])
+    st = (gap_pr_stats_t * max(count, 1))() if stats else None
+    _check(load().gap_pr_run_batch(hs, count, damping, tol, max_iters, ps, st, _stream(stream)),
+           "gap_pr_run_batch")
+    return [st[i].to_dict() for i in range(count)] if stats else None
 
 
 def gap_ppr_batch(h, seed_offsets, seeds, damping: float, tol: float, max_iters: int, scores,
