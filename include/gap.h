@@ -217,24 +217,57 @@ GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
 /* PageRank (§2.1) on `count` independent graphs of any sizes in one
  * persistent, cooperative kernel launched from a CUDA graph.  Each graph i
  * uses its own n_i in the (1-d)/n_i term and x0 = 1/n_i, and stops on its own
- * (its FP64 L1 delta < tol, or max_iters); graphs that stopped cost nothing in
- * later iterations.  FP32 scores with FP32 accumulation in vertex order per
- * row; contributions x/outdeg (0 for dangling vertices), as gap_pr_run.
- *  - graphs: count handles, all on the current device; scores: count device
+ * (its L1 delta < tol, or max_iters); graphs that stopped cost nothing in
+ * later iterations.  FP32 scores and FP32 accumulation; contributions
+ * x/outdeg (0 for dangling vertices), as gap_pr_run.  Rows with more than
+ * tuning.heavy_min_degree in-arcs are gathered in chunks of at most
+ * tuning.chunk_arcs arcs by separate warps and their chunk sums added in chunk
+ * order; lighter rows are pulled 32 consecutive vertices per warp in vertex
+ * order.  A graph's L1 delta is the sum of per-task FP64 deltas, each rounded
+ * to a multiple of 2^-60 and added as integers (exact and independent of
+ * the order in which tasks finish), so a graph's result does not depend on the
+ * other graphs in the batch.
+ *  - graphs: count handles (count <= GAP_BATCH_MAX_GRAPHS), all on the
+ *    current device, each with fewer than 2^31 vertices; scores: count device
  *    pointers, scores[i] holding graphs[i]'s n_i floats (caller-owned; the
- *    arrays must not overlap).
+ *    arrays must not overlap).  A handle may not appear twice.
  *  - stats (optional, count entries): iterations, converged, final_delta,
  *    mass, delta_hist per graph; segments = 1 and bin fields zero.
- *  - Scratch (2 n_i floats per graph, one double per 32 vertices) comes from
- *    the library's stream-ordered pool and is released before return.
+ *  - Scratch (2 n_i floats per graph, the chunk lists) comes from the
+ *    library's stream-ordered pool and is released before return.
  *  - Blocks until the batch is done (it synchronizes `stream`).
  *  - The kernel's grid barriers wait at most 2 s each; a wait that gives up
  *    returns GAP_ERR_TIMEOUT (the context stays usable).
- * Errors: INVALID_ARG (count < 0, NULL handle or scores, a graph on another
- * device, host scores, damping outside [0,1], tol < 0, max_iters < 0),
- * UNSUPPORTED (the kernel cannot be resident), OOM, CUDA, TIMEOUT. */
+ * Errors: INVALID_ARG (count out of range, NULL handle or scores, a graph on
+ * another device, host scores, damping outside [0,1], tol < 0, max_iters < 0,
+ * bad tuning), UNSUPPORTED (the kernel cannot be resident), OOM, CUDA,
+ * TIMEOUT. */
+#define GAP_BATCH_MAX_GRAPHS 65536
+#define GAP_BATCH_DEFAULT_HEAVY 256
+#define GAP_BATCH_DEFAULT_CHUNK 2048
+#define GAP_BATCH_DEFAULT_THREADS 256
+typedef struct {
+  int32_t heavy_min_degree; /* rows with more in-arcs than this are chunked (>= 32) */
+  int32_t chunk_arcs;       /* arcs per chunk of a heavy row, in [32, 2^24] */
+  int32_t block_threads;    /* threads per block of the persistent kernel: 128, 256 or 512 */
+  int32_t blocks_per_sm;    /* resident blocks per SM; 0 = as many as fit */
+} gap_batch_tuning;
+
+/* Fill *t with the built-in tuning (the values above, blocks_per_sm 0). */
+GAP_API void gap_batch_tuning_default(gap_batch_tuning* t);
+
+/* gap_pr_run_batch with the built-in tuning. */
 GAP_API gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
                                     int32_t max_iters, float* const* scores, gap_pr_stats_t* stats, void* stream);
+
+/* gap_pr_run_batch with an explicit tuning (NULL = built-in).  The tuning
+ * changes only how work is split and launched: results are bit-identical for
+ * any block_threads and blocks_per_sm; heavy_min_degree and chunk_arcs change
+ * the summation order of some rows, so results then agree within FP32
+ * rounding. */
+GAP_API gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
+                                       int32_t max_iters, const gap_batch_tuning* tuning, float* const* scores,
+                                       gap_pr_stats_t* stats, void* stream);
 
 /* ------------------------------------------- personalized PageRank batch --- */
 /* Personalized PageRank (the serving workload; not in the paper): the §2.1

@@ -1,22 +1,35 @@
 // batch.cu — PageRank on many independent graphs of uneven size in one
-// persistent, cooperative, CUDA-graph-captured launch.  Each graph follows
-// the §2.1 definition on its own: its own n in the (1-d)/n term, its own L1
-// delta, its own stop.
+// persistent, cooperative kernel launched from a CUDA graph.  Each graph
+// follows the §2.1 definition on its own: its own n in the (1-d)/n term and in
+// x0, its own L1 delta, its own stop (§3.1 tolerance test).
 //
-// Work is flattened into warp tasks: task t of graph i = vertices
-// [32t, 32t+32) of graph i.  Every warp of the persistent grid walks the tasks
-// (grid-stride), skips graphs that have stopped, pulls each tile with the
-// vertex-order warp-merge reduction (fixed summation order, any row degree)
-// and writes the tile's delta to its own slot.  After a grid barrier one warp
-// per running graph adds its tiles' deltas in tile order and applies the stop
-// test; after a second barrier every block reads how many graphs still run.
+// Work items ("tasks"), laid out graph after graph:
+//   light tile  — 32 consecutive vertices of one graph; rows with in-degree
+//                 <= heavy_min_degree are pulled with the vertex-order
+//                 warp-merge reduction (heavier rows of the tile are skipped);
+//   row chunk   — up to chunk_arcs consecutive in-arcs of one heavy row,
+//                 gathered by a warp with coalesced index loads.  A row of one
+//                 chunk is updated by that warp; for a row of several chunks
+//                 each chunk stores its partial sum and the warp that finishes
+//                 last (counted with an atomic) adds the partials in chunk
+//                 order and updates the row.
+// A set-up pass per call (inside the timed region: the split is a run-time
+// decision on the input, §3.2) counts and lists the chunks of every graph.
 //
-// The grid barriers are this file's own and are used only inside a
-// cooperative launch, which guarantees that all blocks are resident.  Each
-// wait is bounded in time: a wait that gives up sets an error code that every
-// other waiter also sees, and all blocks leave the kernel.  Data written by
-// other blocks during the launch (contributions, tile deltas, graph states) is
-// read through L2 (ld.global.cg), never through the non-coherent L1.
+// Per iteration every warp walks the tasks of the graphs still running
+// (grid-stride), and each task adds its |x' - x| to its graph's accumulator as
+// a 64-bit fixed-point integer (units of 2^-60, exact integer atomics, so the
+// graph's delta does not depend on the order in which tasks finish).  After
+// one grid barrier every block reads all accumulators and takes the same stop
+// decision for every graph; accumulators rotate over three buffers so that
+// zeroing the next one never races with readers of the previous one.
+//
+// The grid barrier is this file's own, used only inside a cooperative launch
+// (all blocks resident).  Each wait is bounded in time: a wait that gives up
+// sets an error code that every other waiter also sees, and all blocks leave.
+// Data written by other blocks during the launch (scores, contributions,
+// partials, accumulators) is read through L2 (ld.global.cg), never through the
+// non-coherent L1.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -33,32 +46,40 @@ struct BatchGraph {
   float* c0;
   float* c1;
   int64_t n;
-  int64_t tile_base;  // first task (32-vertex tile) of this graph
-  float base;         // (1 - d) / n of this graph
+  int64_t tiles;  // ceil(n / 32)
+  float base;     // (1 - d) / n of this graph
   float pad;
+};
+
+struct ChunkDesc {
+  int64_t a0;     // first arc of the chunk
+  int64_t first;  // chunk id of the row's first chunk
+  int32_t len;    // arcs in the chunk
+  int32_t v;      // the row (vertex id in its graph)
+  int32_t nch;    // chunks of the row
+  int32_t pad;
 };
 
 struct BatchCtrl {
   unsigned int bar_count;
   unsigned int bar_gen;
-  int32_t error;    // GAP_ERR_TIMEOUT when a barrier wait gave up
-  int32_t running;  // graphs that have not stopped yet
-  int32_t iter;     // iterations the batch ran (max over graphs)
-  int32_t pad;
+  int32_t error;  // GAP_ERR_TIMEOUT when a barrier wait gave up
+  int32_t iter;   // iterations the batch ran (max over graphs)
+  int64_t ntasks;
+  int64_t nchunks;
 };
 
 struct BatchGraphState {
-  int32_t active;
   int32_t iterations;
   int32_t converged;
-  int32_t pad;
   double final_delta;
   double mass;
   double delta_hist[GAP_PR_HIST];
 };
 
-constexpr int BATCH_THREADS = 256;
 constexpr unsigned long long BARRIER_WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr double DELTA_SCALE = 1152921504606846976.0;           // 2^60
+constexpr double DELTA_UNIT = 1.0 / DELTA_SCALE;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -66,8 +87,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Sense-reversing grid barrier (generation counter) with a bounded wait.
-// Returns false when the wait gave up or another block reported an error.
+// Grid barrier (generation counter) with a bounded wait.  Returns false when
+// the wait gave up or another block reported an error.
 __device__ bool grid_barrier(BatchCtrl* ctrl, unsigned int nblocks) {
   __shared__ int ok;
   __syncthreads();
@@ -100,23 +121,27 @@ __device__ bool grid_barrier(BatchCtrl* ctrl, unsigned int nblocks) {
   return ok != 0;
 }
 
-// Largest i with gs[i].tile_base <= task (graphs are laid out in task order).
-__device__ __forceinline__ int find_graph(const BatchGraph* gs, int ng, int64_t task) {
+// Largest i with base[i] <= t (base ascending, base[0] = 0).
+__device__ __forceinline__ int find_graph(const int64_t* __restrict__ base, int ng, int64_t t) {
   int lo = 0, hi = ng - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (gs[mid].tile_base <= task) lo = mid; else hi = mid - 1;
+    if (__ldg(base + mid) <= t) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
 
-// Pull one 32-vertex tile of graph G: the tile's in-arcs are taken 32 at a
-// time in vertex order, each lane finds its row by binary search over the
-// tile's exclusive degree scan, a keyed warp scan forms per-row partial sums
-// and the last lane of each row's run adds it to that row's accumulator.
-// Applies the §2.1 update and writes x and the next contributions; returns the
-// tile's summed |x' - x| (FP64) in every lane.
-__device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float d) {
+__device__ __forceinline__ unsigned long long to_fixed(double v) {
+  return (unsigned long long)__double2ull_rn(v * DELTA_SCALE);
+}
+
+// One 32-vertex light tile: rows of degree <= heavy are pulled with the
+// warp-merge (the tile's arcs taken 32 at a time in vertex order; each lane
+// finds its row by binary search over the exclusive degree scan; a keyed warp
+// scan forms per-row partials; the row's last lane in the batch hands its
+// partial to the row's owner lane).  Returns the tile's |x' - x| (FP64) in
+// every lane.
+__device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float d, int heavy) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const float* cin = parity ? G.c1 : G.c0;
@@ -125,7 +150,8 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
   const bool valid = v < G.n;
   const int64_t rb = valid ? __ldg(G.off + v) : 0;
   const int64_t re = valid ? __ldg(G.off + v + 1) : 0;
-  const int dd = (int)(re - rb);
+  const bool mine = valid && re - rb <= heavy;  // heavy rows belong to chunk tasks
+  const int dd = mine ? (int)(re - rb) : 0;
   int incl = dd;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -155,17 +181,16 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
       const int ro = __shfl_up_sync(FULL, rr, o);
       if (lane >= o && ro == rr) xs = __fadd_rn(xs, t);
     }
-    // row `lane` takes the partial of the last arc it has in this batch
     const bool inter = dd > 0 && excl < b0 + 32 && incl > b0;
     const int tl = (incl < b0 + 32 ? incl : b0 + 32) - 1 - b0;
     const float part = __shfl_sync(FULL, xs, inter ? tl : lane);
     if (inter) acc = __fadd_rn(acc, part);
   }
   double dl = 0.0;
-  if (valid) {
-    const float xo = G.x[v];
+  if (mine) {
+    const float xo = __ldcg(G.x + v);
     const float xn = __fadd_rn(G.base, __fmul_rn(d, acc));
-    G.x[v] = xn;
+    __stcg(G.x + v, xn);
     const int od = __ldg(G.outdeg + v);
     __stcg(cout + v, od > 0 ? xn / (float)od : 0.f);
     const double df = (double)xn - (double)xo;
@@ -174,75 +199,253 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
   return warp_sum(dl);
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch_init(const BatchGraph* __restrict__ gs, int ng,
-                                                               BatchGraphState* st, BatchCtrl* ctrl,
-                                                               int32_t max_iters) {
-  // x0 = 1/n_i, first contributions x0/outdeg, fresh per-graph state
+// Update of one row from its finished in-sum; returns |x' - x|.
+__device__ __forceinline__ double update_row(const BatchGraph& G, int64_t v, float sum, int parity, float d) {
+  float* cout = parity ? G.c0 : G.c1;
+  const float xo = __ldcg(G.x + v);
+  const float xn = __fadd_rn(G.base, __fmul_rn(d, sum));
+  __stcg(G.x + v, xn);
+  const int od = __ldg(G.outdeg + v);
+  __stcg(cout + v, od > 0 ? xn / (float)od : 0.f);
+  const double df = (double)xn - (double)xo;
+  return df < 0 ? -df : df;
+}
+
+// One chunk of a heavy row: lanes take arcs lane, lane+32, ... (4 loads in
+// flight per lane), then a fixed-order warp tree sum.  Returns |x' - x| in
+// lane 0 when this warp updated the row, else 0.
+__device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t cid, float* partial,
+                             unsigned int* ctr, int parity, float d) {
+  const int lane = threadIdx.x & 31;
+  const float* cin = parity ? G.c1 : G.c0;
+  const int32_t* ix = G.idx + c.a0;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int j = lane;
+  for (; j + 96 < c.len; j += 128) {
+    const int u0 = __ldg(ix + j), u1 = __ldg(ix + j + 32), u2 = __ldg(ix + j + 64), u3 = __ldg(ix + j + 96);
+    s0 = __fadd_rn(s0, __ldcg(cin + u0));
+    s1 = __fadd_rn(s1, __ldcg(cin + u1));
+    s2 = __fadd_rn(s2, __ldcg(cin + u2));
+    s3 = __fadd_rn(s3, __ldcg(cin + u3));
+  }
+  for (; j < c.len; j += 32) s0 = __fadd_rn(s0, __ldcg(cin + __ldg(ix + j)));
+  float s = __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
+  s = warp_sum(s);
+  if (c.nch == 1) {
+    double dl = 0.0;
+    if (lane == 0) dl = update_row(G, c.v, s, parity, d);
+    return dl;
+  }
+  // several chunks: publish the partial; the last finisher updates the row
+  int last = 0;
+  if (lane == 0) {
+    __stcg(partial + cid, s);
+    __threadfence();
+    last = atomicAdd(ctr + c.first, 1u) + 1u == (unsigned)c.nch;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return 0.0;
+  __threadfence();
+  float t = 0.f;
+  for (int k = lane; k < c.nch; k += 32) t = __fadd_rn(t, __ldcg(partial + c.first + k));
+  t = warp_sum(t);
+  double dl = 0.0;
+  if (lane == 0) {
+    dl = update_row(G, c.v, t, parity, d);
+    ctr[c.first] = 0;  // ready for the next iteration (after the grid barrier)
+  }
+  return dl;
+}
+
+// ---- set-up: x0, contributions, chunk lists ----------------------------------
+
+__global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng, int heavy, int chunk,
+                             int64_t* chunk_count) {
+  __shared__ long long sh[32];
   for (int i = blockIdx.x; i < ng; i += gridDim.x) {
     const BatchGraph G = gs[i];
     const float x0 = (float)(1.0 / (double)G.n);
+    long long cc = 0;
     for (int64_t v = threadIdx.x; v < G.n; v += blockDim.x) {
       G.x[v] = x0;
       const int od = G.outdeg[v];
       G.c0[v] = od > 0 ? x0 / (float)od : 0.f;
+      const int64_t dg = G.off[v + 1] - G.off[v];
+      if (dg > heavy) cc += (dg + chunk - 1) / chunk;
     }
-    if (threadIdx.x == 0) {
-      memset(&st[i], 0, sizeof(BatchGraphState));
-      st[i].active = max_iters > 0 ? 1 : 0;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    memset(ctrl, 0, sizeof(BatchCtrl));
-    ctrl->running = max_iters > 0 ? ng : 0;
+    cc = block_sum(cc, sh);
+    if (threadIdx.x == 0) chunk_count[i] = cc;
+    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch_persistent(const BatchGraph* __restrict__ gs, int ng,
-                                                                     int64_t ntasks, BatchGraphState* st,
-                                                                     BatchCtrl* ctrl, double* tile_delta,
-                                                                     float d, double tol, int32_t max_iters) {
+// One block: task and chunk bases of every graph (exclusive scans), totals,
+// per-graph state reset, and the control block.
+__global__ void k_batch_plan(const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ chunk_count,
+                             int64_t* task_base, int64_t* chunk_base, BatchGraphState* st, BatchCtrl* ctrl) {
+  __shared__ long long sh_t[1024], sh_c[1024];
+  __shared__ long long carry_t, carry_c;
+  if (threadIdx.x == 0) carry_t = carry_c = 0;
+  __syncthreads();
+  for (int b = 0; b < ng; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    long long t = 0, c = 0;
+    if (i < ng) {
+      c = chunk_count[i];
+      t = gs[i].tiles + c;
+      memset(&st[i], 0, sizeof(BatchGraphState));
+    }
+    sh_t[threadIdx.x] = t;
+    sh_c[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive Hillis-Steele scan
+      long long at = 0, ac = 0;
+      if ((int)threadIdx.x >= o) { at = sh_t[threadIdx.x - o]; ac = sh_c[threadIdx.x - o]; }
+      __syncthreads();
+      sh_t[threadIdx.x] += at;
+      sh_c[threadIdx.x] += ac;
+      __syncthreads();
+    }
+    if (i < ng) {
+      task_base[i] = carry_t + sh_t[threadIdx.x] - t;
+      chunk_base[i] = carry_c + sh_c[threadIdx.x] - c;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) {
+      carry_t += sh_t[threadIdx.x];
+      carry_c += sh_c[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    task_base[ng] = carry_t;
+    chunk_base[ng] = carry_c;
+    memset(ctrl, 0, sizeof(BatchCtrl));
+    ctrl->ntasks = carry_t;
+    ctrl->nchunks = carry_c;
+  }
+}
+
+// Chunk descriptors of every heavy row, in row order (block per graph; an
+// ordered block-wide compaction over the rows).
+__global__ void k_batch_chunks(const BatchGraph* __restrict__ gs, int ng, int heavy, int chunk,
+                               const int64_t* __restrict__ chunk_base, ChunkDesc* desc, unsigned int* ctr) {
+  __shared__ long long warp_tot[32];
+  __shared__ long long run;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = blockIdx.x; i < ng; i += gridDim.x) {
+    const BatchGraph G = gs[i];
+    if (threadIdx.x == 0) run = chunk_base[i];
+    __syncthreads();
+    for (int64_t b = 0; b < G.n; b += blockDim.x) {
+      const int64_t v = b + threadIdx.x;
+      int64_t a0 = 0, dg = 0;
+      long long cnt = 0;
+      if (v < G.n) {
+        a0 = G.off[v];
+        dg = G.off[v + 1] - a0;
+        if (dg > heavy) cnt = (dg + chunk - 1) / chunk;
+      }
+      long long incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) warp_tot[wid] = incl;
+      __syncthreads();
+      long long before = run;
+      for (int w = 0; w < wid; ++w) before += warp_tot[w];
+      const long long first = before + incl - cnt;
+      for (long long k = 0; k < cnt; ++k) {
+        ChunkDesc cd;
+        cd.a0 = a0 + k * chunk;
+        cd.first = first;
+        cd.len = (int32_t)(dg - k * chunk < chunk ? dg - k * chunk : chunk);
+        cd.v = (int32_t)v;
+        cd.nch = (int32_t)cnt;
+        cd.pad = 0;
+        desc[first + k] = cd;
+        ctr[first + k] = 0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int w = 0; w < nw; ++w) tot += warp_tot[w];
+        run += tot;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---- the persistent kernel ----------------------------------------------------
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_batch_persistent(
+    const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ task_base,
+    const int64_t* __restrict__ chunk_base, const ChunkDesc* __restrict__ desc, float* partial, unsigned int* ctr,
+    unsigned long long* acc /* [3][ng] */, BatchGraphState* st, BatchCtrl* ctrl, float d, double tol,
+    int32_t max_iters, int heavy) {
+  extern __shared__ unsigned int active[];  // one bit per graph
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * BATCH_THREADS + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * BATCH_THREADS) >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * THREADS) >> 5;
   const unsigned int nb = gridDim.x;
+  const int words = (ng + 31) >> 5;
+  const int64_t ntasks = ctrl->ntasks;
+  for (int w = threadIdx.x; w < words; w += THREADS) {
+    const int rem = ng - 32 * w;
+    active[w] = max_iters > 0 ? (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u)) : 0u;
+  }
+  __syncthreads();
   __shared__ int running;
   for (int it = 0; it < max_iters; ++it) {
-    // phase A: every tile of every running graph
+    const int parity = it & 1;
+    unsigned long long* acc_now = acc + (int64_t)(it % 3) * ng;
     for (int64_t task = warp; task < ntasks; task += nwarps) {
-      const int i = find_graph(gs, ng, task);
-      if (!__ldcg(&st[i].active)) continue;  // warp-uniform
-      const double dl = pull_tile(gs[i], task - gs[i].tile_base, __ldcg(&st[i].iterations) & 1, d);
-      if (lane == 0) __stcg(&tile_delta[task], dl);
-    }
-    if (!grid_barrier(ctrl, nb)) return;
-    // phase B: per-graph delta in tile order and the stop test
-    for (int64_t i = warp; i < ng; i += nwarps) {
-      if (!__ldcg(&st[i].active)) continue;
-      const int64_t tb = gs[i].tile_base;
-      const int64_t ntiles = (gs[i].n + 31) / 32;
-      double s = 0.0;
-      for (int64_t t = lane; t < ntiles; t += 32) s += __ldcg(&tile_delta[tb + t]);
-      s = warp_sum(s);
-      if (lane == 0) {
-        BatchGraphState& S = st[i];
-        const int k = __ldcg(&S.iterations);
-        if (k < GAP_PR_HIST) S.delta_hist[k] = s;
-        S.final_delta = s;
-        S.iterations = k + 1;
-        S.converged = s < tol;
-        if (S.converged || k + 1 >= max_iters) {
-          S.active = 0;
-          atomicSub(&ctrl->running, 1);
-        }
+      const int i = find_graph(task_base, ng, task);
+      if (!((active[i >> 5] >> (i & 31)) & 1u)) continue;  // warp-uniform
+      const BatchGraph& G = gs[i];
+      const int64_t local = task - __ldg(task_base + i);
+      double dl;
+      if (local < G.tiles) {
+        dl = pull_tile(G, local, parity, d, heavy);
+      } else {
+        const int64_t cid = __ldg(chunk_base + i) + (local - G.tiles);
+        dl = pull_chunk(G, desc[cid], cid, partial, ctr, parity, d);
       }
+      if (lane == 0 && dl != 0.0) atomicAdd(acc_now + i, to_fixed(dl));
+    }
+    if (blockIdx.x == 0) {  // the accumulator of iteration it+1 starts at zero
+      unsigned long long* acc_next = acc + (int64_t)((it + 1) % 3) * ng;
+      for (int i = threadIdx.x; i < ng; i += THREADS) acc_next[i] = 0ull;
     }
     if (!grid_barrier(ctrl, nb)) return;
+    // every block takes the same stop decision for every graph
+    int any = 0;
+    for (int i = threadIdx.x; i < ng; i += THREADS) {
+      if (!((active[i >> 5] >> (i & 31)) & 1u)) continue;
+      const double delta = (double)__ldcg(acc_now + i) * DELTA_UNIT;
+      const bool conv = delta < tol;
+      const bool stop = conv || it + 1 >= max_iters;
+      if (blockIdx.x == 0) {
+        BatchGraphState& S = st[i];
+        if (it < GAP_PR_HIST) S.delta_hist[it] = delta;
+        S.final_delta = delta;
+        S.iterations = it + 1;
+        S.converged = conv;
+      }
+      if (stop) atomicAnd(&active[i >> 5], ~(1u << (i & 31)));
+      else any = 1;
+    }
+    any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-      running = *(volatile int32_t*)&ctrl->running;
+      running = any;
       if (blockIdx.x == 0) ctrl->iter = it + 1;
     }
     __syncthreads();
-    if (running == 0) return;
+    if (!running) return;
   }
 }
 
@@ -258,18 +461,50 @@ __global__ void k_batch_mass(const BatchGraph* __restrict__ gs, int ng, BatchGra
   }
 }
 
+using PersistentFn = void (*)(const BatchGraph*, int, const int64_t*, const int64_t*, const ChunkDesc*, float*,
+                              unsigned int*, unsigned long long*, BatchGraphState*, BatchCtrl*, float, double,
+                              int32_t, int);
+
+PersistentFn persistent_for(int threads) {
+  switch (threads) {
+    case 128: return k_batch_persistent<128>;
+    case 256: return k_batch_persistent<256>;
+    case 512: return k_batch_persistent<512>;
+    default: return nullptr;
+  }
+}
+
 }  // namespace gap
 
 using namespace gap;
 
-extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
-                                       int32_t max_iters, float* const* scores, gap_pr_stats_t* stats,
-                                       void* stream) {
+extern "C" void gap_batch_tuning_default(gap_batch_tuning* t) {
+  if (!t) return;
+  memset(t, 0, sizeof(*t));
+  t->heavy_min_degree = GAP_BATCH_DEFAULT_HEAVY;
+  t->chunk_arcs = GAP_BATCH_DEFAULT_CHUNK;
+  t->block_threads = GAP_BATCH_DEFAULT_THREADS;
+  t->blocks_per_sm = 0;
+}
+
+extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
+                                          int32_t max_iters, const gap_batch_tuning* tuning, float* const* scores,
+                                          gap_pr_stats_t* stats, void* stream) {
   clear_error();
-  if (count < 0 || (count > 0 && (!graphs || !scores)) || !(damping >= 0 && damping <= 1) || !(tol >= 0) ||
-      max_iters < 0) {
+  gap_batch_tuning tu;
+  gap_batch_tuning_default(&tu);
+  if (tuning) tu = *tuning;
+  if (count < 0 || count > GAP_BATCH_MAX_GRAPHS || (count > 0 && (!graphs || !scores)) ||
+      !(damping >= 0 && damping <= 1) || !(tol >= 0) || max_iters < 0) {
     set_error("gap_pr_run_batch: bad argument (count %d, damping %g, tol %g, max_iters %d)", count, damping, tol,
               max_iters);
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (tu.heavy_min_degree < 32 || tu.chunk_arcs < 32 || tu.chunk_arcs > (1 << 24) || !persistent_for(tu.block_threads) ||
+      tu.blocks_per_sm < 0) {
+    set_error("gap_pr_run_batch: bad tuning (heavy_min_degree %d >= 32, chunk_arcs %d in [32, 2^24], "
+              "block_threads %d in {128, 256, 512}, blocks_per_sm %d >= 0)",
+              tu.heavy_min_degree, tu.chunk_arcs, tu.block_threads, tu.blocks_per_sm);
     return GAP_ERR_INVALID_ARG;
   }
   if (count == 0) return GAP_OK;
@@ -277,7 +512,7 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
   int dev = 0;
   GAP_CUDA(cudaGetDevice(&dev));
   std::vector<BatchGraph> hg(count);
-  int64_t tasks = 0, cells = 0;
+  int64_t cells = 0, chunk_cap = 0;
   for (int i = 0; i < count; ++i) {
     gap_graph* g = graphs[i];
     if (!g || !scores[i]) {
@@ -289,18 +524,37 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
                 g->device, dev);
       return GAP_ERR_INVALID_ARG;
     }
+    if (g->n >= (int64_t(1) << 31)) {
+      set_error("gap_pr_run_batch: graph %d has %lld vertices (at most 2^31 - 1)", i, (long long)g->n);
+      return GAP_ERR_INVALID_ARG;
+    }
     hg[i].off = g->in_off;
     hg[i].idx = g->in_idx;
     hg[i].outdeg = g->outdeg;
     hg[i].x = scores[i];
     hg[i].n = g->n;
-    hg[i].tile_base = tasks;
+    hg[i].tiles = (g->n + 31) / 32;
     hg[i].base = (float)((1.0 - damping) / (double)g->n);
     hg[i].pad = 0.f;
-    tasks += (g->n + 31) / 32;
     cells += 2 * g->n;
+    // heavy rows have > heavy_min_degree arcs: at most m/(heavy+1) of them,
+    // each with ceil(deg/chunk) <= deg/chunk + 1 chunks
+    chunk_cap += g->m / tu.chunk_arcs + g->m / (tu.heavy_min_degree + 1) + 1;
   }
-  Scratch cbuf, dgs, dstate, dctrl, tdelta;
+  const int threads = tu.block_threads;
+  const PersistentFn kfn = persistent_for(threads);
+  const size_t smem = sizeof(unsigned int) * ((count + 31) / 32);
+  int per_sm = 0;
+  GAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
+  if (per_sm < 1) {
+    set_error("gap_pr_run_batch: the persistent kernel cannot be resident on this device");
+    return GAP_ERR_UNSUPPORTED;
+  }
+  if (tu.blocks_per_sm > 0) per_sm = std::min(per_sm, tu.blocks_per_sm);
+  const int nsm = device_info().sms;
+  const int grid = nsm * per_sm;
+
+  Scratch cbuf, dgs, dstate, dctrl, dtb, dcb, dcc, ddesc, dpart, dctr, dacc;
   GAP_TRY(cbuf.get(sizeof(float) * cells, s));
   int64_t pos = 0;
   for (int i = 0; i < count; ++i) {
@@ -311,44 +565,54 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
   GAP_TRY(dgs.get(sizeof(BatchGraph) * count, s));
   GAP_TRY(dstate.get(sizeof(BatchGraphState) * count, s));
   GAP_TRY(dctrl.get(sizeof(BatchCtrl), s));
-  GAP_TRY(tdelta.get(sizeof(double) * tasks, s));
+  GAP_TRY(dtb.get(sizeof(int64_t) * (count + 1), s));
+  GAP_TRY(dcb.get(sizeof(int64_t) * (count + 1), s));
+  GAP_TRY(dcc.get(sizeof(int64_t) * count, s));
+  GAP_TRY(ddesc.get(sizeof(ChunkDesc) * chunk_cap, s));
+  GAP_TRY(dpart.get(sizeof(float) * chunk_cap, s));
+  GAP_TRY(dctr.get(sizeof(unsigned int) * chunk_cap, s));
+  GAP_TRY(dacc.get(sizeof(unsigned long long) * 3 * count, s));
   GAP_CUDA(cudaMemcpyAsync(dgs.p, hg.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s));
-  const int nsm = device_info().sms;
-  k_batch_init<<<std::min(count, nsm * 8), BATCH_THREADS, 0, s>>>(dgs.as<BatchGraph>(), count,
-                                                                  dstate.as<BatchGraphState>(),
-                                                                  dctrl.as<BatchCtrl>(), max_iters);
+  GAP_CUDA(cudaMemsetAsync(dacc.p, 0, sizeof(unsigned long long) * 3 * count, s));
+  const int setup_grid = std::min(count, nsm * 8);
+  k_batch_init<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, tu.heavy_min_degree, tu.chunk_arcs,
+                                          dcc.as<int64_t>());
   GAP_LAUNCH_CHECK();
-  int launches = 2;
+  k_batch_plan<<<1, 1024, 0, s>>>(dgs.as<BatchGraph>(), count, dcc.as<int64_t>(), dtb.as<int64_t>(),
+                                  dcb.as<int64_t>(), dstate.as<BatchGraphState>(), dctrl.as<BatchCtrl>());
+  GAP_LAUNCH_CHECK();
+  k_batch_chunks<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, tu.heavy_min_degree, tu.chunk_arcs,
+                                            dcb.as<int64_t>(), ddesc.as<ChunkDesc>(), dctr.as<unsigned int>());
+  GAP_LAUNCH_CHECK();
+  int launches = 3;
   if (max_iters > 0) {
-    // persistent grid: all blocks resident at once (cooperative launch)
-    int per_sm = 0;
-    GAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persistent, BATCH_THREADS, 0));
-    if (per_sm < 1) {
-      set_error("gap_pr_run_batch: the persistent kernel cannot be resident on this device");
-      return GAP_ERR_UNSUPPORTED;
-    }
-    const int grid = nsm * per_sm;
     const BatchGraph* a_gs = dgs.as<BatchGraph>();
     int a_ng = count;
-    int64_t a_tasks = tasks;
+    const int64_t* a_tb = dtb.as<int64_t>();
+    const int64_t* a_cb = dcb.as<int64_t>();
+    const ChunkDesc* a_desc = ddesc.as<ChunkDesc>();
+    float* a_part = dpart.as<float>();
+    unsigned int* a_ctr = dctr.as<unsigned int>();
+    unsigned long long* a_acc = dacc.as<unsigned long long>();
     BatchGraphState* a_st = dstate.as<BatchGraphState>();
     BatchCtrl* a_ctrl = dctrl.as<BatchCtrl>();
-    double* a_td = tdelta.as<double>();
     float a_d = (float)damping;
     double a_tol = tol;
     int32_t a_iters = max_iters;
-    void* args[] = {&a_gs, &a_ng, &a_tasks, &a_st, &a_ctrl, &a_td, &a_d, &a_tol, &a_iters};
+    int a_heavy = tu.heavy_min_degree;
+    void* args[] = {&a_gs, &a_ng, &a_tb, &a_cb, &a_desc, &a_part, &a_ctr, &a_acc, &a_st, &a_ctrl,
+                    &a_d, &a_tol, &a_iters, &a_heavy};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(BATCH_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // The one launch is captured into a CUDA graph on a private stream that
-    // joins the caller's stream by events, then the graph is launched there.
+    // The one launch is captured into a CUDA graph on a private stream, then
+    // the instantiated graph is launched on the caller's stream.
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -358,7 +622,7 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
       cfg.stream = cs;
       cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__); break; }
-      const cudaError_t le = cudaLaunchKernelExC(&cfg, (const void*)k_batch_persistent, args);
+      const cudaError_t le = cudaLaunchKernelExC(&cfg, (const void*)kfn, args);
       e = cudaStreamEndCapture(cs, &graph);
       if (le != cudaSuccess) { st = cuda_fail(le, "cooperative launch under capture", __FILE__, __LINE__); break; }
       if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
@@ -376,8 +640,9 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
     }
     ++launches;
   }
-  k_batch_mass<<<std::min(count, nsm * 8), 256, 0, s>>>(dgs.as<BatchGraph>(), count, dstate.as<BatchGraphState>());
+  k_batch_mass<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dstate.as<BatchGraphState>());
   GAP_LAUNCH_CHECK();
+  ++launches;
   std::vector<BatchGraphState> hs(count);
   BatchCtrl hc;
   GAP_CUDA(cudaMemcpyAsync(hs.data(), dstate.p, sizeof(BatchGraphState) * count, cudaMemcpyDeviceToHost, s));
@@ -402,4 +667,10 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
     return hc.error;
   }
   return GAP_OK;
+}
+
+extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
+                                       int32_t max_iters, float* const* scores, gap_pr_stats_t* stats,
+                                       void* stream) {
+  return gap_pr_run_batch_ex(graphs, count, damping, tol, max_iters, nullptr, scores, stats, stream);
 }

@@ -47,10 +47,19 @@ EXPORTED = (
     "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
-    "gap_pr_run_batch", "gap_ppr_batch", "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
+    "gap_batch_tuning_default", "gap_pr_run_batch", "gap_pr_run_batch_ex", "gap_ppr_batch", "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
     "gap_ppr_server_info", "gap_ppr_server_destroy",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
+GAP_BATCH_MAX_GRAPHS = 65536
+
+
+class gap_batch_tuning(ctypes.Structure):
+    _fields_ = [("heavy_min_degree", ctypes.c_int32), ("chunk_arcs", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class gap_pr_options(ctypes.Structure):
@@ -141,7 +150,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_pr_run_ex": ([vp, dbl, dbl, i32, ctypes.POINTER(gap_pr_options), vp, vp], st),
         "gap_pr_stats": ([vp, ctypes.POINTER(gap_pr_stats_t)], st),
         "gap_pr_run_noalloc": ([vp, dbl, dbl, i32, vp, vp], st),
+        "gap_batch_tuning_default": ([ctypes.POINTER(gap_batch_tuning)], None),
         "gap_pr_run_batch": ([vp, i32, dbl, dbl, i32, vp, vp, vp], st),
+        "gap_pr_run_batch_ex": ([vp, i32, dbl, dbl, i32, ctypes.POINTER(gap_batch_tuning), vp, vp, vp],
+                                st),
         "gap_ppr_batch": ([vp, i32, vp, vp, dbl, dbl, i32, vp, vp, vp], st),
         "gap_ppr_server_create": ([vp, i32, ctypes.c_size_t, dbl, dbl, i32, ctypes.POINTER(vp)], st),
         "gap_ppr_submit": ([vp, vp, i32, vp, ctypes.POINTER(i64)], st),
@@ -310,10 +322,17 @@ def gap_pr_run_noalloc(h, damping: float, tol: float, max_iters: int, scores, st
                                             _stream(stream)), "gap_pr_run_noalloc")
 
 
+def gap_batch_tuning_default():
+    t = gap_batch_tuning()
+    load().gap_batch_tuning_default(ctypes.byref(t))
+    return t
+
+
 def gap_pr_run_batch(handles, scores, damping: float, tol: float, max_iters: int, stats=True,
-                     stream=None):
+                     stream=None, tuning=None):
     """PageRank on len(handles) graphs in one persistent launch (see gap.h);
-    scores[i] is a float32 device tensor of graph i's n floats.  Returns the
+    scores[i] is a float32 device tensor of graph i's n floats.  `tuning` is a
+    gap_batch_tuning or a dict of its fields (None = built-in).  Returns the
     per-graph stats dicts when `stats`."""
     count = len(handles)
     if len(scores) != count:
@@ -324,8 +343,17 @@ def gap_pr_run_batch(handles, scores, damping: float, tol: float, max_iters: int
                                               for h in handles])
     ps = (ctypes.c_void_p * max(count, 1))(*[_ptr(sc) for sc in scores])
     st = (gap_pr_stats_t * max(count, 1))() if stats else None
-    _check(load().gap_pr_run_batch(hs, count, damping, tol, max_iters, ps, st, _stream(stream)),
-           "gap_pr_run_batch")
+    if tuning is None:
+        rc = load().gap_pr_run_batch(hs, count, damping, tol, max_iters, ps, st, _stream(stream))
+    else:
+        if isinstance(tuning, dict):
+            t = gap_batch_tuning_default()
+            for k, v in tuning.items():
+                setattr(t, k, int(v))
+            tuning = t
+        rc = load().gap_pr_run_batch_ex(hs, count, damping, tol, max_iters, ctypes.byref(tuning), ps,
+                                        st, _stream(stream))
+    _check(rc, "gap_pr_run_batch")
     return [st[i].to_dict() for i in range(count)] if stats else None
 
 

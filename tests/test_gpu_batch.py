@@ -149,3 +149,39 @@ def test_batch_edge_arguments(cuda_device):
                                                           device="cuda:0")], D, 1e-4, 10)
     finally:
         g.close()
+
+
+def test_batch_tunings(cuda_device):
+    """Launch shape changes nothing (bit-identical); the heavy-row split only
+    reorders sums (FP32 bar vs the oracle).  A star with a hub of in-degree
+    3000 exercises rows of many chunks."""
+    hub_n = 3001
+    hsrc = np.arange(1, hub_n, dtype=np.int32)
+    hdst = np.zeros(hub_n - 1, np.int32)
+    specs = gapgen.batch_specs(count=6, seed=0x74, min_exp=9, max_exp=13)
+    members = make_batch(specs, [(hub_n, hsrc, hdst, True)])
+    graphs = [gpu_graph(n, s, d, sym) for (n, s, d, sym) in members]
+    try:
+        ref, st_ref = run_batch(graphs, 0.0, 15)
+        import torch
+        for tu in ({"block_threads": 128}, {"block_threads": 512}, {"blocks_per_sm": 1}):
+            xs = [torch.empty(g.n, dtype=torch.float32, device="cuda:0") for g in graphs]
+            st = gap.gap_pr_run_batch([g.handle for g in graphs], xs, D, 0.0, 15, tuning=tu)
+            for a, b, sa, sb in zip(xs, ref, st, st_ref):
+                assert np.array_equal(a.cpu().numpy().astype(np.float64), b)
+                assert sa["final_delta"] == sb["final_delta"]
+        for tu in ({"heavy_min_degree": 32, "chunk_arcs": 32}, {"heavy_min_degree": 100000},
+                   {"heavy_min_degree": 64, "chunk_arcs": 1000}):
+            xs = [torch.empty(g.n, dtype=torch.float32, device="cuda:0") for g in graphs]
+            st = gap.gap_pr_run_batch([g.handle for g in graphs], xs, D, 0.0, 15, tuning=tu)
+            for (n, s, d, sym), x, t in zip(members, xs, st):
+                check_member(x.cpu().numpy().astype(np.float64), t, n, s, d, sym, 0.0, 15)
+        for bad in ({"heavy_min_degree": 8}, {"chunk_arcs": 0}, {"block_threads": 96},
+                    {"blocks_per_sm": -1}):
+            with pytest.raises(gap.GapError) as e:
+                gap.gap_pr_run_batch([graphs[0].handle], [torch.empty(graphs[0].n, device="cuda:0")],
+                                     D, 0.0, 5, tuning=bad)
+            assert e.value.status == gap.GAP_ERR_INVALID_ARG
+    finally:
+        for g in graphs:
+            g.close()
