@@ -14,7 +14,18 @@ value = arcs traversed per second over the timed trials = sum(m * iterations)
 its own replica (the path has no exchange step on one graph per GPU: "replicas
 only"), time is the max over ranks and value sums all ranks' arcs.
 
+The same JSON line also carries (rank 0, N = 1, default --workload all):
+  "batch": PageRank on the uneven batch of 256 graphs (128 R-MAT + 128 grids,
+           2^10..2^18 vertices) in one persistent launch, Gedges/s and the
+           persistent kernel's roofline;
+  "ppr":   personalized-PageRank serving on a Chung-Lu graph (2^24 vertices,
+           5e8 arc draws, exponent 2.1): saturated queries/s, Poisson arrivals
+           at 0.25/0.5/0.9 of it with p50/p99 latency, and one-at-a-time
+           queries/s.
+--workload batch|ppr prints a line for that workload alone.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload all|pagerank|batch|ppr]
 """
 import argparse
 import json
@@ -55,6 +66,11 @@ def parse():
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="convergence loop driver (host: one launch per kernel, visible to ncu)")
     ap.add_argument("--segment-bytes", type=int, default=0, help="L2 blocking segment size (0 = default)")
+    ap.add_argument("--workload", default="all", choices=["all", "pagerank", "batch", "ppr"],
+                    help="all: the PageRank line with batch and ppr entries")
+    ap.add_argument("--ppr-seconds", type=float, default=6.0, help="arrival window per load level")
+    ap.add_argument("--ppr-scale", type=int, default=24)
+    ap.add_argument("--ppr-edges", type=float, default=5e8)
     return ap.parse_args()
 
 
@@ -232,26 +248,12 @@ def run_reference(a, ws, rank):
     }))
 
 
-def main():
-    a = parse()
-    ws, rank, local = dist_env()
-    if a.impl == "reference":
-        run_reference(a, ws, rank)
-        return
-
-    import numpy as np
+def run_pagerank(a, ws, rank, local, dev, pg):
+    """The headline line: K PageRank trials on the kron (or urand) graph."""
     import torch
 
     import gapgen
     from paper_1508_03619_gb300 import gap
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
 
     # ---- graph (untimed) ----
     if a.graph == "urand":
@@ -265,9 +267,17 @@ def main():
     n, m = g.n, g.m
     stream = torch.cuda.current_stream(dev)
     scores = torch.empty(n, dtype=torch.float32, device=dev)
-    opts = gap.gap_pr_options_default()
+    from paper_1508_03619_gb300 import tuning
+
+    def options():
+        """This GPU model's tuned options (autotuner table), --segment-bytes over them."""
+        o = tuning.pagerank_options(local)
+        if a.segment_bytes:
+            o.segment_bytes = a.segment_bytes
+        return o
+
+    opts = options()
     opts.loop = gap.GAP_LOOP_HOST if a.loop == "host" else gap.GAP_LOOP_GRAPH
-    opts.segment_bytes = a.segment_bytes
 
     def trial(out, o=opts):
         gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, o, out)
@@ -322,9 +332,8 @@ def main():
                    "the graph stays resident between trials (paper §2.3)"}
 
     # ---- per-kernel durations (CUDA events around every launch) ----
-    prof = gap.gap_pr_options_default()
+    prof = options()
     prof.timing = 1
-    prof.segment_bytes = a.segment_bytes
     trial(scores, prof)
     _, sp = gap.gap_pr_stats(g.handle)
     roofline = roofline_entry(sp, m, n, sp["segments"])
@@ -332,7 +341,7 @@ def main():
     # ---- FP64 GPU path on the same graph (metric: FP32 vs FP64 at L1 <= 1e-4) ----
     fp64 = None
     if not a.no_fp64:
-        o64 = gap.gap_pr_options_default()
+        o64 = options()
         o64.precision = gap.GAP_PREC_F64
         x64 = torch.empty(n, dtype=torch.float64, device=dev)
         gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, o64, x64)
@@ -352,10 +361,13 @@ def main():
         fp64 = {"value": v64, "unit": UNIT, "fp32_speedup": value / ws / v64 if v64 else None,
                 "l1_fp32_vs_fp64": l1, "iterations": s64["iterations"]}
 
+    g.close()
+    del scores, host_scores
+    if not a.no_fp64:
+        del x64
+    torch.cuda.empty_cache()
     if rank != 0:
-        if pg:
-            pg.destroy_process_group()
-        return
+        return None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
@@ -367,7 +379,228 @@ def main():
     }
     if not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(a)
-    print(json.dumps(line))
+    return line
+
+
+
+def batch_tuning():
+    """The per-GPU tuning table entry for this device (autotuned), else None
+    (the library's built-in values)."""
+    from paper_1508_03619_gb300 import tuning
+    return tuning.batch_tuning_for_device()
+
+
+def measure_batch(a, dev, steps, warmup):
+    """PageRank on the uneven 256-graph batch in one persistent launch per
+    step (tol 1e-4, each graph stops on its own).  The batch's CSCs (about
+    1 GB of indices) exceed L2, so no flush between steps."""
+    import numpy as np
+    import torch
+
+    import gapgen
+    from paper_1508_03619_gb300 import gap
+
+    specs = gapgen.batch_specs()
+    graphs = [gap.Graph.from_edges(s.n, *s.edges(), symmetrize=True) for s in specs]
+    ns = np.array([g.n for g in graphs], np.int64)
+    ms = np.array([g.m for g in graphs], np.int64)
+    xs = [torch.empty(g.n, dtype=torch.float32, device=dev) for g in graphs]
+    hs = [g.handle for g in graphs]
+    tu = batch_tuning()
+    for _ in range(warmup):
+        st = gap.gap_pr_run_batch(hs, xs, DAMPING, TOL, MAX_ITERS, tuning=tu)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    loop_ms = []
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        st = gap.gap_pr_run_batch(hs, xs, DAMPING, TOL, MAX_ITERS, tuning=tu)
+        loop_ms.append(st[0]["phase_ms"]["pull0"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_step = e0.elapsed_time(e1) / steps
+    its = np.array([t["iterations"] for t in st], np.int64)
+    arcs = float((its * ms).sum())
+    # algorithmic bytes: 8 per arc (index + gathered contribution), 24 per row
+    # per iteration (offsets, out-degree, x read and write, contribution write)
+    alg = float((its * (8 * ms + 24 * ns)).sum())
+    kern_ms = float(np.median(loop_ms))
+    peak, kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    out = {
+        "workload": "batch of 256 graphs: 128 R-MAT (2^10..2^18 vertices, edge factor 8..32, symmetrized) "
+                    "+ 128 grids (2^10..2^18 vertices, 5% edge deletions), FP32, d=0.85, tol=1e-4 per graph",
+        "graphs": len(graphs), "n_total": int(ns.sum()), "m_total": int(ms.sum()),
+        "iterations": {"min": int(its.min()), "max": int(its.max()), "mean": float(its.mean())},
+        "value": arcs / (ms_step / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms_step, "steps": steps,
+        "gpu_launches_per_step": st[0]["kernel_launches"],
+        "tuning": tu if tu is not None else gap.gap_batch_tuning_default().to_dict(),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_batch_persistent (all iterations of all graphs, one launch)",
+                     "alg_bytes_per_launch": alg, "launch_ms": kern_ms,
+                     "peak_source": f"{kind} hbm_gbs"},
+        "phase_ms": {k: st[0]["phase_ms"][k] for k in ("prep", "pull0", "output")},
+        "l2": "inputs larger than L2 (1+ GB of CSC per batch), no flush",
+    }
+    # the same graphs one trial at a time through gap_pr_run
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for h, x in zip(hs, xs):
+        gap.gap_pr_run(h, DAMPING, TOL, MAX_ITERS, x)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = e0.elapsed_time(e1)
+    out["one_graph_at_a_time"] = {"ms": seq_ms, "value": arcs / (seq_ms / 1e3) / 1e9,
+                                  "batch_speedup": seq_ms / ms_step}
+    for g in graphs:
+        g.close()
+    del xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_ppr(a, dev):
+    """Personalized-PageRank serving: a continuous-batching server over a
+    resident Chung-Lu graph.  Saturated throughput (a burst of queries), then
+    Poisson arrivals at 0.25/0.5/0.9 of it for --ppr-seconds each; latency is
+    completion minus scheduled arrival.  One-at-a-time: gap_ppr_batch with one
+    query per call."""
+    import numpy as np
+    import torch
+
+    import gapgen
+    from paper_1508_03619_gb300 import gap
+
+    n = 1 << a.ppr_scale
+    m_draw = int(a.ppr_edges)
+    src, dst = gapgen.chung_lu_device(n, m_draw, 2.1, 0x5C, device=dev)
+    g = gap.Graph.from_edges(n, src, dst, symmetrize=False)
+    del src, dst
+    torch.cuda.empty_cache()
+    outdeg = g.export_outdeg()
+    cand = np.flatnonzero(outdeg > 0)
+    rng = np.random.default_rng(0x5E)
+
+    def draw():
+        return rng.choice(cand, size=int(rng.integers(1, 65))).astype(np.int32)
+
+    res = {"workload": f"PPR serving on Chung-Lu n=2^{a.ppr_scale}, {m_draw:.3g} arc draws, exponent 2.1, "
+                       f"directed; queries of 1..64 seeds; FP32; d=0.85, tol=1e-4 per query",
+           "n": g.n, "m": g.m}
+    # one query at a time (one column per call)
+    one = torch.empty(n, dtype=torch.float32, device=dev)
+    gap.gap_ppr_batch(g.handle, np.array([0, 3], np.int64), draw()[:3], DAMPING, TOL, MAX_ITERS, one)
+    t0 = time.perf_counter()
+    k1 = 3
+    its1 = []
+    for _ in range(k1):
+        q = draw()
+        st = gap.gap_ppr_batch(g.handle, np.array([0, len(q)], np.int64), q, DAMPING, TOL, MAX_ITERS, one)
+        its1.append(st[0]["iterations"])
+    res["one_at_a_time_qps"] = k1 / (time.perf_counter() - t0)
+    res["one_at_a_time_iterations"] = its1
+    del one
+
+    srv = gap.PprServer(g.handle, max_cols=128, hbm_reserve=16 << 30, damping=DAMPING, tol=TOL,
+                        max_iters=MAX_ITERS)
+    cols = srv.info()["columns"]
+    ring = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3 * cols)]
+    owner = [None] * len(ring)
+    res["columns"] = cols
+
+    def run_arrivals(times):
+        """Submit at the scheduled times; returns (latencies_ms, makespan_s, iterations)."""
+        lat, iters = [], []
+        pending = []
+        start = time.perf_counter()
+        for j, ts in enumerate(times):
+            slot = j % len(ring)
+            if owner[slot] is not None:  # reuse a buffer only after its query finished
+                tk, t_sched, t_sub = owner[slot]
+                info = srv.wait(tk)
+                lat.append((t_sub - t_sched) * 1e3 + info["latency_ms"])
+                iters.append(info["iterations"])
+                pending.remove(slot)
+            now = time.perf_counter() - start
+            if ts > now:
+                time.sleep(ts - now)
+            t_sub = time.perf_counter() - start
+            owner[slot] = (srv.submit(draw(), ring[slot]), ts, t_sub)
+            pending.append(slot)
+        for slot in list(pending):
+            tk, t_sched, t_sub = owner[slot]
+            info = srv.wait(tk)
+            lat.append((t_sub - t_sched) * 1e3 + info["latency_ms"])
+            iters.append(info["iterations"])
+        for slot in range(len(owner)):
+            owner[slot] = None
+        return np.array(lat), time.perf_counter() - start, iters
+
+    run_arrivals([0.0] * cols)  # warm-up burst
+    burst = 2 * cols
+    lat, span, iters = run_arrivals([0.0] * burst)
+    sat = burst / span
+    res["saturated_qps"] = sat
+    res["saturated_iterations_mean"] = float(np.mean(iters))
+    loads = []
+    for f in (0.25, 0.5, 0.9):
+        lam = f * sat
+        gaps = rng.exponential(1.0 / lam, size=int(lam * a.ppr_seconds * 1.5) + 8)
+        times = np.cumsum(gaps)
+        times = times[times < a.ppr_seconds].tolist()
+        lat, span, _ = run_arrivals(times)
+        loads.append({"load": f, "arrival_qps": lam, "queries": len(times),
+                      "served_qps": len(times) / span if span > 0 else None,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))})
+    res["poisson"] = loads
+    res["batching_gain"] = sat / res["one_at_a_time_qps"]
+    srv.close()
+    g.close()
+    del ring
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    line = None
+    if a.workload in ("all", "pagerank"):
+        line = run_pagerank(a, ws, rank, local, dev, pg)
+        if line is not None and a.workload == "all" and ws == 1:
+            line["batch"] = measure_batch(a, dev, max(1, a.steps), max(3, a.warmup))
+            line["ppr"] = measure_ppr(a, dev)
+    elif rank == 0:
+        if a.workload == "batch":
+            b = measure_batch(a, dev, max(1, a.steps), max(1, a.warmup))
+            line = {"metric": METRIC, "value": b.pop("value"), "unit": UNIT, "n_gpus": 1,
+                    "steps": b["steps"], "warmup": a.warmup, "ms_per_step": b.pop("ms_per_step"),
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic", "config": {"workload": b.pop("workload")},
+                    "roofline": b.pop("roofline"), "batch": b}
+        else:
+            p = measure_ppr(a, dev)
+            line = {"metric": METRIC, "value": p["saturated_qps"], "unit": "queries/s", "n_gpus": 1,
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic", "config": {"workload": p.pop("workload")}, "ppr": p}
+    if line is not None:
+        print(json.dumps(line))
     if pg:
         pg.destroy_process_group()
 

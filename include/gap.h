@@ -232,7 +232,10 @@ GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
  *    pointers, scores[i] holding graphs[i]'s n_i floats (caller-owned; the
  *    arrays must not overlap).  A handle may not appear twice.
  *  - stats (optional, count entries): iterations, converged, final_delta,
- *    mass, delta_hist per graph; segments = 1 and bin fields zero.
+ *    mass, delta_hist per graph; segments = 1 and bin fields zero; every
+ *    entry carries the batch-wide device times (CUDA events) in phase_ms:
+ *    [GAP_PHASE_PREP] the set-up kernels (x0, chunk lists), [GAP_PHASE_PULL0]
+ *    the persistent kernel (all iterations), [GAP_PHASE_OUTPUT] the mass sums.
  *  - Scratch (2 n_i floats per graph, the chunk lists) comes from the
  *    library's stream-ordered pool and is released before return.
  *  - Blocks until the batch is done (it synchronizes `stream`).

@@ -27,9 +27,9 @@
 // The grid barrier is this file's own, used only inside a cooperative launch
 // (all blocks resident).  Each wait is bounded in time: a wait that gives up
 // sets an error code that every other waiter also sees, and all blocks leave.
-// Data written by other blocks during the launch (scores, contributions,
-// partials, accumulators) is read through L2 (ld.global.cg), never through the
-// non-coherent L1.
+// Data written by other blocks during the launch is read with coherent loads
+// after a fence: plain loads after the grid barrier, ld.global.cg for chunk
+// partials and accumulators; never with the non-coherent ld.global.nc.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -76,6 +76,14 @@ struct BatchGraphState {
   double mass;
   double delta_hist[GAP_PR_HIST];
 };
+
+// Contributions are gathered with plain (L1-cacheable) loads: they were
+// written before the last grid barrier, whose fences order those writes before
+// these reads (the PTX memory model's fence-fence synchronization), so a
+// cached line can never be stale.  Column indices are streamed once per
+// iteration and loaded with the evict-first hint to leave L1 to the gathers.
+__device__ __forceinline__ float gather_c(const float* p) { return *p; }
+__device__ __forceinline__ int load_idx(const int32_t* p) { return __ldcs(p); }
 
 constexpr unsigned long long BARRIER_WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr double DELTA_SCALE = 1152921504606846976.0;           // 2^60
@@ -173,7 +181,7 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
     const int64_t rbr = __shfl_sync(FULL, rb, rr);
     const int exr = __shfl_sync(FULL, excl, rr);
     float val = 0.f;
-    if (j < total) val = __ldcg(cin + __ldg(G.idx + rbr + (j - exr)));
+    if (j < total) val = gather_c(cin + load_idx(G.idx + rbr + (j - exr)));
     float xs = val;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -222,13 +230,14 @@ __device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t ci
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   int j = lane;
   for (; j + 96 < c.len; j += 128) {
-    const int u0 = __ldg(ix + j), u1 = __ldg(ix + j + 32), u2 = __ldg(ix + j + 64), u3 = __ldg(ix + j + 96);
-    s0 = __fadd_rn(s0, __ldcg(cin + u0));
-    s1 = __fadd_rn(s1, __ldcg(cin + u1));
-    s2 = __fadd_rn(s2, __ldcg(cin + u2));
-    s3 = __fadd_rn(s3, __ldcg(cin + u3));
+    const int u0 = load_idx(ix + j), u1 = load_idx(ix + j + 32), u2 = load_idx(ix + j + 64),
+              u3 = load_idx(ix + j + 96);
+    s0 = __fadd_rn(s0, gather_c(cin + u0));
+    s1 = __fadd_rn(s1, gather_c(cin + u1));
+    s2 = __fadd_rn(s2, gather_c(cin + u2));
+    s3 = __fadd_rn(s3, gather_c(cin + u3));
   }
-  for (; j < c.len; j += 32) s0 = __fadd_rn(s0, __ldcg(cin + __ldg(ix + j)));
+  for (; j < c.len; j += 32) s0 = __fadd_rn(s0, gather_c(cin + load_idx(ix + j)));
   float s = __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
   s = warp_sum(s);
   if (c.nch == 1) {
@@ -572,8 +581,18 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_TRY(dpart.get(sizeof(float) * chunk_cap, s));
   GAP_TRY(dctr.get(sizeof(unsigned int) * chunk_cap, s));
   GAP_TRY(dacc.get(sizeof(unsigned long long) * 3 * count, s));
+  // phase events: set-up kernels, the persistent kernel, the mass reduction
+  struct Events {
+    cudaEvent_t e[4] = {};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  for (cudaEvent_t& x : ev.e) GAP_CUDA(cudaEventCreate(&x));
   GAP_CUDA(cudaMemcpyAsync(dgs.p, hg.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s));
   GAP_CUDA(cudaMemsetAsync(dacc.p, 0, sizeof(unsigned long long) * 3 * count, s));
+  GAP_CUDA(cudaEventRecord(ev.e[0], s));
   const int setup_grid = std::min(count, nsm * 8);
   k_batch_init<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, tu.heavy_min_degree, tu.chunk_arcs,
                                           dcc.as<int64_t>());
@@ -585,6 +604,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
                                             dcb.as<int64_t>(), ddesc.as<ChunkDesc>(), dctr.as<unsigned int>());
   GAP_LAUNCH_CHECK();
   int launches = 3;
+  GAP_CUDA(cudaEventRecord(ev.e[1], s));
   if (max_iters > 0) {
     const BatchGraph* a_gs = dgs.as<BatchGraph>();
     int a_ng = count;
@@ -640,18 +660,30 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
     }
     ++launches;
   }
+  GAP_CUDA(cudaEventRecord(ev.e[2], s));
   k_batch_mass<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dstate.as<BatchGraphState>());
   GAP_LAUNCH_CHECK();
+  GAP_CUDA(cudaEventRecord(ev.e[3], s));
   ++launches;
   std::vector<BatchGraphState> hs(count);
   BatchCtrl hc;
   GAP_CUDA(cudaMemcpyAsync(hs.data(), dstate.p, sizeof(BatchGraphState) * count, cudaMemcpyDeviceToHost, s));
   GAP_CUDA(cudaMemcpyAsync(&hc, dctrl.p, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, s));
   GAP_CUDA(cudaStreamSynchronize(s));
+  float ms_prep = 0.f, ms_loop = 0.f, ms_out = 0.f;
+  GAP_CUDA(cudaEventElapsedTime(&ms_prep, ev.e[0], ev.e[1]));
+  GAP_CUDA(cudaEventElapsedTime(&ms_loop, ev.e[1], ev.e[2]));
+  GAP_CUDA(cudaEventElapsedTime(&ms_out, ev.e[2], ev.e[3]));
   if (stats) {
     for (int i = 0; i < count; ++i) {
       gap_pr_stats_t& o = stats[i];
       memset(&o, 0, sizeof(o));
+      o.phase_ms[GAP_PHASE_PREP] = ms_prep;
+      o.phase_ms[GAP_PHASE_PULL0] = ms_loop;
+      o.phase_ms[GAP_PHASE_OUTPUT] = ms_out;
+      o.phase_launches[GAP_PHASE_PREP] = 3;
+      o.phase_launches[GAP_PHASE_PULL0] = max_iters > 0 ? 1 : 0;
+      o.phase_launches[GAP_PHASE_OUTPUT] = 1;
       o.iterations = hs[i].iterations;
       o.converged = hs[i].converged;
       o.final_delta = hs[i].final_delta;
