@@ -34,7 +34,7 @@
 #include <cstring>
 #include <vector>
 
-#include "graph.cuh"
+#include "chunks.cuh"
 
 namespace gap {
 
@@ -49,15 +49,6 @@ struct BatchGraph {
   int64_t tiles;  // ceil(n / 32)
   float base;     // (1 - d) / n of this graph
   float pad;
-};
-
-struct ChunkDesc {
-  int64_t a0;     // first arc of the chunk
-  int64_t first;  // chunk id of the row's first chunk
-  int32_t len;    // arcs in the chunk
-  int32_t v;      // the row (vertex id in its graph)
-  int32_t nch;    // chunks of the row
-  int32_t pad;
 };
 
 struct BatchCtrl {
@@ -268,122 +259,29 @@ __device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t ci
 
 // ---- set-up: x0, contributions, chunk lists ----------------------------------
 
-__global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng, int heavy, int chunk,
-                             int64_t* chunk_count) {
-  __shared__ long long sh[32];
+__global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng) {
   for (int i = blockIdx.x; i < ng; i += gridDim.x) {
     const BatchGraph G = gs[i];
     const float x0 = (float)(1.0 / (double)G.n);
-    long long cc = 0;
     for (int64_t v = threadIdx.x; v < G.n; v += blockDim.x) {
       G.x[v] = x0;
       const int od = G.outdeg[v];
       G.c0[v] = od > 0 ? x0 / (float)od : 0.f;
-      const int64_t dg = G.off[v + 1] - G.off[v];
-      if (dg > heavy) cc += (dg + chunk - 1) / chunk;
     }
-    cc = block_sum(cc, sh);
-    if (threadIdx.x == 0) chunk_count[i] = cc;
-    __syncthreads();
   }
 }
 
-// One block: task and chunk bases of every graph (exclusive scans), totals,
-// per-graph state reset, and the control block.
-__global__ void k_batch_plan(const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ chunk_count,
-                             int64_t* task_base, int64_t* chunk_base, BatchGraphState* st, BatchCtrl* ctrl) {
-  __shared__ long long sh_t[1024], sh_c[1024];
-  __shared__ long long carry_t, carry_c;
-  if (threadIdx.x == 0) carry_t = carry_c = 0;
-  __syncthreads();
-  for (int b = 0; b < ng; b += blockDim.x) {
-    const int i = b + threadIdx.x;
-    long long t = 0, c = 0;
-    if (i < ng) {
-      c = chunk_count[i];
-      t = gs[i].tiles + c;
-      memset(&st[i], 0, sizeof(BatchGraphState));
-    }
-    sh_t[threadIdx.x] = t;
-    sh_c[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive Hillis-Steele scan
-      long long at = 0, ac = 0;
-      if ((int)threadIdx.x >= o) { at = sh_t[threadIdx.x - o]; ac = sh_c[threadIdx.x - o]; }
-      __syncthreads();
-      sh_t[threadIdx.x] += at;
-      sh_c[threadIdx.x] += ac;
-      __syncthreads();
-    }
-    if (i < ng) {
-      task_base[i] = carry_t + sh_t[threadIdx.x] - t;
-      chunk_base[i] = carry_c + sh_c[threadIdx.x] - c;
-    }
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) {
-      carry_t += sh_t[threadIdx.x];
-      carry_c += sh_c[threadIdx.x];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    task_base[ng] = carry_t;
-    chunk_base[ng] = carry_c;
-    memset(ctrl, 0, sizeof(BatchCtrl));
-    ctrl->ntasks = carry_t;
-    ctrl->nchunks = carry_c;
-  }
-}
-
-// Chunk descriptors of every heavy row, in row order (block per graph; an
-// ordered block-wide compaction over the rows).
-__global__ void k_batch_chunks(const BatchGraph* __restrict__ gs, int ng, int heavy, int chunk,
-                               const int64_t* __restrict__ chunk_base, ChunkDesc* desc, unsigned int* ctr) {
-  __shared__ long long warp_tot[32];
-  __shared__ long long run;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = blockIdx.x; i < ng; i += gridDim.x) {
-    const BatchGraph G = gs[i];
-    if (threadIdx.x == 0) run = chunk_base[i];
-    __syncthreads();
-    for (int64_t b = 0; b < G.n; b += blockDim.x) {
-      const int64_t v = b + threadIdx.x;
-      int64_t a0 = 0, dg = 0;
-      long long cnt = 0;
-      if (v < G.n) {
-        a0 = G.off[v];
-        dg = G.off[v + 1] - a0;
-        if (dg > heavy) cnt = (dg + chunk - 1) / chunk;
-      }
-      long long incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane == 31) warp_tot[wid] = incl;
-      __syncthreads();
-      long long before = run;
-      for (int w = 0; w < wid; ++w) before += warp_tot[w];
-      const long long first = before + incl - cnt;
-      for (long long k = 0; k < cnt; ++k) {
-        ChunkDesc cd;
-        cd.a0 = a0 + k * chunk;
-        cd.first = first;
-        cd.len = (int32_t)(dg - k * chunk < chunk ? dg - k * chunk : chunk);
-        cd.v = (int32_t)v;
-        cd.nch = (int32_t)cnt;
-        cd.pad = 0;
-        desc[first + k] = cd;
-        ctr[first + k] = 0;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        long long tot = 0;
-        for (int w = 0; w < nw; ++w) tot += warp_tot[w];
-        run += tot;
-      }
-      __syncthreads();
+// Task bases (tiles before graph i, from the host, plus chunks before graph
+// i), per-graph state reset and the control block.
+__global__ void k_batch_plan(int ng, const int64_t* __restrict__ tile_prefix, const int64_t* __restrict__ chunk_base,
+                             int64_t* task_base, BatchGraphState* st, BatchCtrl* ctrl) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= ng; i += gridDim.x * blockDim.x) {
+    task_base[i] = tile_prefix[i] + chunk_base[i];
+    if (i < ng) memset(&st[i], 0, sizeof(BatchGraphState));
+    if (i == ng) {
+      memset(ctrl, 0, sizeof(BatchCtrl));
+      ctrl->ntasks = task_base[i];
+      ctrl->nchunks = chunk_base[i];
     }
   }
 }
@@ -521,6 +419,8 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   int dev = 0;
   GAP_CUDA(cudaGetDevice(&dev));
   std::vector<BatchGraph> hg(count);
+  std::vector<ChunkGraph> hcg(count);
+  std::vector<int64_t> tile_prefix(count + 1, 0);
   int64_t cells = 0, chunk_cap = 0;
   for (int i = 0; i < count; ++i) {
     gap_graph* g = graphs[i];
@@ -545,10 +445,11 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
     hg[i].tiles = (g->n + 31) / 32;
     hg[i].base = (float)((1.0 - damping) / (double)g->n);
     hg[i].pad = 0.f;
+    hcg[i].off = g->in_off;
+    hcg[i].n = g->n;
+    tile_prefix[i + 1] = tile_prefix[i] + hg[i].tiles;
     cells += 2 * g->n;
-    // heavy rows have > heavy_min_degree arcs: at most m/(heavy+1) of them,
-    // each with ceil(deg/chunk) <= deg/chunk + 1 chunks
-    chunk_cap += g->m / tu.chunk_arcs + g->m / (tu.heavy_min_degree + 1) + 1;
+    chunk_cap += chunk_capacity(g->m, tu.heavy_min_degree, tu.chunk_arcs);
   }
   const int threads = tu.block_threads;
   const PersistentFn kfn = persistent_for(threads);
@@ -563,7 +464,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   const int nsm = device_info().sms;
   const int grid = nsm * per_sm;
 
-  Scratch cbuf, dgs, dstate, dctrl, dtb, dcb, dcc, ddesc, dpart, dctr, dacc;
+  Scratch cbuf, dgs, dstate, dctrl, dtb, dcb, dtp, dcg, ddesc, dpart, dctr, dacc;
   GAP_TRY(cbuf.get(sizeof(float) * cells, s));
   int64_t pos = 0;
   for (int i = 0; i < count; ++i) {
@@ -576,7 +477,8 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_TRY(dctrl.get(sizeof(BatchCtrl), s));
   GAP_TRY(dtb.get(sizeof(int64_t) * (count + 1), s));
   GAP_TRY(dcb.get(sizeof(int64_t) * (count + 1), s));
-  GAP_TRY(dcc.get(sizeof(int64_t) * count, s));
+  GAP_TRY(dtp.get(sizeof(int64_t) * (count + 1), s));
+  GAP_TRY(dcg.get(sizeof(ChunkGraph) * count, s));
   GAP_TRY(ddesc.get(sizeof(ChunkDesc) * chunk_cap, s));
   GAP_TRY(dpart.get(sizeof(float) * chunk_cap, s));
   GAP_TRY(dctr.get(sizeof(unsigned int) * chunk_cap, s));
@@ -593,17 +495,18 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_CUDA(cudaMemcpyAsync(dgs.p, hg.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s));
   GAP_CUDA(cudaMemsetAsync(dacc.p, 0, sizeof(unsigned long long) * 3 * count, s));
   GAP_CUDA(cudaEventRecord(ev.e[0], s));
+  GAP_CUDA(cudaMemcpyAsync(dtp.p, tile_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  GAP_CUDA(cudaMemcpyAsync(dcg.p, hcg.data(), sizeof(ChunkGraph) * count, cudaMemcpyHostToDevice, s));
   const int setup_grid = std::min(count, nsm * 8);
-  k_batch_init<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, tu.heavy_min_degree, tu.chunk_arcs,
-                                          dcc.as<int64_t>());
+  k_batch_init<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count);
   GAP_LAUNCH_CHECK();
-  k_batch_plan<<<1, 1024, 0, s>>>(dgs.as<BatchGraph>(), count, dcc.as<int64_t>(), dtb.as<int64_t>(),
-                                  dcb.as<int64_t>(), dstate.as<BatchGraphState>(), dctrl.as<BatchCtrl>());
+  ChunkBuilder cb;
+  GAP_TRY(build_chunks(&cb, dcg.as<ChunkGraph>(), hcg.data(), count, tu.heavy_min_degree, tu.chunk_arcs,
+                       ddesc.as<ChunkDesc>(), dctr.as<unsigned int>(), dcb.as<int64_t>(), s));
+  k_batch_plan<<<(count + 256) / 256, 256, 0, s>>>(count, dtp.as<int64_t>(), dcb.as<int64_t>(), dtb.as<int64_t>(),
+                                                   dstate.as<BatchGraphState>(), dctrl.as<BatchCtrl>());
   GAP_LAUNCH_CHECK();
-  k_batch_chunks<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, tu.heavy_min_degree, tu.chunk_arcs,
-                                            dcb.as<int64_t>(), ddesc.as<ChunkDesc>(), dctr.as<unsigned int>());
-  GAP_LAUNCH_CHECK();
-  int launches = 3;
+  int launches = 5;
   GAP_CUDA(cudaEventRecord(ev.e[1], s));
   if (max_iters > 0) {
     const BatchGraph* a_gs = dgs.as<BatchGraph>();
@@ -681,7 +584,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
       o.phase_ms[GAP_PHASE_PREP] = ms_prep;
       o.phase_ms[GAP_PHASE_PULL0] = ms_loop;
       o.phase_ms[GAP_PHASE_OUTPUT] = ms_out;
-      o.phase_launches[GAP_PHASE_PREP] = 3;
+      o.phase_launches[GAP_PHASE_PREP] = 5;
       o.phase_launches[GAP_PHASE_PULL0] = max_iters > 0 ? 1 : 0;
       o.phase_launches[GAP_PHASE_OUTPUT] = 1;
       o.iterations = hs[i].iterations;

@@ -8,24 +8,37 @@
 // gathers one coalesced KP-wide row C[u][*].  A per-vertex bitmask says which
 // columns have the vertex as a seed.
 //
-// Column independence: the arithmetic of column j — the sum over a row's arcs
-// in ascending order, x' = b + d*s, c' = x'/outdeg, and |x' - x| reduced over
-// fixed 256-row blocks in a fixed order — does not depend on KP, on the slot
-// j occupies, or on the other columns, so a query's result and its iteration
-// count are the same alone and in any mix.  A column that met its tolerance
-// (or max_iters) stops updating at once, like a run of its own would.
+// Work: rows with at most PPR_HEAVY in-arcs are pulled in 256-row blocks (32
+// row slots x 8 rounds; a slot's LR lanes cover 4 columns each); heavier rows
+// are split into chunks of PPR_CHUNK arcs (chunks.cuh) pulled one chunk per
+// row slot, so no block waits on a hub row.  A row of several chunks is
+// finished by the slot that completes its last chunk, which adds the chunk
+// sums in chunk order.
+//
+// Column independence: the arithmetic of column j — within a row (or chunk)
+// the sum over arcs in ascending order, a chunked row's chunk sums added in
+// chunk order, x' = b + d*s, c' = x'/outdeg — depends only on the graph (the
+// chunk split uses fixed PPR_HEAVY / PPR_CHUNK), never on KP, on the slot j
+// occupies, or on the other columns.  The L1 delta of column j is a sum of
+// FP64 terms (per 256-row block, or per chunked row) each rounded to a
+// multiple of 2^-60 and added as 64-bit integers, which is exact and
+// independent of order.  So a query's result and its iteration count are the
+// same alone and in any mix.  A column that met its tolerance (or max_iters)
+// stops updating at once, like a run of its own would.
 #include <algorithm>
 #include <vector>
 
+#include "chunks.cuh"
 #include "graph.cuh"
 #include "ppr.cuh"
 
 namespace gap {
 
-constexpr int PPR_ROWS = 32;        // rows per CTA round (one per row slot)
+constexpr int PPR_ROWS = 32;        // row slots per CTA
 constexpr int PPR_SUB = 8;          // rounds per delta block
-constexpr int PPR_BLOCK_ROWS = PPR_ROWS * PPR_SUB;  // 256 rows per delta partial
+constexpr int PPR_BLOCK_ROWS = PPR_ROWS * PPR_SUB;  // 256 rows per delta block
 constexpr int PPR_KMAX = 128;
+constexpr double PPR_DELTA_SCALE = 1152921504606846976.0;  // 2^60
 
 struct PprArgs {
   const int64_t* __restrict__ off;
@@ -41,110 +54,173 @@ struct PprArgs {
   const float* __restrict__ base;         // [KP] (1-d)/|S_j|
   const int32_t* __restrict__ active;     // [KP] 1: column updates this iteration
   float d;
-  double* partial;                        // [nblocks][KP]
+  const ChunkDesc* __restrict__ chunks;   // heavy-row chunks
+  int64_t nchunks;
+  float* cpart;                           // [nchunks][KP] chunk sums of multi-chunk rows
+  unsigned int* cctr;                     // [nchunks] finished chunks, at the row's first chunk
+  unsigned long long* acc;                // [KP] fixed-point L1 delta of this iteration
 };
 
-// One CTA = 32 row slots x LR lanes; lane g of a row covers columns 4g..4g+3.
+__device__ __forceinline__ unsigned long long ppr_fixed(double v) {
+  return (unsigned long long)__double2ull_rn(v * PPR_DELTA_SCALE);
+}
+
+// Sequential (ascending) sums of 4 columns over arcs [b, e).
+__device__ __forceinline__ float4 ppr_row_sum(const PprArgs& a, int64_t b, int64_t e, int col0) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int64_t j = b;
+  for (; j + 3 < e; j += 4) {
+    const int32_t u0 = __ldcs(a.idx + j), u1 = __ldcs(a.idx + j + 1), u2 = __ldcs(a.idx + j + 2),
+                  u3 = __ldcs(a.idx + j + 3);
+    const float4 c0 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u0 * a.KP + col0));
+    const float4 c1 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u1 * a.KP + col0));
+    const float4 c2 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u2 * a.KP + col0));
+    const float4 c3 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u3 * a.KP + col0));
+    s0 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s0, c0.x), c1.x), c2.x), c3.x);
+    s1 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s1, c0.y), c1.y), c2.y), c3.y);
+    s2 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s2, c0.z), c1.z), c2.z), c3.z);
+    s3 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s3, c0.w), c1.w), c2.w), c3.w);
+  }
+  for (; j < e; ++j) {
+    const float4 c = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)__ldcs(a.idx + j) * a.KP + col0));
+    s0 = __fadd_rn(s0, c.x);
+    s1 = __fadd_rn(s1, c.y);
+    s2 = __fadd_rn(s2, c.z);
+    s3 = __fadd_rn(s3, c.w);
+  }
+  return make_float4(s0, s1, s2, s3);
+}
+
+// Update of row v, columns col0..col0+3, from their in-sums; adds |x' - x| of
+// the active columns to dl[].
+__device__ __forceinline__ void ppr_update(const PprArgs& a, int64_t v, int col0, float4 s4, const int* act,
+                                           const float* bq, double* dl) {
+  const float sum[4] = {s4.x, s4.y, s4.z, s4.w};
+  const uint32_t mw = a.seedmask[v * a.mask_words + (col0 >> 5)];
+  const int deg = a.outdeg[v];
+  float* xr = a.x + v * a.KP + col0;
+  float* cr = a.cout + v * a.KP + col0;
+  const float4 xo4 = __ldcg(reinterpret_cast<const float4*>(xr));
+  const float xo[4] = {xo4.x, xo4.y, xo4.z, xo4.w};
+  float xn[4], cn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (act[q]) {
+      const float bb = (mw >> ((col0 + q) & 31)) & 1u ? bq[q] : 0.f;
+      xn[q] = __fadd_rn(bb, __fmul_rn(a.d, sum[q]));
+      const double dd = (double)xn[q] - (double)xo[q];
+      dl[q] += dd < 0 ? -dd : dd;
+    } else {
+      xn[q] = xo[q];  // frozen column: keep its scores
+    }
+    cn[q] = deg > 0 ? xn[q] / (float)deg : 0.f;
+  }
+  __stcg(reinterpret_cast<float4*>(xr), make_float4(xn[0], xn[1], xn[2], xn[3]));
+  __stcg(reinterpret_cast<float4*>(cr), make_float4(cn[0], cn[1], cn[2], cn[3]));
+}
+
+// One CTA = 32 row slots x LR lanes; lane g of a slot covers columns 4g..4g+3.
 template <int LR>
 __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
-  __shared__ double sh[PPR_ROWS][PPR_KMAX];
+  constexpr int K = 4 * LR;  // == KP
+  __shared__ double sh[PPR_ROWS][K];
+  __shared__ int slot_last[PPR_ROWS];
   const int g = threadIdx.x % LR;
   const int r = threadIdx.x / LR;
   const int col0 = 4 * g;
   const int64_t nblocks = (a.n + PPR_BLOCK_ROWS - 1) / PPR_BLOCK_ROWS;
   int act[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) act[q] = a.active[col0 + q];
   float bq[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) bq[q] = a.base[col0 + q];
+  for (int q = 0; q < 4; ++q) {
+    act[q] = a.active[col0 + q];
+    bq[q] = a.base[col0 + q];
+  }
+  unsigned long long qblk = 0;                  // column threadIdx.x (< K): light-block terms
+  unsigned long long qrow[4] = {0, 0, 0, 0};    // columns col0..+3: chunked-row terms
+  // ---- light rows, 256-row blocks ----
   for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
     double dacc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int sub = 0; sub < PPR_SUB; ++sub) {
       const int64_t v = blk * PPR_BLOCK_ROWS + sub * PPR_ROWS + r;
       if (v >= a.n) break;
       const int64_t b = a.off[v], e = a.off[v + 1];
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int64_t j = b;
-      for (; j + 3 < e; j += 4) {
-        const int32_t u0 = __ldcs(a.idx + j), u1 = __ldcs(a.idx + j + 1), u2 = __ldcs(a.idx + j + 2),
-                      u3 = __ldcs(a.idx + j + 3);
-        const float4 c0 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u0 * a.KP + col0));
-        const float4 c1 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u1 * a.KP + col0));
-        const float4 c2 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u2 * a.KP + col0));
-        const float4 c3 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u3 * a.KP + col0));
-        s0 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s0, c0.x), c1.x), c2.x), c3.x);
-        s1 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s1, c0.y), c1.y), c2.y), c3.y);
-        s2 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s2, c0.z), c1.z), c2.z), c3.z);
-        s3 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s3, c0.w), c1.w), c2.w), c3.w);
-      }
-      for (; j < e; ++j) {
-        const float4 c = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)__ldcs(a.idx + j) * a.KP + col0));
-        s0 = __fadd_rn(s0, c.x);
-        s1 = __fadd_rn(s1, c.y);
-        s2 = __fadd_rn(s2, c.z);
-        s3 = __fadd_rn(s3, c.w);
-      }
-      const float sum[4] = {s0, s1, s2, s3};
-      const uint32_t mw = a.seedmask[v * a.mask_words + (col0 >> 5)];
-      const int deg = a.outdeg[v];
-      float* xr = a.x + v * a.KP + col0;
-      float* cr = a.cout + v * a.KP + col0;
-      const float4 xo4 = *reinterpret_cast<const float4*>(xr);
-      const float xo[4] = {xo4.x, xo4.y, xo4.z, xo4.w};
-      float xn[4], cn[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (act[q]) {
-          const float bb = (mw >> ((col0 + q) & 31)) & 1u ? bq[q] : 0.f;
-          xn[q] = __fadd_rn(bb, __fmul_rn(a.d, sum[q]));
-          const double dd = (double)xn[q] - (double)xo[q];
-          dacc[q] += dd < 0 ? -dd : dd;
-        } else {
-          xn[q] = xo[q];  // frozen column: keep its scores
-        }
-        cn[q] = deg > 0 ? xn[q] / (float)deg : 0.f;
-      }
-      *reinterpret_cast<float4*>(xr) = make_float4(xn[0], xn[1], xn[2], xn[3]);
-      *reinterpret_cast<float4*>(cr) = make_float4(cn[0], cn[1], cn[2], cn[3]);
+      if (e - b > PPR_HEAVY) continue;  // a chunked row
+      ppr_update(a, v, col0, ppr_row_sum(a, b, e, col0), act, bq, dacc);
     }
     // per-column sum over the 32 row slots, in slot order
 #pragma unroll
     for (int q = 0; q < 4; ++q) sh[r][col0 + q] = dacc[q];
     __syncthreads();
-    for (int c = threadIdx.x; c < a.KP; c += blockDim.x) {
+    if (threadIdx.x < K) {
       double t = 0.0;
-      for (int rr = 0; rr < PPR_ROWS; ++rr) t += sh[rr][c];
-      a.partial[blk * a.KP + c] = t;
+      for (int rr = 0; rr < PPR_ROWS; ++rr) t += sh[rr][threadIdx.x];
+      qblk += ppr_fixed(t);
     }
     __syncthreads();
   }
-}
-
-// Two-level fixed-order reduction of the per-block partials: out[grp][c] =
-// sum of partial[grp*FAN + i][c] for i ascending.
-constexpr int PPR_FAN = 256;
-__global__ void k_ppr_reduce(const double* __restrict__ partial, int64_t nblocks, int KP, double* __restrict__ out) {
-  const int64_t grp = blockIdx.x;
-  for (int c = threadIdx.x; c < KP; c += blockDim.x) {
-    double t = 0.0;
-    const int64_t b0 = grp * PPR_FAN, b1 = std::min<int64_t>(b0 + PPR_FAN, nblocks);
-    for (int64_t bb = b0; bb < b1; ++bb) t += partial[bb * KP + c];
-    out[grp * KP + c] = t;
+  // ---- chunks of heavy rows, one per row slot ----
+  for (int64_t c0 = (int64_t)blockIdx.x * PPR_ROWS; c0 < a.nchunks; c0 += (int64_t)gridDim.x * PPR_ROWS) {
+    const int64_t cid = c0 + r;
+    ChunkDesc cd;
+    cd.nch = 0;
+    float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (cid < a.nchunks) {
+      cd = a.chunks[cid];
+      s4 = ppr_row_sum(a, cd.a0, cd.a0 + cd.len, col0);
+    }
+    if (cd.nch == 1) {
+      double dl[4] = {0.0, 0.0, 0.0, 0.0};
+      ppr_update(a, cd.v, col0, s4, act, bq, dl);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) qrow[q] += ppr_fixed(dl[q]);
+    } else if (cd.nch > 1) {
+      __stcg(reinterpret_cast<float4*>(a.cpart + cid * a.KP + col0), s4);
+      __threadfence();
+    }
+    __syncthreads();  // every lane's partial is fenced before its slot counts the chunk
+    if (g == 0) {
+      int last = 0;
+      if (cd.nch > 1) last = atomicAdd(a.cctr + cd.first, 1u) + 1u == (unsigned)cd.nch;
+      slot_last[r] = last;
+    }
+    __syncthreads();
+    if (slot_last[r]) {
+      __threadfence();
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      for (int k = 0; k < cd.nch; ++k) {  // chunk sums in chunk order
+        const float4 p = __ldcg(reinterpret_cast<const float4*>(a.cpart + (cd.first + k) * a.KP + col0));
+        t0 = __fadd_rn(t0, p.x);
+        t1 = __fadd_rn(t1, p.y);
+        t2 = __fadd_rn(t2, p.z);
+        t3 = __fadd_rn(t3, p.w);
+      }
+      double dl[4] = {0.0, 0.0, 0.0, 0.0};
+      ppr_update(a, cd.v, col0, make_float4(t0, t1, t2, t3), act, bq, dl);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) qrow[q] += ppr_fixed(dl[q]);
+      if (g == 0) a.cctr[cd.first] = 0u;  // ready for the next iteration
+    }
   }
+  if (threadIdx.x < K && qblk) atomicAdd(a.acc + threadIdx.x, qblk);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (qrow[q]) atomicAdd(a.acc + col0 + q, qrow[q]);
 }
 
-// Per column: delta, history, stop test; active flags for the next iteration.
-__global__ void k_ppr_finalize(PprCtrl* ctrl, const double* __restrict__ part2, int64_t ngrp, int KP, double tol,
-                               int32_t max_iters, cudaGraphConditionalHandle handle, int use_handle) {
+// Per column: delta, history, stop test; active flags for the next iteration;
+// the delta accumulators start again at zero.
+__global__ void k_ppr_finalize(PprCtrl* ctrl, int KP, double tol, int32_t max_iters,
+                               cudaGraphConditionalHandle handle, int use_handle) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int c = threadIdx.x; c < KP; c += blockDim.x) {
     PprColumn& col = ctrl->col[c];
+    const unsigned long long q = ctrl->acc[c];
+    ctrl->acc[c] = 0ull;
     if (!col.active) continue;
-    double t = 0.0;
-    for (int64_t gI = 0; gI < ngrp; ++gI) t += part2[gI * KP + c];
+    const double t = (double)q / PPR_DELTA_SCALE;
     const int k = col.iterations;
     if (k < GAP_PPR_HIST) col.delta_hist[k] = t;
     col.final_delta = t;
@@ -218,20 +294,46 @@ gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStr
   e->mask_words = (kp + 31) / 32;
   e->d = d;
   e->nblocks = (g->n + PPR_BLOCK_ROWS - 1) / PPR_BLOCK_ROWS;
-  e->ngrp = (e->nblocks + PPR_FAN - 1) / PPR_FAN;
   const size_t cells = (size_t)g->n * kp;
   GAP_TRY(e->xbuf.get(sizeof(float) * cells, s));
   GAP_TRY(e->cbuf.get(2 * sizeof(float) * cells, s));
   GAP_TRY(e->mask.get(sizeof(uint32_t) * g->n * e->mask_words, s));
-  GAP_TRY(e->part.get(sizeof(double) * e->nblocks * kp, s));
-  GAP_TRY(e->part2.get(sizeof(double) * e->ngrp * kp, s));
   GAP_TRY(e->ctrl.get(sizeof(PprCtrl), s));
+  // chunk list of the heavy rows (fixed split: part of every column's arithmetic)
+  const int64_t cap = chunk_capacity(g->m, PPR_HEAVY, PPR_CHUNK);
+  GAP_TRY(e->chunks.get(sizeof(ChunkDesc) * cap, s));
+  GAP_TRY(e->cctr.get(sizeof(unsigned int) * cap, s));
+  {
+    Scratch dg, cbase;
+    ChunkGraph hg{g->in_off, g->n};
+    GAP_TRY(dg.get(sizeof(ChunkGraph), s));
+    GAP_TRY(cbase.get(sizeof(int64_t) * 2, s));
+    GAP_CUDA(cudaMemcpyAsync(dg.p, &hg, sizeof(ChunkGraph), cudaMemcpyHostToDevice, s));
+    ChunkBuilder cb;
+    GAP_TRY(build_chunks(&cb, dg.as<ChunkGraph>(), &hg, 1, PPR_HEAVY, PPR_CHUNK, e->chunks.as<ChunkDesc>(),
+                         e->cctr.as<unsigned int>(), cbase.as<int64_t>(), s));
+    int64_t hb[2] = {0, 0};
+    GAP_CUDA(cudaMemcpyAsync(hb, cbase.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    GAP_CUDA(cudaStreamSynchronize(s));
+    e->nchunks = hb[1];
+  }
+  GAP_TRY(e->cpart.get(sizeof(float) * (size_t)(e->nchunks > 0 ? e->nchunks : 1) * kp, s));
   GAP_CUDA(cudaMemsetAsync(e->xbuf.p, 0, sizeof(float) * cells, s));
   GAP_CUDA(cudaMemsetAsync(e->cbuf.p, 0, 2 * sizeof(float) * cells, s));
   GAP_CUDA(cudaMemsetAsync(e->mask.p, 0, sizeof(uint32_t) * g->n * e->mask_words, s));
   k_ppr_ctrl_init<<<1, 32, 0, s>>>(e->ctrl.as<PprCtrl>());
   GAP_LAUNCH_CHECK();
   return GAP_OK;
+}
+
+void ppr_engine_release(PprEngine* e) {
+  e->xbuf.release();
+  e->cbuf.release();
+  e->mask.release();
+  e->ctrl.release();
+  e->chunks.release();
+  e->cctr.release();
+  e->cpart.release();
 }
 
 float* ppr_c(PprEngine* e, int which) {
@@ -280,23 +382,35 @@ gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStre
   a.base = ctrl->base;
   a.active = ctrl->active;
   a.d = (float)e->d;
-  a.partial = e->part.as<double>();
+  a.chunks = e->chunks.as<ChunkDesc>();
+  a.nchunks = e->nchunks;
+  a.cpart = e->cpart.as<float>();
+  a.cctr = e->cctr.as<unsigned int>();
+  a.acc = ctrl->acc;
   const int LR = e->KP / 4;
   const int threads = PPR_ROWS * LR;
-  const int grid = (int)std::min<int64_t>(e->nblocks, (int64_t)device_info().sms * std::max(1, 2048 / threads));
+  const void* fn = nullptr;
   switch (LR) {
-    case 1: k_ppr_spmm<1><<<grid, threads, 0, s>>>(a); break;
-    case 2: k_ppr_spmm<2><<<grid, threads, 0, s>>>(a); break;
-    case 4: k_ppr_spmm<4><<<grid, threads, 0, s>>>(a); break;
-    case 8: k_ppr_spmm<8><<<grid, threads, 0, s>>>(a); break;
-    case 16: k_ppr_spmm<16><<<grid, threads, 0, s>>>(a); break;
-    case 32: k_ppr_spmm<32><<<grid, threads, 0, s>>>(a); break;
+    case 1: fn = (const void*)k_ppr_spmm<1>; break;
+    case 2: fn = (const void*)k_ppr_spmm<2>; break;
+    case 4: fn = (const void*)k_ppr_spmm<4>; break;
+    case 8: fn = (const void*)k_ppr_spmm<8>; break;
+    case 16: fn = (const void*)k_ppr_spmm<16>; break;
+    case 32: fn = (const void*)k_ppr_spmm<32>; break;
     default: set_error("bad column width %d", e->KP); return GAP_ERR_INVALID_ARG;
   }
+  // one wave of resident CTAs, grid-striding over row blocks and chunks
+  if (e->resident == 0) {
+    int per_sm = 0;
+    GAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0));
+    e->resident = std::max(1, per_sm) * device_info().sms;
+  }
+  const int64_t work = std::max<int64_t>(e->nblocks, (e->nchunks + PPR_ROWS - 1) / PPR_ROWS);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(work, e->resident));
+  void* args[] = {&a};
+  GAP_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, s));
   GAP_LAUNCH_CHECK();
-  k_ppr_reduce<<<(unsigned)e->ngrp, 128, 0, s>>>(e->part.as<double>(), e->nblocks, e->KP, e->part2.as<double>());
-  GAP_LAUNCH_CHECK();
-  k_ppr_finalize<<<1, 128, 0, s>>>(ctrl, e->part2.as<double>(), e->ngrp, e->KP, tol, max_iters, h, use_h);
+  k_ppr_finalize<<<1, 128, 0, s>>>(ctrl, e->KP, tol, max_iters, h, use_h);
   GAP_LAUNCH_CHECK();
   e->parity ^= 1;
   return GAP_OK;

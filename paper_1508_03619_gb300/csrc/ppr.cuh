@@ -8,6 +8,10 @@ namespace gap {
 
 constexpr int GAP_PPR_HIST = 64;
 constexpr int PPR_COLS_MAX = 128;
+// Rows with more in-arcs than PPR_HEAVY are pulled in chunks of PPR_CHUNK arcs.
+// Both are fixed: the split is part of every column's summation order.
+constexpr int PPR_HEAVY = 128;
+constexpr int PPR_CHUNK = 256;
 
 struct PprColumn {
   int32_t active;      // updates in the next iteration
@@ -23,6 +27,7 @@ struct PprCtrl {
   int32_t any_active;  // some column still iterating
   int32_t active[PPR_COLS_MAX];
   float base[PPR_COLS_MAX];  // (1-d)/|S_j|
+  unsigned long long acc[PPR_COLS_MAX];  // this iteration's L1 delta, units of 2^-60
   PprColumn col[PPR_COLS_MAX];
 };
 
@@ -32,9 +37,11 @@ struct PprEngine {
   int KP = 0;
   int mask_words = 1;
   double d = 0.85;
-  int64_t nblocks = 0, ngrp = 0;
+  int64_t nblocks = 0;
+  int64_t nchunks = 0;
+  int resident = 0;  // CTAs of the SpMM kernel resident at once (set on first step)
   int parity = 0;
-  Scratch xbuf, cbuf, mask, part, part2, ctrl;
+  Scratch xbuf, cbuf, mask, ctrl, chunks, cctr, cpart;
 };
 
 gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStream_t s);
@@ -44,6 +51,7 @@ gap_status ppr_engine_set_column(PprEngine* e, int col, const int32_t* d_seeds, 
 gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStream_t s,
                            cudaGraphConditionalHandle h, int use_h);
 gap_status ppr_engine_extract(PprEngine* e, int col, float* out, cudaStream_t s);
+void ppr_engine_release(PprEngine* e);  // scratch released in stream order
 int ppr_width_for(int q);
 
 }  // namespace gap

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "chunks.cuh"
 #include "ppr.cuh"
 
 namespace gap {
@@ -178,12 +179,7 @@ static void srv_free(gap_ppr_server* S) {
   for (auto& kv : S->all) delete kv.second;
   S->all.clear();
   // the engine's scratch is released on its stream by its destructors
-  S->eng.xbuf.release();
-  S->eng.cbuf.release();
-  S->eng.mask.release();
-  S->eng.part.release();
-  S->eng.part2.release();
-  S->eng.ctrl.release();
+  ppr_engine_release(&S->eng);
   if (S->s) {
     cudaStreamSynchronize(S->s);
     cudaStreamDestroy(S->s);
@@ -213,8 +209,9 @@ gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_re
   int kp = ppr_width_for(max_cols);
   auto need = [&](int k) {
     const double cells = (double)g->n * k;
+    const double chunks = (double)chunk_capacity(g->m, PPR_HEAVY, PPR_CHUNK);
     return cells * 12.0 + (double)g->n * 4.0 * ((k + 31) / 32) + (double)g->n * 4.0 + (double)k * SERVER_MAX_SEEDS * 4.0 +
-           (double)((g->n + 255) / 256) * k * 8.0 + (64 << 20);
+           chunks * (sizeof(ChunkDesc) + 4.0 + 4.0 * k) + (64 << 20);
   };
   while (kp > 4 && need(kp) + (double)hbm_reserve > (double)free_b) kp /= 2;
   if (need(kp) + (double)hbm_reserve > (double)free_b) {

@@ -32,9 +32,19 @@ def run_ppr(g, offs, seeds, tol, iters):
     return out.cpu().numpy().reshape(q, g.n).astype(np.float64), st
 
 
+def _hub_graph():
+    """A hub with 3000 in-arcs (12 chunks of 256) plus a sparse random part."""
+    n = 3001
+    rs = np.random.default_rng(7)
+    src = np.concatenate([np.arange(1, n), rs.integers(0, n, 6000)]).astype(np.int32)
+    dst = np.concatenate([np.zeros(n - 1, np.int64), rs.integers(0, n, 6000)]).astype(np.int32)
+    return src, dst
+
+
 CASES = [
     ("kron13", 1 << 13, *gapgen.kron(13, 16, 0x51), True),
     ("chunglu", 1 << 13, *gapgen.chung_lu(1 << 13, 16 << 13, 2.1, 0x52), False),
+    ("hub", 3001, *_hub_graph(), False),
 ]
 
 
