@@ -154,7 +154,10 @@ typedef struct {
   uint32_t kahan_hubs;    /* compensated sums on rows above hub_threshold in-edges */
   int64_t hub_threshold;  /* default 10000 */
   uint32_t deterministic; /* FP64: thread-per-row ascending-source sums */
-  uint32_t l2_window;     /* L2 persistence window on the contribution arrays */
+  uint32_t l2_window;     /* 1: mark the two contribution arrays persisting in L2
+                             (an access policy window) when they fit in the
+                             device's persisting carve-out and no L2 blocking is
+                             active; results are unchanged, only caching */
   uint32_t loop;          /* GAP_LOOP_GRAPH | GAP_LOOP_HOST */
   uint32_t timing;        /* 1: time every kernel with CUDA events (forces the host
                              loop); per-phase times land in gap_pr_stats_t */
@@ -207,6 +210,8 @@ typedef struct {
   double phase_ms[GAP_PR_PHASES]; /* summed kernel time per phase (options.timing) */
   int32_t phase_launches[GAP_PR_PHASES];
   int32_t kernel_launches; /* CUDA kernels this run launched (set by gap_pr_stats) */
+  int32_t pad0;
+  int64_t l2_window_bytes; /* bytes marked persisting in L2 (options.l2_window), 0 if none */
 } gap_pr_stats_t;
 
 /* Synchronize the stream of the last run on g and report it.  Returns GAP_OK,

@@ -33,6 +33,8 @@ struct gap_graph {
   int32_t launches_fixed = 0;            // kernels of the last run outside the loop
   int32_t launches_per_iter = 0;         // kernels per iteration of the last run
   int32_t last_segments = 1;             // bin plan of the last run
+  int64_t last_l2_window = 0;            // bytes the last run marked persisting in L2
+  int l2_reset_pending = 0;              // persisting lines to release once that run is done
   int64_t last_bin_hi[GAP_PR_BINS] = {};
   int32_t last_bin_lanes[GAP_PR_BINS] = {};
   int32_t last_bin_seg[GAP_PR_BINS] = {};

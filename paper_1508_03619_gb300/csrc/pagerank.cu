@@ -1246,6 +1246,40 @@ struct LaunchRec {
   int64_t poff2;  // slice of a hub fix-up
 };
 
+// L2 persistence window (options.l2_window): the two contribution buffers
+// (one allocation) are marked persisting when they fit in the device's
+// persisting carve-out, so the gathers of every iteration find them in L2
+// while the column-index stream passes through.  Returns the window bytes, 0
+// when it does not apply.  Only caching changes, never a result.
+static size_t l2_window_setup(void* base, size_t bytes, cudaAccessPolicyWindow* w) {
+  const DeviceInfo& di = device_info();
+  if (di.max_persist_l2 == 0 || di.max_window <= 0 || bytes > (size_t)di.max_window || bytes > di.max_persist_l2)
+    return 0;
+  size_t limit = 0;
+  if (cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (limit < bytes && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  memset(w, 0, sizeof(*w));
+  w->base_ptr = base;
+  w->num_bytes = bytes;
+  w->hitRatio = 1.0f;
+  w->hitProp = cudaAccessPropertyPersisting;
+  w->missProp = cudaAccessPropertyStreaming;
+  return bytes;
+}
+
+static cudaError_t set_stream_window(cudaStream_t st, const cudaAccessPolicyWindow& w) {
+  cudaStreamAttrValue v;
+  memset(&v, 0, sizeof(v));
+  v.accessPolicyWindow = w;
+  return cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
+}
+
 template <class Acc>
 static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iters, const gap_pr_options& o,
                             Acc* user_scores, cudaStream_t s) {
@@ -1557,19 +1591,39 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     return GAP_OK;
   };
 
+  cudaAccessPolicyWindow win;
+  const size_t win_bytes = (o.l2_window && S == 1) ? l2_window_setup(cbuf.p, 2 * (bf16 ? xbytes / 2 : xbytes), &win)
+                                                   : 0;
   if (max_iters > 0) {
     if (o.loop == GAP_LOOP_HOST || o.timing) {
       int32_t* done_h = g->flag_host;
-      for (int32_t k = 0; k < max_iters; ++k) {
-        GAP_TRY(launch_body(s, 0, 0));
-        GAP_CUDA(cudaMemcpyAsync(done_h, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        GAP_CUDA(cudaStreamSynchronize(s));
+      cudaStreamAttrValue prev;
+      memset(&prev, 0, sizeof(prev));
+      if (win_bytes) {  // on the caller's stream for the loop, then restored
+        GAP_CUDA(cudaStreamGetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &prev));
+        GAP_CUDA(set_stream_window(s, win));
+      }
+      gap_status ls = GAP_OK;
+      for (int32_t k = 0; k < max_iters && ls == GAP_OK; ++k) {
+        ls = launch_body(s, 0, 0);
+        if (ls != GAP_OK) break;
+        if (cudaMemcpyAsync(done_h, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          ls = cuda_fail(cudaGetLastError(), "host loop", __FILE__, __LINE__);
+          break;
+        }
         tm.collect();
         if (*done_h) break;
       }
+      if (win_bytes) cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &prev);
+      if (ls != GAP_OK) return ls;
     } else {
       cudaStream_t cs = nullptr;
       GAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      if (win_bytes && set_stream_window(cs, win) != cudaSuccess) {  // captured into the kernel nodes
+        cudaStreamDestroy(cs);
+        return cuda_fail(cudaGetLastError(), "access policy window", __FILE__, __LINE__);
+      }
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
       gap_status st = GAP_OK;
@@ -1635,6 +1689,8 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   g->launches_fixed = 1 /*ctrl*/ + 6 /*binning*/ + 1 /*init*/ + 2 /*mass*/ + (S > 1 && seg_rows > 0 ? 1 : 0) +
                       (S > 1 && seg_rows > 0 && nhubs > 0 ? 1 : 0) + (small_packed ? 6 : 0);
   g->last_segments = S;
+  g->last_l2_window = (int64_t)win_bytes;
+  g->l2_reset_pending = win_bytes ? 1 : 0;
   for (int q = 0; q < NBINS; ++q) {
     g->last_bin_hi[q] = t.bin[q].hi;
     g->last_bin_lanes[q] = t.bin[q].lanes;
@@ -1726,6 +1782,12 @@ gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out) {
   *out = *g->stats_host;
   out->kernel_launches = g->launches_fixed + out->iterations * g->launches_per_iter;
   out->segments = g->last_segments;
+  out->l2_window_bytes = g->last_l2_window;
+  if (g->l2_reset_pending) {  // the run is over: its persisting lines become normal again
+    cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
+    g->l2_reset_pending = 0;
+  }
   for (int q = 0; q < GAP_PR_BINS; ++q) {
     out->bin_max_degree[q] = g->last_bin_hi[q];
     out->bin_lanes[q] = g->last_bin_lanes[q];

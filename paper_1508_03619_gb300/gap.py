@@ -82,7 +82,8 @@ class gap_pr_stats_t(ctypes.Structure):
                 ("bin_segmented", ctypes.c_int32 * GAP_PR_BINS), ("segments", ctypes.c_int32),
                 ("phase_ms", ctypes.c_double * GAP_PR_PHASES),
                 ("phase_launches", ctypes.c_int32 * GAP_PR_PHASES),
-                ("kernel_launches", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("l2_window_bytes", ctypes.c_int64)]
 
     def to_dict(self):
         k = min(self.iterations, GAP_PR_HIST)
@@ -95,7 +96,8 @@ class gap_pr_stats_t(ctypes.Structure):
                 "segments": self.segments,
                 "phase_ms": dict(zip(PHASE_NAMES, self.phase_ms)),
                 "phase_launches": dict(zip(PHASE_NAMES, self.phase_launches)),
-                "kernel_launches": self.kernel_launches}
+                "kernel_launches": self.kernel_launches,
+                "l2_window_bytes": self.l2_window_bytes}
 
 
 class gap_ppr_query_info_t(ctypes.Structure):

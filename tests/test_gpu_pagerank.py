@@ -217,3 +217,22 @@ def test_kron22_full_config(cuda_device):
     assert oracle.verify(off, idx, xt) < 1e-4
     print(f"kron22: m={g.m} fp32 L1 {l1:.3e} rel {rel:.3e} iters {stt['iterations']} (oracle {kt})")
     g.close()
+
+
+def test_l2_window_changes_no_result(cuda_device):
+    """options.l2_window marks the contribution arrays persisting in L2 when
+    they fit; the scores and deltas are bit-identical to a run without it."""
+    n = 1 << 18
+    src, dst = gapgen.kron(18, 16, 0x81)
+    g = gpu_graph(n, src, dst, True)
+    try:
+        x0, st0, _ = run_gpu(g, 0.0, 15)
+        x1, st1, _ = run_gpu(g, 0.0, 15, l2_window=1)
+        assert np.array_equal(x0, x1)
+        assert st0["deltas"] == st1["deltas"]
+        assert st0["l2_window_bytes"] == 0
+        assert st1["l2_window_bytes"] in (0, 2 * 4 * n)  # 0 when the device has no persisting carve-out
+        x2, st2, _ = run_gpu(g, 0.0, 15, l2_window=1, loop=gap.GAP_LOOP_HOST)
+        assert np.array_equal(x0, x2)
+    finally:
+        g.close()
