@@ -182,6 +182,36 @@ int oracle_pr_verify(int64_t n, const int64_t* off, const int32_t* idx, double d
 }
 
 /*
+ * The §2.1 equation evaluated for a few rows only, one by one, in pull form:
+ * for each listed vertex v,
+ *   out[i] = (1-d)/n + d * sum_{u in N-(v)} x[u] / |N+(u)|
+ * with the in-neighbours u = in_idx[in_off[v] .. in_off[v+1]) taken in stored
+ * order and x[u]/|N+(u)| = 0 for a vertex without out-neighbours (its mass is
+ * dropped, as in push_iteration).  For a score vector y this gives y' on the
+ * sampled rows, so sum |y'[v] - y[v]| over a uniform sample, scaled by n /
+ * nrows, estimates the §3 verifier's summed change on graphs too large for a
+ * full serial iteration.  Returns 0, or -1 on a bad argument.
+ */
+int oracle_pr_rows(int64_t n, const int64_t* in_off, const int32_t* in_idx, const int32_t* outdeg, double d,
+                   const double* x, int64_t nrows, const int64_t* rows, double* out) {
+  if (n <= 0 || nrows < 0) return -1;
+  const double base = (1.0 - d) / (double)n;
+  for (int64_t i = 0; i < nrows; ++i) {
+    const int64_t v = rows[i];
+    if (v < 0 || v >= n) return -1;
+    double s = 0.0;
+    for (int64_t j = in_off[v]; j < in_off[v + 1]; ++j) {
+      const int32_t u = in_idx[j];
+      if (u < 0 || u >= n) return -1;
+      if (outdeg[u] > 0) s += x[u] / (double)outdeg[u];
+    }
+    double prod = d * s;
+    out[i] = base + prod;
+  }
+  return 0;
+}
+
+/*
  * Personalized PageRank (not in the paper; the serving workload's variant of
  * the §2.1 equation): the teleport term (1-d)/n becomes (1-d) * t[v] with t
  * uniform over the seed set S (t[v] = 1/|S| for v in S, else 0).  Repeated

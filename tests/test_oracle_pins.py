@@ -320,3 +320,32 @@ def test_oracle_golden_fingerprint():
     with open(os.path.join(here, "urand4096_oracle.json")) as f:
         want = json.load(f)
     assert make_golden.fingerprint() == want
+
+
+def test_pr_rows_is_one_pull_iteration():
+    """The sampled-row update (used at sizes the full serial iteration cannot
+    reach) is the §2.1 equation: on every row it equals the next push
+    iterate, and it agrees with a dense evaluation y' = b + d A^T D^-1 x."""
+    rng = np.random.default_rng(11)
+    n = 300
+    src = rng.integers(0, 250, 2000).astype(np.int32)  # vertices >= 250 are dangling
+    dst = rng.integers(0, n // 2, 2000).astype(np.int32)  # vertices >= n/2 without in-arcs
+    src[:40] = dst[:40]                                    # self-loops, removed by the builder
+    off, idx = oracle.build_csr(n, src, dst)
+    in_off, in_idx = oracle.build_csc(n, src, dst)
+    outdeg = np.diff(off).astype(np.int32)
+    assert (outdeg == 0).any()
+    x5, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=5)
+    x6, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=6)
+    y = oracle.pr_rows(in_off, in_idx, outdeg, x5, np.arange(n))
+    assert np.max(np.abs(y - x6)) <= 1e-15
+    A = np.zeros((n, n))
+    for u in range(n):
+        A[u, idx[off[u]:off[u + 1]]] = 1.0
+    c = np.where(outdeg > 0, x5 / np.maximum(outdeg, 1), 0.0)
+    dense = (1 - oracle.DAMPING) / n + oracle.DAMPING * (A.T @ c)
+    assert np.max(np.abs(y - dense)) <= 1e-15
+    sub = rng.choice(n, 17, replace=False)
+    assert np.array_equal(oracle.pr_rows(in_off, in_idx, outdeg, x5, sub), y[sub])
+    # sampled estimate of the verifier's summed change is unbiased: full sample = exact
+    assert abs(np.abs(y - x5).sum() - oracle.verify(off, idx, x5)) <= 1e-15
