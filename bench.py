@@ -169,12 +169,14 @@ def roofline_entry(sp, m, n, segments, contrib_bytes=4):
     peak, peak_kind = measured_hbm_peak()
     achieved = per_launch_alg / (per_launch_ms / 1e3) / 1e9
     lanes = b["lanes"]
-    kname = {0: "k_pull_hub_chunks", 256: "k_pull_cta"}.get(
-        lanes, ("k_pull_group_seg<%d>" if b["segmented"] else "k_pull_group<%d>") % lanes)
-    if q == 0:
-        kname = "k_pull_zero"
-    elif q == 1 and lanes == 1:
-        kname = "k_pull_short"
+    if lanes == -1:  # vertex-order warp-merge of the small rows
+        kname = "k_pull_small_coo<float,8,32>" if segments > 1 else "k_pull_small<float,4>"
+    elif lanes == 0:
+        kname = "k_pull_hub_chunks"
+    elif lanes == 256:
+        kname = "k_pull_cta"
+    else:
+        kname = ("k_pull_group_seg<%d>" if b["segmented"] else "k_pull_group<%d>") % lanes
     loop_ms = sum(sp["phase_ms"][k] for k in pulls + ["hub_fixup", "finalize"])
     iter_ms = loop_ms / iters
     iter_bytes = per_arc * m + per_row * n

@@ -259,11 +259,18 @@ __device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t ci
 
 // ---- set-up: x0, contributions, chunk lists ----------------------------------
 
-__global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng) {
-  for (int i = blockIdx.x; i < ng; i += gridDim.x) {
-    const BatchGraph G = gs[i];
-    const float x0 = (float)(1.0 / (double)G.n);
-    for (int64_t v = threadIdx.x; v < G.n; v += blockDim.x) {
+// One warp per 32-vertex tile of any graph (tiles laid out graph after graph,
+// tile_prefix[i] = first tile of graph i): x0 = 1/n_i, c0 = x0 / outdeg.
+__global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ tile_prefix) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ntiles = tile_prefix[ng];
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int i = find_graph(tile_prefix, ng, t);
+    const BatchGraph& G = gs[i];
+    const int64_t v = (t - tile_prefix[i]) * 32 + lane;
+    if (v < G.n) {
+      const float x0 = (float)(1.0 / (double)G.n);
       G.x[v] = x0;
       const int od = G.outdeg[v];
       G.c0[v] = od > 0 ? x0 / (float)od : 0.f;
@@ -277,7 +284,7 @@ __global__ void k_batch_plan(int ng, const int64_t* __restrict__ tile_prefix, co
                              int64_t* task_base, BatchGraphState* st, BatchCtrl* ctrl) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= ng; i += gridDim.x * blockDim.x) {
     task_base[i] = tile_prefix[i] + chunk_base[i];
-    if (i < ng) memset(&st[i], 0, sizeof(BatchGraphState));
+    if (i < ng) st[i].iterations = 0;  // the rest of the state was zeroed on the stream
     if (i == ng) {
       memset(ctrl, 0, sizeof(BatchCtrl));
       ctrl->ntasks = task_base[i];
@@ -356,15 +363,31 @@ __global__ void __launch_bounds__(THREADS) k_batch_persistent(
   }
 }
 
-__global__ void k_batch_mass(const BatchGraph* __restrict__ gs, int ng, BatchGraphState* st) {
-  __shared__ double sh[32];
-  for (int i = blockIdx.x; i < ng; i += gridDim.x) {
-    const BatchGraph G = gs[i];
-    double s = 0.0;
-    for (int64_t v = threadIdx.x; v < G.n; v += blockDim.x) s += (double)G.x[v];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) st[i].mass = s;
-    __syncthreads();
+// Mass of every graph in FP64: per-tile sums (one warp per 32-vertex tile),
+// then per graph the tile sums in a fixed order (one warp per graph).
+__global__ void k_batch_mass_tiles(const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ tile_prefix,
+                                   double* tile_mass) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ntiles = tile_prefix[ng];
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int i = find_graph(tile_prefix, ng, t);
+    const BatchGraph& G = gs[i];
+    const int64_t v = (t - tile_prefix[i]) * 32 + lane;
+    const double m = warp_sum(v < G.n ? (double)G.x[v] : 0.0);
+    if (lane == 0) tile_mass[t] = m;
+  }
+}
+
+__global__ void k_batch_mass(int ng, const int64_t* __restrict__ tile_prefix, const double* __restrict__ tile_mass,
+                             BatchGraphState* st) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < ng;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double m = 0.0;
+    for (int64_t t = tile_prefix[i] + lane; t < tile_prefix[i + 1]; t += 32) m += tile_mass[t];
+    m = warp_sum(m);
+    if (lane == 0) st[i].mass = m;
   }
 }
 
@@ -497,8 +520,10 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_CUDA(cudaEventRecord(ev.e[0], s));
   GAP_CUDA(cudaMemcpyAsync(dtp.p, tile_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
   GAP_CUDA(cudaMemcpyAsync(dcg.p, hcg.data(), sizeof(ChunkGraph) * count, cudaMemcpyHostToDevice, s));
-  const int setup_grid = std::min(count, nsm * 8);
-  k_batch_init<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count);
+  const int64_t all_tiles = tile_prefix[count];
+  const int tile_grid = stride_grid(all_tiles * 32, 256, 8);
+  GAP_CUDA(cudaMemsetAsync(dstate.p, 0, sizeof(BatchGraphState) * count, s));
+  k_batch_init<<<tile_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dtp.as<int64_t>());
   GAP_LAUNCH_CHECK();
   ChunkBuilder cb;
   GAP_TRY(build_chunks(&cb, dcg.as<ChunkGraph>(), hcg.data(), count, tu.heavy_min_degree, tu.chunk_arcs,
@@ -564,8 +589,16 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
     ++launches;
   }
   GAP_CUDA(cudaEventRecord(ev.e[2], s));
-  k_batch_mass<<<setup_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dstate.as<BatchGraphState>());
-  GAP_LAUNCH_CHECK();
+  {
+    Scratch tm;
+    GAP_TRY(tm.get(sizeof(double) * (all_tiles > 0 ? all_tiles : 1), s));
+    k_batch_mass_tiles<<<tile_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dtp.as<int64_t>(), tm.as<double>());
+    GAP_LAUNCH_CHECK();
+    k_batch_mass<<<stride_grid((int64_t)count * 32, 256, 8), 256, 0, s>>>(count, dtp.as<int64_t>(), tm.as<double>(),
+                                                                        dstate.as<BatchGraphState>());
+    GAP_LAUNCH_CHECK();
+  }
+  ++launches;
   GAP_CUDA(cudaEventRecord(ev.e[3], s));
   ++launches;
   std::vector<BatchGraphState> hs(count);
@@ -586,7 +619,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
       o.phase_ms[GAP_PHASE_OUTPUT] = ms_out;
       o.phase_launches[GAP_PHASE_PREP] = 5;
       o.phase_launches[GAP_PHASE_PULL0] = max_iters > 0 ? 1 : 0;
-      o.phase_launches[GAP_PHASE_OUTPUT] = 1;
+      o.phase_launches[GAP_PHASE_OUTPUT] = 2;
       o.iterations = hs[i].iterations;
       o.converged = hs[i].converged;
       o.final_delta = hs[i].final_delta;

@@ -239,76 +239,6 @@ __device__ __forceinline__ void write_partial(double dl, double* partial) {
   if (threadIdx.x == 0) partial[blockIdx.x] = dl;
 }
 
-// ---- bin 0: rows without in-edges -------------------------------------------
-// x' = (1-d)/n exactly; once two iterations have written both c buffers in the
-// current contribution format, x and c already hold their final values and the
-// launch returns at once (block partial 0).  A BF16 -> FP32 ladder switch asks
-// for two more writes.
-template <class Acc>
-__global__ void __launch_bounds__(PR_THREADS) k_pull_zero(PrArgs<Acc> a) {
-  const IterState st = iter_state(a);
-  double dl = 0.0;
-  if (st.it < a.ctrl->zero_fill_until) {
-    for (int64_t i = a.begin + blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; i < a.end;
-         i += (int64_t)gridDim.x * PR_THREADS)
-      dl += update_row(a, __ldcs(a.list + i), Acc(0), st.cout, st.wb);
-  }
-  write_partial(dl, a.partial);
-}
-
-// ---- bin 1: short rows, one thread per row, RPT rows per thread -------------
-// All loads of RPT rows are issued before the first dependent add, so each
-// thread keeps up to RPT*MAXD gathers in flight.
-template <class Acc, int RPT, int MAXD>
-__global__ void __launch_bounds__(PR_THREADS) k_pull_short(PrArgs<Acc> a) {
-  const IterState st = iter_state(a);
-  double dl = 0.0;
-  const int64_t T = (int64_t)gridDim.x * PR_THREADS;
-  for (int64_t i0 = a.begin + (blockIdx.x * (int64_t)PR_THREADS + threadIdx.x); i0 < a.end; i0 += T * RPT) {
-    int64_t v[RPT], b[RPT];
-    int n[RPT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int64_t i = i0 + r * T;
-      v[r] = i < a.end ? __ldcs(a.list + i) : -1;
-    }
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      b[r] = v[r] >= 0 ? a.off[v[r]] : 0;
-      n[r] = v[r] >= 0 ? (int)(a.off[v[r] + 1] - b[r]) : 0;
-    }
-    int32_t u[RPT][MAXD];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r)
-#pragma unroll
-      for (int k = 0; k < MAXD; ++k) u[r][k] = k < n[r] ? ld_idx(a.idx + b[r] + k) : -1;
-    Acc s[RPT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      Acc cv[MAXD];
-#pragma unroll
-      for (int k = 0; k < MAXD; ++k) {
-        if constexpr (std::is_same<Acc, double>::value) {
-          cv[k] = u[r][k] >= 0 ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u[r][k]) : 0.0;
-        } else {
-          cv[k] = u[r][k] >= 0 ? (st.rb ? ld_c_f(reinterpret_cast<const __nv_bfloat16*>(st.cin), u[r][k])
-                                        : ld_c_f(reinterpret_cast<const float*>(st.cin), u[r][k]))
-                               : 0.f;
-        }
-      }
-      s[r] = Acc(0);
-#pragma unroll
-      for (int k = 0; k < MAXD; ++k)
-        if (k < n[r]) s[r] = add_rn(s[r], cv[k]);
-    }
-#pragma unroll
-    for (int r = 0; r < RPT; ++r)
-      if (v[r] >= 0) dl += update_row(a, v[r], s[r], st.cout, st.wb);
-  }
-  write_partial(dl, a.partial);
-}
-
-
 // ---- rows with small in-degree, in vertex order ("warp merge") --------------
 // A warp takes 32 consecutive vertices.  Rows with in-degree <= small_max are
 // owned here (larger rows are skipped; their bins handle them).  The owned
@@ -1135,7 +1065,6 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
 constexpr int64_t DEFAULT_SEGMENT_BYTES = 32ll << 20;  // GB300: ~126 MB of L2 over two dies
 constexpr int64_t HUB_CHUNK = 32768;
 constexpr int64_t HUB_CHUNK_SEG = 4096;
-constexpr int SHORT_RPT = 4;  // rows per thread in bin 1
 constexpr int64_t SMALL_MAX = 64;  // rows up to this in-degree go to k_pull_small
 constexpr int64_t SMALL_MAX_SEG = 255;  // ... and to the packed COO passes when L2-blocked
 constexpr int SMALL_UB = 4;        // 32-arc batches in flight per warp
@@ -1237,7 +1166,7 @@ struct PhaseTimer {
   }
 };
 
-enum LaunchKind { L_ZERO, L_SHORT, L_SMALL, L_SMALL_SEG, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
+enum LaunchKind { L_SMALL, L_SMALL_SEG, L_GROUP, L_CTA, L_HUB, L_GROUP_SEG, L_HUB_SEG };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -1435,12 +1364,6 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     } else if (r.lanes == LANES_SMALL) {
       r.kind = L_SMALL;
       r.grid = stride_grid(n, PR_THREADS, 8);
-    } else if (q == BIN_ZERO && !o.deterministic) {
-      r.kind = L_ZERO;
-      r.grid = stride_grid(rows, PR_THREADS, 8);
-    } else if (q == BIN_1 && !o.deterministic) {
-      r.kind = L_SHORT;
-      r.grid = stride_grid(rows, PR_THREADS * SHORT_RPT, 8);
     } else if (r.lanes == LANES_CTA) {
       r.kind = L_CTA;
       r.grid = stride_grid(rows, 1, 8);
@@ -1535,7 +1458,6 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       const int phase = GAP_PHASE_PULL0 + r.bin;
       int tk = tm.begin();
       switch (r.kind) {
-        case L_ZERO: k_pull_zero<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_SMALL: k_pull_small<Acc, SMALL_UB><<<r.grid, PR_THREADS, 0, ls>>>(b, n, t.bin[r.bin].hi); break;
         case L_SMALL_SEG:
           k_pull_small_coo<Acc, SMALL_K, std::is_same<Acc, double>::value ? SMALL_TPC / 2 : SMALL_TPC>
@@ -1543,7 +1465,6 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
                                               sm_tend.as<int64_t>(), sm_packed.as<int32_t>(),
                                               sm_prow.as<int32_t>(), sm_pp.as<Acc>());
           break;
-        case L_SHORT: k_pull_short<Acc, SHORT_RPT, 4><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_CTA: k_pull_cta<Acc><<<r.grid, PR_THREADS, 0, ls>>>(b); break;
         case L_GROUP:
           if (r.lanes == 1) k_pull_group<1, Acc><<<r.grid, PR_THREADS, 0, ls>>>(b);

@@ -8,10 +8,10 @@
 // gathers one coalesced KP-wide row C[u][*].  A per-vertex bitmask says which
 // columns have the vertex as a seed.
 //
-// Work: rows with at most PPR_HEAVY in-arcs are pulled in 256-row blocks (32
-// row slots x 8 rounds; a slot's LR lanes cover 4 columns each); heavier rows
-// are split into chunks of PPR_CHUNK arcs (chunks.cuh) pulled one chunk per
-// row slot, so no block waits on a hub row.  A row of several chunks is
+// Work: rows with at most PPR_HEAVY in-arcs are pulled one per row slot (32
+// slots per CTA, grid-stride; a slot's LR lanes cover 4 columns each); heavier
+// rows are split into chunks of PPR_CHUNK arcs (chunks.cuh) pulled one chunk
+// per slot, so no slot waits on a hub row.  A row of several chunks is
 // finished by the slot that completes its last chunk, which adds the chunk
 // sums in chunk order.
 //
@@ -20,8 +20,7 @@
 // chunk order, x' = b + d*s, c' = x'/outdeg — depends only on the graph (the
 // chunk split uses fixed PPR_HEAVY / PPR_CHUNK), never on KP, on the slot j
 // occupies, or on the other columns.  The L1 delta of column j is a sum of
-// FP64 terms (per 256-row block, or per chunked row) each rounded to a
-// multiple of 2^-60 and added as 64-bit integers, which is exact and
+// FP64 terms (one per row) each rounded to a multiple of 2^-60 and added as 64-bit integers, which is exact and
 // independent of order.  So a query's result and its iteration count are the
 // same alone and in any mix.  A column that met its tolerance (or max_iters)
 // stops updating at once, like a run of its own would.
@@ -35,8 +34,6 @@
 namespace gap {
 
 constexpr int PPR_ROWS = 32;        // row slots per CTA
-constexpr int PPR_SUB = 8;          // rounds per delta block
-constexpr int PPR_BLOCK_ROWS = PPR_ROWS * PPR_SUB;  // 256 rows per delta block
 constexpr int PPR_KMAX = 128;
 constexpr double PPR_DELTA_SCALE = 1152921504606846976.0;  // 2^60
 
@@ -65,7 +62,7 @@ __device__ __forceinline__ unsigned long long ppr_fixed(double v) {
   return (unsigned long long)__double2ull_rn(v * PPR_DELTA_SCALE);
 }
 
-// Sequential (ascending) sums of 4 columns over arcs [b, e).
+// Sequential (ascending) sums of 4 columns over arcs [b, e), by one lane.
 __device__ __forceinline__ float4 ppr_row_sum(const PprArgs& a, int64_t b, int64_t e, int col0) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   int64_t j = b;
@@ -89,6 +86,53 @@ __device__ __forceinline__ float4 ppr_row_sum(const PprArgs& a, int64_t b, int64
     s3 = __fadd_rn(s3, c.w);
   }
   return make_float4(s0, s1, s2, s3);
+}
+
+// The same sums (same order) for a slot of LR >= 8 lanes: the slot loads LR
+// column indices at a time (one coalesced request, the next group fetched while
+// the current one is gathered) and walks them in order, 4 gathers in flight.
+// `mask` holds the slot's lanes; g is this lane's index in the slot.
+template <int LR>
+__device__ __forceinline__ float4 ppr_row_sum_slot(const PprArgs& a, int64_t b, int64_t e, int col0, int g,
+                                                   unsigned mask) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int32_t nxt = b + g < e ? __ldcs(a.idx + b + g) : 0;
+  for (int64_t base = b; base < e; base += LR) {
+    const int32_t cur = nxt;
+    const int cnt = (int)(e - base < LR ? e - base : LR);
+    nxt = base + LR + g < e ? __ldcs(a.idx + base + LR + g) : 0;
+    int k = 0;
+    for (; k + 3 < cnt; k += 4) {
+      const int32_t u0 = __shfl_sync(mask, cur, k, LR), u1 = __shfl_sync(mask, cur, k + 1, LR),
+                    u2 = __shfl_sync(mask, cur, k + 2, LR), u3 = __shfl_sync(mask, cur, k + 3, LR);
+      const float4 c0 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u0 * a.KP + col0));
+      const float4 c1 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u1 * a.KP + col0));
+      const float4 c2 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u2 * a.KP + col0));
+      const float4 c3 = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u3 * a.KP + col0));
+      s0 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s0, c0.x), c1.x), c2.x), c3.x);
+      s1 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s1, c0.y), c1.y), c2.y), c3.y);
+      s2 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s2, c0.z), c1.z), c2.z), c3.z);
+      s3 = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s3, c0.w), c1.w), c2.w), c3.w);
+    }
+    for (; k < cnt; ++k) {
+      const int32_t u = __shfl_sync(mask, cur, k, LR);
+      const float4 c = __ldg(reinterpret_cast<const float4*>(a.cin + (int64_t)u * a.KP + col0));
+      s0 = __fadd_rn(s0, c.x);
+      s1 = __fadd_rn(s1, c.y);
+      s2 = __fadd_rn(s2, c.z);
+      s3 = __fadd_rn(s3, c.w);
+    }
+  }
+  return make_float4(s0, s1, s2, s3);
+}
+
+template <int LR>
+__device__ __forceinline__ float4 ppr_sum(const PprArgs& a, int64_t b, int64_t e, int col0, int g, unsigned mask) {
+  if constexpr (LR >= 8) {
+    return ppr_row_sum_slot<LR>(a, b, e, col0, g, mask);
+  } else {
+    return ppr_row_sum(a, b, e, col0);
+  }
 }
 
 // Update of row v, columns col0..col0+3, from their in-sums; adds |x' - x| of
@@ -119,73 +163,62 @@ __device__ __forceinline__ void ppr_update(const PprArgs& a, int64_t v, int col0
   __stcg(reinterpret_cast<float4*>(cr), make_float4(cn[0], cn[1], cn[2], cn[3]));
 }
 
-// One CTA = 32 row slots x LR lanes; lane g of a slot covers columns 4g..4g+3.
+// One CTA = 32 row slots x LR lanes; lane g of a slot covers columns 4g..4g+3;
+// a slot's lanes are consecutive lanes of one warp.  Light rows are taken
+// grid-stride, one per slot; then the chunks of heavy rows, one per slot.  Each
+// row's |x' - x| is rounded to fixed point and summed in registers, so slots
+// never wait for each other; one atomic per column and thread at the end.
 template <int LR>
 __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
-  constexpr int K = 4 * LR;  // == KP
-  __shared__ double sh[PPR_ROWS][K];
-  __shared__ int slot_last[PPR_ROWS];
+  const int lane = threadIdx.x & 31;
   const int g = threadIdx.x % LR;
   const int r = threadIdx.x / LR;
   const int col0 = 4 * g;
-  const int64_t nblocks = (a.n + PPR_BLOCK_ROWS - 1) / PPR_BLOCK_ROWS;
-  int act[4];
-  float bq[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    act[q] = a.active[col0 + q];
-    bq[q] = a.base[col0 + q];
+  const unsigned mask = LR == 32 ? 0xffffffffu : (((1u << LR) - 1u) << (lane - g));
+  __shared__ int act_s[4 * LR];  // per column: updates this iteration
+  __shared__ float bq_s[4 * LR];  // per column: (1-d)/|S_j|
+  if (threadIdx.x < 4 * LR) {
+    act_s[threadIdx.x] = a.active[threadIdx.x];
+    bq_s[threadIdx.x] = a.base[threadIdx.x];
   }
-  unsigned long long qblk = 0;                  // column threadIdx.x (< K): light-block terms
-  unsigned long long qrow[4] = {0, 0, 0, 0};    // columns col0..+3: chunked-row terms
-  // ---- light rows, 256-row blocks ----
-  for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
-    double dacc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int sub = 0; sub < PPR_SUB; ++sub) {
-      const int64_t v = blk * PPR_BLOCK_ROWS + sub * PPR_ROWS + r;
-      if (v >= a.n) break;
-      const int64_t b = a.off[v], e = a.off[v + 1];
-      if (e - b > PPR_HEAVY) continue;  // a chunked row
-      ppr_update(a, v, col0, ppr_row_sum(a, b, e, col0), act, bq, dacc);
-    }
-    // per-column sum over the 32 row slots, in slot order
+  __syncthreads();
+  const int* act = act_s + col0;
+  const float* bq = bq_s + col0;
+  unsigned long long qacc[4] = {0, 0, 0, 0};  // columns col0..col0+3
+  // ---- light rows ----
+  const int64_t slots = (int64_t)gridDim.x * PPR_ROWS;
+  for (int64_t v = (int64_t)blockIdx.x * PPR_ROWS + r; v < a.n; v += slots) {
+    const int64_t b = a.off[v], e = a.off[v + 1];
+    if (e - b > PPR_HEAVY) continue;  // a chunked row
+    double dl[4] = {0.0, 0.0, 0.0, 0.0};
+    ppr_update(a, v, col0, ppr_sum<LR>(a, b, e, col0, g, mask), act, bq, dl);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sh[r][col0 + q] = dacc[q];
-    __syncthreads();
-    if (threadIdx.x < K) {
-      double t = 0.0;
-      for (int rr = 0; rr < PPR_ROWS; ++rr) t += sh[rr][threadIdx.x];
-      qblk += ppr_fixed(t);
-    }
-    __syncthreads();
+    for (int q = 0; q < 4; ++q) qacc[q] += ppr_fixed(dl[q]);
   }
-  // ---- chunks of heavy rows, one per row slot ----
-  for (int64_t c0 = (int64_t)blockIdx.x * PPR_ROWS; c0 < a.nchunks; c0 += (int64_t)gridDim.x * PPR_ROWS) {
+  // ---- chunks of heavy rows, one per slot ----
+  for (int64_t c0 = (int64_t)blockIdx.x * PPR_ROWS; c0 < a.nchunks; c0 += slots) {
     const int64_t cid = c0 + r;
     ChunkDesc cd;
     cd.nch = 0;
     float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (cid < a.nchunks) {
       cd = a.chunks[cid];
-      s4 = ppr_row_sum(a, cd.a0, cd.a0 + cd.len, col0);
+      s4 = ppr_sum<LR>(a, cd.a0, cd.a0 + cd.len, col0, g, mask);
     }
+    int last = 0;
     if (cd.nch == 1) {
       double dl[4] = {0.0, 0.0, 0.0, 0.0};
       ppr_update(a, cd.v, col0, s4, act, bq, dl);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) qrow[q] += ppr_fixed(dl[q]);
+      for (int q = 0; q < 4; ++q) qacc[q] += ppr_fixed(dl[q]);
     } else if (cd.nch > 1) {
       __stcg(reinterpret_cast<float4*>(a.cpart + cid * a.KP + col0), s4);
       __threadfence();
     }
-    __syncthreads();  // every lane's partial is fenced before its slot counts the chunk
-    if (g == 0) {
-      int last = 0;
-      if (cd.nch > 1) last = atomicAdd(a.cctr + cd.first, 1u) + 1u == (unsigned)cd.nch;
-      slot_last[r] = last;
-    }
-    __syncthreads();
-    if (slot_last[r]) {
+    __syncwarp();  // every lane's partial is fenced before its slot counts the chunk
+    if (g == 0 && cd.nch > 1) last = atomicAdd(a.cctr + cd.first, 1u) + 1u == (unsigned)cd.nch;
+    last = __shfl_sync(0xffffffffu, last, lane - g);
+    if (last) {
       __threadfence();
       float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
       for (int k = 0; k < cd.nch; ++k) {  // chunk sums in chunk order
@@ -198,14 +231,13 @@ __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
       double dl[4] = {0.0, 0.0, 0.0, 0.0};
       ppr_update(a, cd.v, col0, make_float4(t0, t1, t2, t3), act, bq, dl);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) qrow[q] += ppr_fixed(dl[q]);
+      for (int q = 0; q < 4; ++q) qacc[q] += ppr_fixed(dl[q]);
       if (g == 0) a.cctr[cd.first] = 0u;  // ready for the next iteration
     }
   }
-  if (threadIdx.x < K && qblk) atomicAdd(a.acc + threadIdx.x, qblk);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    if (qrow[q]) atomicAdd(a.acc + col0 + q, qrow[q]);
+    if (qacc[q]) atomicAdd(a.acc + col0 + q, qacc[q]);
 }
 
 // Per column: delta, history, stop test; active flags for the next iteration;
@@ -293,7 +325,7 @@ gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStr
   e->KP = kp;
   e->mask_words = (kp + 31) / 32;
   e->d = d;
-  e->nblocks = (g->n + PPR_BLOCK_ROWS - 1) / PPR_BLOCK_ROWS;
+  e->nblocks = (g->n + PPR_ROWS - 1) / PPR_ROWS;
   const size_t cells = (size_t)g->n * kp;
   GAP_TRY(e->xbuf.get(sizeof(float) * cells, s));
   GAP_TRY(e->cbuf.get(2 * sizeof(float) * cells, s));
