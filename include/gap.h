@@ -145,6 +145,13 @@ GAP_API gap_status gap_pr_run_f64(gap_graph_t* g, double damping, double tol, in
 #define GAP_LOOP_GRAPH 0u   /* convergence loop on the device: CUDA-graph while node */
 #define GAP_LOOP_HOST 1u    /* host loop: one synchronization per iteration */
 #define GAP_NO_LADDER INT32_MIN
+#define GAP_ALGO_PULL 0u   /* pull over the CSC (§3): degree-binned gather-SpMV (default) */
+#define GAP_ALGO_BINNED 1u /* propagation blocking: each iteration scatters (value,
+                              target) pairs from the out-direction CSR into target
+                              bins of 32768 vertices, then sums every bin in shared
+                              memory and applies the §2.1 update; FP32 only, at most
+                              2^27 vertices; the order of additions within a bin varies
+                              from run to run (results agree within FP32 rounding) */
 
 typedef struct {
   uint32_t precision;     /* GAP_PREC_F32 | GAP_PREC_F64 */
@@ -169,6 +176,11 @@ typedef struct {
   int64_t small_max_degree; /* rows with at most this many in-edges are pulled in vertex
                                order by the warp-merge kernel (0 = default 64; at most
                                512, and 255 when L2 blocking is active) */
+  uint32_t algorithm;     /* GAP_ALGO_PULL | GAP_ALGO_BINNED; BINNED with FP64, BF16
+                             contributions, deterministic or > 2^27 vertices returns
+                             GAP_ERR_UNSUPPORTED.  With BINNED, phase_ms[PULL0] is the
+                             scatter and phase_ms[PULL1] the binned sums */
+  uint32_t pad_;
 } gap_pr_options;
 
 /* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on

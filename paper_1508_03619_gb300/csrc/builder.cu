@@ -425,6 +425,7 @@ static gap_status build_from_device_edges(int64_t n, int64_t m, const int32_t* d
   gap_graph* g = new gap_graph();
   g->n = n;
   g->key_bits = b;
+  g->symmetric = symmetrize;
   cudaGetDevice(&g->device);
   gap_status st = GAP_OK;
   do {
@@ -591,6 +592,30 @@ gap_status gap_graph_info(const gap_graph_t* g, int64_t* n, int64_t* m, int64_t*
   return GAP_OK;
 }
 
+// Out-direction CSR: sort the reversed stored arcs (tail << b | head).
+static gap_status build_out_csr(gap_graph* g, cudaStream_t s) {
+  Scratch keys, alt;
+  GAP_TRY(keys.get(sizeof(uint64_t) * (g->m > 0 ? g->m : 1), s));
+  GAP_TRY(alt.get(sizeof(uint64_t) * (g->m > 0 ? g->m : 1), s));
+  k_csr_reverse_keys<<<stride_grid(g->n, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(g->in_off, g->in_idx, g->n,
+                                                                              g->key_bits, keys.as<uint64_t>());
+  GAP_LAUNCH_CHECK();
+  uint64_t* sorted = nullptr;
+  GAP_TRY(radix_sort_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), g->m, 2 * g->key_bits, s, &sorted));
+  int64_t* off = nullptr;
+  GAP_CUDA(cudaMalloc(&off, sizeof(int64_t) * (g->n + 1)));
+  int32_t* oidx = nullptr;
+  int64_t mo = 0;
+  gap_status st = keys_to_csr(sorted, g->m, 0, g->n, g->key_bits, off, &oidx, &mo, nullptr, s);
+  if (st != GAP_OK) {
+    cudaFree(off);
+    return st;
+  }
+  g->out_off = off;
+  g->out_idx = oidx;
+  return GAP_OK;
+}
+
 gap_status gap_graph_export_csr(gap_graph_t* g, int dir, int64_t* offsets, int32_t* idx, void* stream) {
   clear_error();
   if (!g || !offsets || (g->m > 0 && !idx) || (dir != 0 && dir != 1)) {
@@ -598,28 +623,7 @@ gap_status gap_graph_export_csr(gap_graph_t* g, int dir, int64_t* offsets, int32
     return GAP_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (dir == 0 && !g->out_off) {
-    // out-direction: sort the reversed stored arcs (tail << b | head)
-    Scratch keys, alt;
-    GAP_TRY(keys.get(sizeof(uint64_t) * (g->m > 0 ? g->m : 1), s));
-    GAP_TRY(alt.get(sizeof(uint64_t) * (g->m > 0 ? g->m : 1), s));
-    k_csr_reverse_keys<<<stride_grid(g->n, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(
-        g->in_off, g->in_idx, g->n, g->key_bits, keys.as<uint64_t>());
-    GAP_LAUNCH_CHECK();
-    uint64_t* sorted = nullptr;
-    GAP_TRY(radix_sort_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), g->m, 2 * g->key_bits, s, &sorted));
-    int64_t* off = nullptr;
-    GAP_CUDA(cudaMalloc(&off, sizeof(int64_t) * (g->n + 1)));
-    int32_t* oidx = nullptr;
-    int64_t mo = 0;
-    gap_status st = keys_to_csr(sorted, g->m, 0, g->n, g->key_bits, off, &oidx, &mo, nullptr, s);
-    if (st != GAP_OK) {
-      cudaFree(off);
-      return st;
-    }
-    g->out_off = off;
-    g->out_idx = oidx;
-  }
+  if (dir == 0 && !g->out_off) GAP_TRY(build_out_csr(g, s));
   const int64_t* so = dir == 0 ? g->out_off : g->in_off;
   const int32_t* si = dir == 0 ? g->out_idx : g->in_idx;
   GAP_CUDA(cudaMemcpyAsync(offsets, so, sizeof(int64_t) * (g->n + 1), cudaMemcpyDefault, s));
@@ -648,3 +652,19 @@ void gap_graph_destroy(gap_graph_t* g) {
 }
 
 }  // extern "C"
+
+namespace gap {
+
+gap_status graph_out_csr(gap_graph* g, cudaStream_t s, const int64_t** off, const int32_t** idx) {
+  if (g->symmetric) {
+    *off = g->in_off;
+    *idx = g->in_idx;
+    return GAP_OK;
+  }
+  if (!g->out_off) GAP_TRY(build_out_csr(g, s));
+  *off = g->out_off;
+  *idx = g->out_idx;
+  return GAP_OK;
+}
+
+}  // namespace gap

@@ -18,6 +18,7 @@ struct gap_graph {
   int64_t n_dangling = 0;
   int64_t max_in_degree = 0;
   int key_bits = 1;  // bits per vertex id in sort keys
+  int symmetric = 0;  // built with GAP_SYMMETRIZE: the out-direction CSR equals the in-direction one
   int64_t* in_off = nullptr;
   int32_t* in_idx = nullptr;
   int32_t* outdeg = nullptr;
@@ -47,5 +48,10 @@ namespace gap {
 // *result (== keys or alt).
 gap_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t count, int bits, cudaStream_t s,
                           uint64_t** result);
+
+// The out-direction CSR of g (rows sorted by target): the in-direction arrays
+// for a symmetrized graph, else built once on the device (kept by the handle,
+// like the in-direction CSR).
+gap_status graph_out_csr(gap_graph* g, cudaStream_t s, const int64_t** off, const int32_t** idx);
 
 }  // namespace gap

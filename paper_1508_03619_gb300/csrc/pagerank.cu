@@ -1623,6 +1623,395 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   return GAP_OK;
 }
 
+// ============================================================================
+// Propagation-blocked iteration (options.algorithm = GAP_ALGO_BINNED, FP32).
+//
+// The pull kernels above gather one random contribution per arc; on this GPU
+// each such gather is one L1 -> L2 request, and that request rate bounds them.
+// Here every iteration instead streams the out-direction CSR once:
+//   scatter  each CTA takes a chunk of arcs (sources in order), counts its arcs
+//            per target bin of PB_BIN vertices in shared memory, reserves one
+//            run per bin in the bin's region of the pair arrays (one atomic per
+//            bin and chunk), stages (value, target) pairs by bin and writes the
+//            runs out coalesced;
+//   sum      one CTA per bin streams the bin's pairs into PB_BIN shared-memory
+//            accumulators and applies the §2.1 update to the bin's rows (fused
+//            delta, next contribution), one fixed-order FP64 delta partial per
+//            bin.
+// Bin b's region holds exactly the in-arcs of its vertices, so it starts at
+// in_off[b * PB_BIN].  The additions within a bin happen in an order that
+// varies between runs (shared-memory atomics), so results agree with the pull
+// path within FP32 rounding only.
+constexpr int PB_BIN_LOG = 15;
+constexpr int PB_BIN = 1 << PB_BIN_LOG;  // targets per bin: 128 KB of FP32 sums
+constexpr int PB_THREADS = 1024;
+constexpr int PB_WARPS = PB_THREADS / 32;
+constexpr int PB_MAX_BINS = 4096;        // n <= 2^27
+constexpr int PB_SMEM = 227 * 1024;
+
+struct PbArgs {
+  const int64_t* __restrict__ ooff;  // out-direction CSR
+  const int32_t* __restrict__ oidx;
+  int64_t n, m;
+  int nbins;
+  int chunk;  // arcs per scatter chunk
+  const float* c0;  // contributions: read c0 in even iterations, c1 in odd ones
+  const float* c1;
+  const PrCtrl* ctrl;
+  unsigned long long* cursor;  // [nbins] next free pair slot of each bin
+  float* pval;                 // [m] pair values
+  uint16_t* ploc;              // [m] pair targets within their bin
+};
+
+__host__ __device__ inline size_t pb_scatter_smem(int chunk, int nbins) {
+  const int nb = (nbins + 1) & ~1;  // keeps the 8-byte table aligned
+  return (size_t)chunk * 8 + (size_t)nb * 8 + (size_t)nbins * 8;
+}
+
+// Largest r with off[r] <= j (j < off[n]).
+__device__ __forceinline__ int64_t pb_row_of(const int64_t* __restrict__ off, int64_t n, int64_t j) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= j) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(PB_THREADS) k_pb_scatter(PbArgs a) {
+  extern __shared__ __align__(16) unsigned char pb_smem[];
+  float* sval = reinterpret_cast<float*>(pb_smem);                 // [chunk]
+  uint32_t* sdst = reinterpret_cast<uint32_t*>(sval + a.chunk);    // [chunk]
+  const int nbe = (a.nbins + 1) & ~1;
+  unsigned int* cur = reinterpret_cast<unsigned int*>(sdst + a.chunk);  // [nbins] counts, then stage cursors
+  unsigned int* soff = cur + nbe;                                       // [nbins] stage offsets
+  unsigned long long* gbase = reinterpret_cast<unsigned long long*>(soff + nbe);  // [nbins] global run starts
+  __shared__ unsigned int warp_tot[PB_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nchunks = (a.m + a.chunk - 1) / a.chunk;
+  const int per = (a.nbins + PB_THREADS - 1) / PB_THREADS;  // bins per thread in the scan
+  const float* cin = (a.ctrl->iter & 1) ? a.c1 : a.c0;
+  for (int64_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
+    const int64_t A0 = k * (int64_t)a.chunk;
+    const int len = (int)((a.m - A0) < a.chunk ? (a.m - A0) : a.chunk);
+    for (int b = threadIdx.x; b < a.nbins; b += PB_THREADS) cur[b] = 0u;
+    __syncthreads();
+    // 1. arcs of the chunk per bin
+    for (int i = threadIdx.x; i < len; i += PB_THREADS)
+      atomicAdd(&cur[(uint32_t)__ldg(a.oidx + A0 + i) >> PB_BIN_LOG], 1u);
+    __syncthreads();
+    // 2. stage offsets (exclusive scan over bins, `per` consecutive bins per
+    //    thread) and one reserved run per non-empty bin
+    unsigned int local = 0;
+    for (int q = 0; q < per; ++q) {
+      const int b = threadIdx.x * per + q;
+      if (b < a.nbins) local += cur[b];
+    }
+    unsigned int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    unsigned int before = incl - local;
+    for (int w = 0; w < wid; ++w) before += warp_tot[w];
+    for (int q = 0; q < per; ++q) {
+      const int b = threadIdx.x * per + q;
+      if (b < a.nbins) {
+        const unsigned int c = cur[b];
+        soff[b] = before;
+        gbase[b] = c ? atomicAdd(a.cursor + b, (unsigned long long)c) : 0ull;
+        cur[b] = before;
+        before += c;
+      }
+    }
+    __syncthreads();
+    // 3. stage (value, target) pairs by bin; warp w walks its share of the
+    //    chunk's arcs source row by source row
+    const int64_t s0 = A0 + (int64_t)len * wid / PB_WARPS, s1 = A0 + (int64_t)len * (wid + 1) / PB_WARPS;
+    if (s0 < s1) {
+      int64_t r = pb_row_of(a.ooff, a.n, s0);
+      int64_t pos = s0;
+      while (pos < s1) {
+        const int64_t re = a.ooff[r + 1];
+        if (re <= pos) {  // rows without arcs
+          ++r;
+          continue;
+        }
+        const int64_t e = re < s1 ? re : s1;
+        const float c = cin[r];
+        for (int64_t j = pos + lane; j < e; j += 32) {
+          const uint32_t v = (uint32_t)__ldg(a.oidx + j);
+          const unsigned int slot = atomicAdd(&cur[v >> PB_BIN_LOG], 1u);
+          sval[slot] = c;
+          sdst[slot] = v;
+        }
+        pos = e;
+        ++r;
+      }
+    }
+    __syncthreads();
+    // 4. staged runs out: consecutive slots of a bin go to consecutive pair slots
+    for (int i = threadIdx.x; i < len; i += PB_THREADS) {
+      const uint32_t v = sdst[i];
+      const int b = (int)(v >> PB_BIN_LOG);
+      const unsigned long long dst = gbase[b] + (unsigned long long)(i - (int)soff[b]);
+      __stcs(a.pval + dst, sval[i]);
+      __stcs(a.ploc + dst, (uint16_t)(v & (PB_BIN - 1)));
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(PB_THREADS) k_pb_sum(PrArgs<float> pa, const float* __restrict__ pval,
+                                                       const uint16_t* __restrict__ ploc,
+                                                       const int64_t* __restrict__ in_off, int64_t n, int nbins,
+                                                       unsigned long long* cursor, double* partial) {
+  extern __shared__ __align__(16) unsigned char pb_smem[];
+  float* acc = reinterpret_cast<float*>(pb_smem);  // [PB_BIN]
+  __shared__ double sh[32];
+  void* cout = (pa.ctrl->iter & 1) ? pa.c0 : pa.c1;
+  for (int b = blockIdx.x; b < nbins; b += gridDim.x) {
+    for (int t = threadIdx.x; t < PB_BIN; t += PB_THREADS) acc[t] = 0.f;
+    __syncthreads();
+    const int64_t v0 = (int64_t)b << PB_BIN_LOG;
+    const int64_t v1 = v0 + PB_BIN < n ? v0 + PB_BIN : n;
+    const int64_t p0 = in_off[v0], p1 = in_off[v1];
+    int64_t p = p0 + threadIdx.x;
+    for (; p + 3 * PB_THREADS < p1; p += 4 * PB_THREADS) {
+      const float x0 = __ldcs(pval + p), x1 = __ldcs(pval + p + PB_THREADS), x2 = __ldcs(pval + p + 2 * PB_THREADS),
+                  x3 = __ldcs(pval + p + 3 * PB_THREADS);
+      const uint16_t l0 = __ldcs(ploc + p), l1 = __ldcs(ploc + p + PB_THREADS), l2 = __ldcs(ploc + p + 2 * PB_THREADS),
+                     l3 = __ldcs(ploc + p + 3 * PB_THREADS);
+      atomicAdd(acc + l0, x0);
+      atomicAdd(acc + l1, x1);
+      atomicAdd(acc + l2, x2);
+      atomicAdd(acc + l3, x3);
+    }
+    for (; p < p1; p += PB_THREADS) atomicAdd(acc + __ldcs(ploc + p), __ldcs(pval + p));
+    __syncthreads();
+    double dl = 0.0;
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += PB_THREADS) dl += update_row(pa, v, acc[v - v0], cout, false);
+    dl = block_sum(dl, sh);
+    if (threadIdx.x == 0) {
+      partial[b] = dl;
+      cursor[b] = (unsigned long long)p0;  // the next iteration fills the bin from its start again
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_pb_cursor_init(const int64_t* __restrict__ in_off, int64_t n, int nbins,
+                                 unsigned long long* cursor) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+    const int64_t v0 = (int64_t)b << PB_BIN_LOG;
+    cursor[b] = (unsigned long long)in_off[v0 < n ? v0 : n];
+  }
+}
+
+// Runs `body` (one iteration, launches on the given stream) until the device
+// stop flag is set or max_iters: a host loop with one synchronization per
+// iteration (options.loop = GAP_LOOP_HOST, or timing), else one CUDA graph whose
+// WHILE node repeats the captured body until k_finalize clears the condition.
+template <class Body>
+static gap_status drive_loop(gap_graph* g, cudaStream_t s, int32_t max_iters, PrCtrl* dctrl, PhaseTimer& tm,
+                             Body& body, bool host_loop) {
+  if (max_iters <= 0) return GAP_OK;
+  if (host_loop) {
+    int32_t* done_h = g->flag_host;
+    for (int32_t k = 0; k < max_iters; ++k) {
+      GAP_TRY(body(s, 0, 0));
+      GAP_CUDA(cudaMemcpyAsync(done_h, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      GAP_CUDA(cudaStreamSynchronize(s));
+      tm.collect();
+      if (*done_h) break;
+    }
+    return GAP_OK;
+  }
+  cudaStream_t cs = nullptr;
+  GAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  gap_status st = GAP_OK;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "cudaGraphCreate", __FILE__, __LINE__); break; }
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphConditionalHandleCreate", __FILE__, __LINE__); break; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphAddNode(while)", __FILE__, __LINE__); break; }
+    e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__); break; }
+    const gap_status bs = body(cs, h, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (bs != GAP_OK) { st = bs; break; }
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); break; }
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__); break; }
+  } while (0);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
+static gap_status run_trial_binned(gap_graph* g, double d, double tol, int32_t max_iters, const gap_pr_options& o,
+                                   float* user_scores, cudaStream_t s) {
+  const int64_t n = g->n, m = g->m;
+  const int nbins = (int)((n + PB_BIN - 1) / PB_BIN);
+  if (nbins > PB_MAX_BINS) {
+    set_error("binned algorithm: %lld vertices exceed its limit of %lld", (long long)n,
+              (long long)PB_MAX_BINS * PB_BIN);
+    return GAP_ERR_UNSUPPORTED;
+  }
+  const int64_t* ooff = nullptr;
+  const int32_t* oidx = nullptr;
+  GAP_TRY(graph_out_csr(g, s, &ooff, &oidx));  // built once per graph (graph representation, not trial state)
+  const bool user_dev = is_device_ptr(user_scores);
+  const size_t xbytes = sizeof(float) * (size_t)n;
+  // scatter chunk: as many staged pairs as fit beside the bin tables
+  const size_t tables = pb_scatter_smem(0, nbins);
+  const int chunk = (int)(((size_t)PB_SMEM - tables) / 8) & ~1023;
+  if (chunk < 4096) {
+    set_error("binned algorithm: bin tables leave no room for staging");
+    return GAP_ERR_UNSUPPORTED;
+  }
+  const size_t scatter_smem = pb_scatter_smem(chunk, nbins);
+  const size_t sum_smem = sizeof(float) * PB_BIN;
+  GAP_CUDA(cudaFuncSetAttribute(k_pb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem));
+  GAP_CUDA(cudaFuncSetAttribute(k_pb_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sum_smem));
+
+  Scratch xs, cbuf, ctrl, pv, pl, cursor, partial;
+  float* x = user_scores;
+  if (!user_dev) {
+    GAP_TRY(xs.get(xbytes, s));
+    x = xs.as<float>();
+  }
+  GAP_TRY(cbuf.get(2 * xbytes, s));
+  GAP_TRY(ctrl.get(sizeof(PrCtrl), s));
+  GAP_TRY(pv.get(sizeof(float) * (m > 0 ? m : 1), s));
+  GAP_TRY(pl.get(sizeof(uint16_t) * (m > 0 ? m : 1), s));
+  GAP_TRY(cursor.get(sizeof(unsigned long long) * nbins, s));
+  GAP_TRY(partial.get(sizeof(double) * nbins, s));
+  void* c0 = cbuf.p;
+  void* c1 = static_cast<char*>(cbuf.p) + xbytes;
+  PrCtrl* dctrl = ctrl.as<PrCtrl>();
+  k_ctrl_init<<<1, 32, 0, s>>>(dctrl, 0, 0, 0.0);
+  GAP_LAUNCH_CHECK();
+  PhaseTimer tm;
+  tm.init(o.timing != 0, s);
+  int tok = tm.begin();
+  k_pb_cursor_init<<<(nbins + 255) / 256, 256, 0, s>>>(g->in_off, n, nbins, cursor.as<unsigned long long>());
+  GAP_LAUNCH_CHECK();
+  tm.end(GAP_PHASE_PREP, tok);
+  tok = tm.begin();
+  k_init<float><<<stride_grid(n, 256, 8), 256, 0, s>>>(n, (float)(1.0 / (double)n), x, g->outdeg, c0, 0);
+  GAP_LAUNCH_CHECK();
+  tm.end(GAP_PHASE_INIT, tok);
+
+  PrArgs<float> pa{};
+  pa.off = g->in_off;
+  pa.idx = g->in_idx;
+  pa.outdeg = g->outdeg;
+  pa.x = x;
+  pa.c0 = c0;
+  pa.c1 = c1;
+  pa.base = (float)((1.0 - d) / (double)n);
+  pa.d = (float)d;
+  pa.ctrl = dctrl;
+  const int nsm = device_info().sms;
+  const int64_t nchunks = (m + chunk - 1) / chunk;
+  const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>(nchunks, nsm));
+  const int ggrid = std::min(nbins, nsm);
+  float* dpv = pv.as<float>();
+  uint16_t* dpl = pl.as<uint16_t>();
+  unsigned long long* dcur = cursor.as<unsigned long long>();
+  double* dpart = partial.as<double>();
+
+  // One iteration.  The kernels read the iteration count on the device to pick
+  // the contribution buffer they read and the one they write, so the same
+  // launches serve every iteration and the CUDA graph's loop body.
+  PbArgs a;
+  a.ooff = ooff;
+  a.oidx = oidx;
+  a.n = n;
+  a.m = m;
+  a.nbins = nbins;
+  a.chunk = chunk;
+  a.c0 = static_cast<const float*>(c0);
+  a.c1 = static_cast<const float*>(c1);
+  a.ctrl = dctrl;
+  a.cursor = dcur;
+  a.pval = dpv;
+  a.ploc = dpl;
+  auto launch_body = [&](cudaStream_t ls, cudaGraphConditionalHandle h, int use_h) -> gap_status {
+    int t1 = tm.begin();
+    if (m > 0) {
+      k_pb_scatter<<<sgrid, PB_THREADS, scatter_smem, ls>>>(a);
+      GAP_LAUNCH_CHECK();
+    }
+    tm.end(GAP_PHASE_PULL0, t1);
+    t1 = tm.begin();
+    k_pb_sum<<<ggrid, PB_THREADS, sum_smem, ls>>>(pa, dpv, dpl, g->in_off, n, nbins, dcur, dpart);
+    GAP_LAUNCH_CHECK();
+    tm.end(GAP_PHASE_PULL0 + 1, t1);
+    t1 = tm.begin();
+    k_finalize<<<1, 1024, 0, ls>>>(dctrl, dpart, nbins, tol, max_iters, h, use_h);
+    GAP_LAUNCH_CHECK();
+    tm.end(GAP_PHASE_FINALIZE, t1);
+    return GAP_OK;
+  };
+  GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing));
+
+  tok = tm.begin();
+  {
+    const int mg = stride_grid(n, 256, 4);
+    Scratch mp;
+    GAP_TRY(mp.get(sizeof(double) * mg, s));
+    k_mass_partial<float><<<mg, 256, 0, s>>>(x, n, mp.as<double>());
+    GAP_LAUNCH_CHECK();
+    k_mass_final<<<1, 1024, 0, s>>>(dctrl, mp.as<double>(), mg);
+    GAP_LAUNCH_CHECK();
+  }
+  if (!user_dev) GAP_CUDA(cudaMemcpyAsync(user_scores, x, xbytes, cudaMemcpyDefault, s));
+  tm.end(GAP_PHASE_OUTPUT, tok);
+  GAP_CUDA(cudaMemcpyAsync(g->stats_host, &dctrl->st, sizeof(gap_pr_stats_t), cudaMemcpyDeviceToHost, s));
+  if (tm.on) {
+    GAP_CUDA(cudaStreamSynchronize(s));
+    tm.collect();
+    for (int q = 0; q < GAP_PR_PHASES; ++q) {
+      g->stats_host->phase_ms[q] = tm.ms[q];
+      g->stats_host->phase_launches[q] = tm.launches[q];
+    }
+  }
+  g->launches_per_iter = m > 0 ? 3 : 2;
+  g->launches_fixed = 1 /*ctrl*/ + 1 /*cursors*/ + 1 /*init*/ + 2 /*mass*/;
+  g->last_segments = 1;
+  for (int q = 0; q < NBINS; ++q) {
+    g->last_bin_hi[q] = 0;
+    g->last_bin_lanes[q] = 0;
+    g->last_bin_seg[q] = 0;
+  }
+  g->last_l2_window = 0;
+  g->l2_reset_pending = 0;
+  g->last_stream = s;
+  g->has_run = 1;
+  g->last_tol = tol;
+  return GAP_OK;
+}
+
 static gap_status check_run_args(gap_graph* g, double d, double tol, int32_t max_iters, const void* scores) {
   clear_error();
   if (!g) { set_error("graph is NULL"); return GAP_ERR_INVALID_ARG; }
@@ -1655,6 +2044,8 @@ void gap_pr_options_default(gap_pr_options* o) {
   o->timing = 0;
   o->segment_bytes = 0;
   o->small_max_degree = 0;
+  o->algorithm = GAP_ALGO_PULL;
+  o->pad_ = 0;
 }
 
 gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters, const gap_pr_options* opt,
@@ -1674,8 +2065,16 @@ gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max
     set_error("deterministic mode is defined for F64 precision");
     return GAP_ERR_UNSUPPORTED;
   }
+  if (o.algorithm != GAP_ALGO_PULL && o.algorithm != GAP_ALGO_BINNED) { set_error("bad algorithm"); return GAP_ERR_INVALID_ARG; }
+  if (o.algorithm == GAP_ALGO_BINNED &&
+      (o.precision != GAP_PREC_F32 || o.contrib != GAP_CONTRIB_F32 || o.deterministic)) {
+    set_error("the binned algorithm runs FP32 scores with FP32 contributions only");
+    return GAP_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   if (g->has_run && g->last_stream != s) cudaStreamSynchronize(g->last_stream);  // stats buffer reuse
+  if (o.algorithm == GAP_ALGO_BINNED)
+    return run_trial_binned(g, damping, tol, max_iters, o, static_cast<float*>(scores), s);
   if (o.precision == GAP_PREC_F64)
     return run_trial<double>(g, damping, tol, max_iters, o, static_cast<double*>(scores), s);
   return run_trial<float>(g, damping, tol, max_iters, o, static_cast<float*>(scores), s);

@@ -52,6 +52,8 @@ EXPORTED = (
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
+GAP_ALGO_PULL = 0
+GAP_ALGO_BINNED = 1
 
 
 class gap_batch_tuning(ctypes.Structure):
@@ -68,7 +70,8 @@ class gap_pr_options(ctypes.Structure):
                 ("hub_threshold", ctypes.c_int64), ("deterministic", ctypes.c_uint32),
                 ("l2_window", ctypes.c_uint32), ("loop", ctypes.c_uint32),
                 ("timing", ctypes.c_uint32), ("segment_bytes", ctypes.c_int64),
-                ("small_max_degree", ctypes.c_int64)]
+                ("small_max_degree", ctypes.c_int64), ("algorithm", ctypes.c_uint32),
+                ("pad_", ctypes.c_uint32)]
 
 
 class gap_pr_stats_t(ctypes.Structure):

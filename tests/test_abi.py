@@ -38,18 +38,24 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layout_matches_c(tmp_path):
+    """Every struct the binding shares with C has the same size and field offsets."""
+    fields = [("gap_pr_options", gap.gap_pr_options), ("gap_pr_stats_t", gap.gap_pr_stats_t),
+              ("gap_batch_tuning", gap.gap_batch_tuning),
+              ("gap_ppr_query_info_t", gap.gap_ppr_query_info_t)]
+    lines, want = [], []
+    for cname, py in fields:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for f, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(py, f).offset)
     src = tmp_path / "sz.c"
-    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gap.h"\n'
-                   'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(gap_pr_options),'
-                   ' sizeof(gap_pr_stats_t), offsetof(gap_pr_options, hub_threshold),'
-                   ' offsetof(gap_pr_stats_t, delta_hist), offsetof(gap_pr_stats_t, device_error));}\n')
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gap.h"\nint main(){'
+                   + "".join(lines) + "}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", f"-I{INCLUDE}", str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                        check=True).stdout.split()))
-    want = [ctypes.sizeof(gap.gap_pr_options), ctypes.sizeof(gap.gap_pr_stats_t),
-            gap.gap_pr_options.hub_threshold.offset, gap.gap_pr_stats_t.delta_hist.offset,
-            gap.gap_pr_stats_t.device_error.offset]
     assert got == want
 
 
@@ -61,6 +67,7 @@ def test_status_strings_and_defaults():
     assert (o.precision, o.contrib, o.kahan_hubs, o.hub_threshold, o.deterministic, o.loop) == \
         (gap.GAP_PREC_F32, gap.GAP_CONTRIB_F32, 1, 10000, 0, gap.GAP_LOOP_GRAPH)
     assert o.bf16_until_log2_delta == gap.GAP_NO_LADDER
+    assert o.algorithm == gap.GAP_ALGO_PULL and o.l2_window == 0
 
 
 @pytest.mark.parametrize("n,m", [(0, 0), (-1, 0), (2 ** 31, 0)])

@@ -236,3 +236,62 @@ def test_l2_window_changes_no_result(cuda_device):
         assert np.array_equal(x0, x2)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("case", ["urand_directed", "kron_sym", "ragged_bins"])
+def test_binned_algorithm_fp32_parity(cuda_device, case):
+    """options.algorithm = GAP_ALGO_BINNED (scatter into target bins, shared-
+    memory sums) meets the FP32 bars against the oracle, with several bins and
+    a ragged last bin."""
+    if case == "urand_directed":
+        n = 70000
+        src, dst = gapgen.urand(n, 16 * n, 0x91)
+        sym = False
+    elif case == "kron_sym":
+        n = 1 << 17
+        src, dst = gapgen.kron(17, 16, 0x92)
+        sym = True
+    else:
+        n = 3 * 32768 + 17
+        src, dst = gapgen.urand(n, 4 * n, 0x93)
+        sym = True
+    off, idx = oracle_graph(n, src, dst, sym)
+    g = gpu_graph(n, src, dst, sym)
+    try:
+        x, st, status = run_gpu(g, 0.0, 20, algorithm=gap.GAP_ALGO_BINNED)
+        xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 20)
+        assert st["iterations"] == 20
+        assert_fp32_parity(x, xo)
+        x, st, status = run_gpu(g, 1e-4, 100, algorithm=gap.GAP_ALGO_BINNED)
+        _, ko, _ = oracle.pagerank(off, idx, D, 1e-4, 100)
+        assert st["converged"] and abs(st["iterations"] - ko) <= 1
+        assert oracle.verify(off, idx, x, D) < 1e-4
+        xh, sth, _ = run_gpu(g, 0.0, 20, algorithm=gap.GAP_ALGO_BINNED, loop=gap.GAP_LOOP_HOST)
+        assert_fp32_parity(xh, xo)
+    finally:
+        g.close()
+
+
+def test_binned_algorithm_edges(cuda_device):
+    import torch
+    # no arcs: every score (1-d)/n after one iteration
+    g = gpu_graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    try:
+        x, st, _ = run_gpu(g, 0.0, 3, algorithm=gap.GAP_ALGO_BINNED)
+        assert np.allclose(x, (1 - D) / 5, rtol=1e-6)
+    finally:
+        g.close()
+    src, dst = gapgen.urand(100, 400, 0x94)
+    g = gpu_graph(100, src, dst)
+    try:
+        for kw in ({"f64": True}, {"contrib": gap.GAP_CONTRIB_BF16}):
+            with pytest.raises(gap.GapError) as e:
+                run_gpu(g, 0.0, 3, algorithm=gap.GAP_ALGO_BINNED, **kw)
+            assert e.value.status == gap.GAP_ERR_UNSUPPORTED
+        o = gap.gap_pr_options_default()
+        o.algorithm = 7
+        with pytest.raises(gap.GapError) as e:
+            gap.gap_pr_run_ex(g.handle, D, 0.0, 3, o, torch.empty(100, device="cuda:0"))
+        assert e.value.status == gap.GAP_ERR_INVALID_ARG
+    finally:
+        g.close()
