@@ -53,7 +53,7 @@ NCU_TRAFFIC = {"k_pull_group_seg<32>": 0.8855e9}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=16, help="timed trials (the paper runs 16)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gap", choices=["gap", "reference"])
     ap.add_argument("--graph", default="kron", choices=["kron", "urand"],
@@ -296,9 +296,12 @@ def run_pagerank(a, ws, rank, local, dev, pg):
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
+    tev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     ev0.record(stream)
-    for _ in range(a.steps):
+    tev[0].record(stream)
+    for k in range(a.steps):
         trial(scores)
+        tev[k + 1].record(stream)
         status, st = gap.gap_pr_stats(g.handle)  # per-trial iteration count (syncs)
         iters.append(st["iterations"])
     ev1.record(stream)
@@ -307,6 +310,7 @@ def run_pagerank(a, ws, rank, local, dev, pg):
         pg.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    trial_ms = [tev[k].elapsed_time(tev[k + 1]) for k in range(a.steps)]
     launches = st["kernel_launches"] * a.steps
     if pg:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
@@ -377,6 +381,10 @@ def run_pagerank(a, ws, rank, local, dev, pg):
         "config": {**workload_config(a), "n": n, "m": m,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "iterations": iters, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+        "trials_ms": {"all": trial_ms, "min": min(trial_ms),
+                      "median": sorted(trial_ms)[len(trial_ms) // 2],
+                      "note": "each trial: allocation, binning, iterations to tol, output (paper §2.3); "
+                              "the stats read between trials is outside these events"},
         "roofline": roofline, "fp64": fp64,
     }
     if not a.no_cpu_baseline and ws == 1:
@@ -542,8 +550,21 @@ def measure_ppr(a, dev):
 
     run_arrivals([0.0] * cols)  # warm-up burst
     burst = 2 * cols
+    steps0 = srv.info()["steps"]
     lat, span, iters = run_arrivals([0.0] * burst)
+    steps = srv.info()["steps"] - steps0
     sat = burst / span
+    # roofline of the SpMM iterations of the burst: per iteration 4 B index + 4·cols B
+    # of gathered contribution row per arc, (8 + 4 + 12·cols) B per row
+    step_ms = span * 1e3 / max(steps, 1)
+    alg = (4 + 4 * cols) * g.m + (12 + 12 * cols) * g.n
+    peak, kind = measured_hbm_peak()
+    res["roofline"] = {"bound": "hbm", "achieved": alg / (step_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                       "frac": alg / (step_ms / 1e3) / 1e9 / peak, "traffic": None,
+                       "kernel": f"k_ppr_spmm<{cols // 4}> (+ finalize), one engine iteration",
+                       "alg_bytes_per_iteration": alg, "iteration_ms": step_ms, "iterations": steps,
+                       "peak_source": f"{kind} hbm_gbs",
+                       "note": "iteration time = burst span / engine iterations (admission and copies included)"}
     res["saturated_qps"] = sat
     res["saturated_iterations_mean"] = float(np.mean(iters))
     loads = []
