@@ -250,6 +250,19 @@ def run_reference(a, ws, rank):
     }))
 
 
+def combine_ranks(ms, arcs, pg, device):
+    """Whole-job figures of N replicas: the slowest rank's time and every rank's
+    arcs.  Without a process group the local figures are returned."""
+    if pg is None:
+        return ms, arcs
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    c = torch.tensor([float(arcs)], device=device, dtype=torch.float64)
+    pg.all_reduce(c, op=pg.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def run_pagerank(a, ws, rank, local, dev, pg):
     """The headline line: K PageRank trials on the kron (or urand) graph."""
     import torch
@@ -312,11 +325,7 @@ def run_pagerank(a, ws, rank, local, dev, pg):
     ms = ev0.elapsed_time(ev1)
     trial_ms = [tev[k].elapsed_time(tev[k + 1]) for k in range(a.steps)]
     launches = st["kernel_launches"] * a.steps
-    if pg:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    arcs = m * sum(iters) * ws
+    ms, arcs = combine_ranks(ms, m * sum(iters), pg, dev)
     value = arcs / (ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI with a pinned host output buffer ----
