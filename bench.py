@@ -376,6 +376,36 @@ def run_pagerank(a, ws, rank, local, dev, pg):
         fp64 = {"value": v64, "unit": UNIT, "fp32_speedup": value / ws / v64 if v64 else None,
                 "l1_fp32_vs_fp64": l1, "iterations": s64["iterations"]}
 
+    # ---- BF16-stored contributions (Kahan sums on hub rows), error vs the FP64 GPU path ----
+    bf16 = None
+    if not a.no_fp64:
+        bf16 = {}
+        xb = torch.empty(n, dtype=torch.float32, device=dev)
+        for label, ladder in (("ladder", -10), ("bf16_only", gap.GAP_NO_LADDER)):
+            ob = options()
+            ob.contrib = gap.GAP_CONTRIB_BF16
+            ob.bf16_until_log2_delta = ladder
+            gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, ob, xb)
+            gap.gap_pr_stats(g.handle)
+            kb = max(1, min(3, a.steps))
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            itb = 0
+            b0.record(stream)
+            for _ in range(kb):
+                gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, ob, xb)
+                _, sb = gap.gap_pr_stats(g.handle)
+                itb += sb["iterations"]
+            b1.record(stream)
+            torch.cuda.synchronize(dev)
+            vb = m * itb / (b0.elapsed_time(b1) / 1e3) / 1e9
+            bf16[label] = {"value": vb, "unit": UNIT, "vs_fp32": vb / (value / ws),
+                           "l1_vs_fp64": float((x64 - xb.double()).abs().sum().item()),
+                           "iterations": sb["iterations"], "bf16_iterations": sb["bf16_iters"],
+                           "final_delta": sb["final_delta"]}
+        bf16["note"] = ("contributions stored as BF16 with Kahan-compensated sums on rows above 10^4 "
+                        "in-arcs; 'ladder' switches to FP32 contributions once delta <= 2^-10")
+        del xb
+
     g.close()
     del scores, host_scores
     if not a.no_fp64:
@@ -394,7 +424,7 @@ def run_pagerank(a, ws, rank, local, dev, pg):
                       "median": sorted(trial_ms)[len(trial_ms) // 2],
                       "note": "each trial: allocation, binning, iterations to tol, output (paper §2.3); "
                               "the stats read between trials is outside these events"},
-        "roofline": roofline, "fp64": fp64,
+        "roofline": roofline, "fp64": fp64, "bf16": bf16,
     }
     if not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(a)

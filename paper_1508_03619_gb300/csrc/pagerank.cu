@@ -1209,6 +1209,80 @@ static cudaError_t set_stream_window(cudaStream_t st, const cudaAccessPolicyWind
   return cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
 }
 
+// Runs `body` (one iteration, launches on the given stream) until the device
+// stop flag is set or max_iters: a host loop with one synchronization per
+// iteration (options.loop = GAP_LOOP_HOST, or timing), else one CUDA graph whose
+// WHILE node repeats the captured body until k_finalize clears the condition.
+// `win` (may be NULL): an L2 access policy window set on the launching stream
+// for the loop (restored afterwards) or captured into the graph's kernel nodes.
+template <class Body>
+static gap_status drive_loop(gap_graph* g, cudaStream_t s, int32_t max_iters, PrCtrl* dctrl, PhaseTimer& tm,
+                             Body& body, bool host_loop, const cudaAccessPolicyWindow* win) {
+  if (max_iters <= 0) return GAP_OK;
+  if (host_loop) {
+    int32_t* done_h = g->flag_host;
+    cudaStreamAttrValue prev;
+    memset(&prev, 0, sizeof(prev));
+    if (win) {
+      GAP_CUDA(cudaStreamGetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &prev));
+      GAP_CUDA(set_stream_window(s, *win));
+    }
+    gap_status ls = GAP_OK;
+    for (int32_t k = 0; k < max_iters; ++k) {
+      ls = body(s, 0, 0);
+      if (ls != GAP_OK) break;
+      if (cudaMemcpyAsync(done_h, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        ls = cuda_fail(cudaGetLastError(), "host loop", __FILE__, __LINE__);
+        break;
+      }
+      tm.collect();
+      if (*done_h) break;
+    }
+    if (win) cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &prev);
+    return ls;
+  }
+  cudaStream_t cs = nullptr;
+  GAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  if (win && set_stream_window(cs, *win) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(cudaGetLastError(), "access policy window", __FILE__, __LINE__);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  gap_status st = GAP_OK;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "cudaGraphCreate", __FILE__, __LINE__); break; }
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphConditionalHandleCreate", __FILE__, __LINE__); break; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphAddNode(while)", __FILE__, __LINE__); break; }
+    e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__); break; }
+    const gap_status bs = body(cs, h, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (bs != GAP_OK) { st = bs; break; }
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); break; }
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__); break; }
+  } while (0);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
 template <class Acc>
 static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iters, const gap_pr_options& o,
                             Acc* user_scores, cudaStream_t s) {
@@ -1515,71 +1589,8 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   cudaAccessPolicyWindow win;
   const size_t win_bytes = (o.l2_window && S == 1) ? l2_window_setup(cbuf.p, 2 * (bf16 ? xbytes / 2 : xbytes), &win)
                                                    : 0;
-  if (max_iters > 0) {
-    if (o.loop == GAP_LOOP_HOST || o.timing) {
-      int32_t* done_h = g->flag_host;
-      cudaStreamAttrValue prev;
-      memset(&prev, 0, sizeof(prev));
-      if (win_bytes) {  // on the caller's stream for the loop, then restored
-        GAP_CUDA(cudaStreamGetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &prev));
-        GAP_CUDA(set_stream_window(s, win));
-      }
-      gap_status ls = GAP_OK;
-      for (int32_t k = 0; k < max_iters && ls == GAP_OK; ++k) {
-        ls = launch_body(s, 0, 0);
-        if (ls != GAP_OK) break;
-        if (cudaMemcpyAsync(done_h, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-          ls = cuda_fail(cudaGetLastError(), "host loop", __FILE__, __LINE__);
-          break;
-        }
-        tm.collect();
-        if (*done_h) break;
-      }
-      if (win_bytes) cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &prev);
-      if (ls != GAP_OK) return ls;
-    } else {
-      cudaStream_t cs = nullptr;
-      GAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-      if (win_bytes && set_stream_window(cs, win) != cudaSuccess) {  // captured into the kernel nodes
-        cudaStreamDestroy(cs);
-        return cuda_fail(cudaGetLastError(), "access policy window", __FILE__, __LINE__);
-      }
-      cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      gap_status st = GAP_OK;
-      do {
-        if (cudaGraphCreate(&graph, 0) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "cudaGraphCreate", __FILE__, __LINE__); break; }
-        cudaGraphConditionalHandle h;
-        cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphConditionalHandleCreate", __FILE__, __LINE__); break; }
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphAddNode(while)", __FILE__, __LINE__); break; }
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__); break; }
-        gap_status bs = launch_body(cs, h, 1);
-        cudaGraph_t captured = nullptr;
-        e = cudaStreamEndCapture(cs, &captured);
-        if (bs != GAP_OK) { st = bs; break; }
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); break; }
-        e = cudaGraphLaunch(exec, s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__); break; }
-      } while (0);
-      if (exec) cudaGraphExecDestroy(exec);
-      if (graph) cudaGraphDestroy(graph);
-      cudaStreamDestroy(cs);
-      if (st != GAP_OK) return st;
-    }
-  }
+  GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing != 0,
+                     win_bytes ? &win : nullptr));
 
   // ---- output + stats ----
   tok = tm.begin();
@@ -1811,62 +1822,6 @@ __global__ void k_pb_cursor_init(const int64_t* __restrict__ in_off, int64_t n, 
   }
 }
 
-// Runs `body` (one iteration, launches on the given stream) until the device
-// stop flag is set or max_iters: a host loop with one synchronization per
-// iteration (options.loop = GAP_LOOP_HOST, or timing), else one CUDA graph whose
-// WHILE node repeats the captured body until k_finalize clears the condition.
-template <class Body>
-static gap_status drive_loop(gap_graph* g, cudaStream_t s, int32_t max_iters, PrCtrl* dctrl, PhaseTimer& tm,
-                             Body& body, bool host_loop) {
-  if (max_iters <= 0) return GAP_OK;
-  if (host_loop) {
-    int32_t* done_h = g->flag_host;
-    for (int32_t k = 0; k < max_iters; ++k) {
-      GAP_TRY(body(s, 0, 0));
-      GAP_CUDA(cudaMemcpyAsync(done_h, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      GAP_CUDA(cudaStreamSynchronize(s));
-      tm.collect();
-      if (*done_h) break;
-    }
-    return GAP_OK;
-  }
-  cudaStream_t cs = nullptr;
-  GAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  gap_status st = GAP_OK;
-  do {
-    if (cudaGraphCreate(&graph, 0) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "cudaGraphCreate", __FILE__, __LINE__); break; }
-    cudaGraphConditionalHandle h;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphConditionalHandleCreate", __FILE__, __LINE__); break; }
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
-    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphAddNode(while)", __FILE__, __LINE__); break; }
-    e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__); break; }
-    const gap_status bs = body(cs, h, 1);
-    cudaGraph_t captured = nullptr;
-    e = cudaStreamEndCapture(cs, &captured);
-    if (bs != GAP_OK) { st = bs; break; }
-    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__); break; }
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); break; }
-    e = cudaGraphLaunch(exec, s);
-    if (e != cudaSuccess) { st = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__); break; }
-  } while (0);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  cudaStreamDestroy(cs);
-  return st;
-}
-
 static gap_status run_trial_binned(gap_graph* g, double d, double tol, int32_t max_iters, const gap_pr_options& o,
                                    float* user_scores, cudaStream_t s) {
   const int64_t n = g->n, m = g->m;
@@ -1973,7 +1928,7 @@ static gap_status run_trial_binned(gap_graph* g, double d, double tol, int32_t m
     tm.end(GAP_PHASE_FINALIZE, t1);
     return GAP_OK;
   };
-  GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing));
+  GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing != 0, nullptr));
 
   tok = tm.begin();
   {
