@@ -15,23 +15,31 @@
 // between two buffers because every row gathers from all of c.
 //
 // Degree bins (hardware tuning constants, the same for every graph, §2.3):
-//   bin 0  no in-edges: x' = (1-d)/n exactly, so only iterations 1 and 2 (which
-//          fill both c buffers) touch these rows
-//   bin 1  deg <= 4      one thread per row, four rows per thread
-//   bin 2  deg <= 16     4 lanes per row
-//   bin 3  deg <= 64     8 lanes per row
-//   bin 4  deg <= 2048   one warp per row        | segmented: deg <= 512, 8 lanes
-//   bin 5  deg <= 32768  one CTA per row         | segmented: one warp
-//   bin 6  larger        32768-arc chunks per CTA + ordered fix-up (hub rows)
+//   bin 0    in-degree <= small (64 whole-row, 255 when L2-blocked; tuned per
+//            GPU), including rows without in-edges: vertex-order warp merge
+//            (k_pull_small), or, when L2-blocked, a segment-major packed COO
+//            copy made per trial (k_small_count / k_small_pack, then
+//            k_pull_small_coo once per segment).  Rows without in-edges keep
+//            x' = (1-d)/n, so they are written only while both c buffers still
+//            need it (iterations < zero_fill_until).
+//   bins 1-3 empty with these thresholds; the FP64 deterministic mode puts every
+//            row in a one-thread-per-row group (the oracle's addition order)
+//   bin 4    in-degree <= 2048: one warp per row | L2-blocked: <= 512, 8 lanes
+//   bin 5    in-degree <= 32768: one CTA per row | L2-blocked: one warp
+//   bin 6    larger (hubs): 32768-arc chunks (4096 when L2-blocked) + an
+//            ordered fix-up that adds the chunk sums in chunk order
 //
 // L2 blocking ("segmented" bins): when the contribution array is larger than
-// the segment size, rows of bins 4-6 are pulled one source segment
-// [s*W, (s+1)*W) at a time.  CSC rows are sorted by source, so a segment is a
-// contiguous sub-range of every row (split points found once per trial by
-// binary search); one pass per segment keeps that segment's contributions hot
-// in L2 while the index stream flows through with evict-first loads.  Row
-// partial sums (FP64) are added in ascending segment order, so every sum still
-// has a fixed order and results are reproducible run to run.
+// the segment size, rows are pulled one source segment [s*W, (s+1)*W) at a
+// time.  CSC rows are sorted by source, so a segment is a contiguous sub-range
+// of every row (split points found once per trial by binary search); one pass
+// per segment keeps that segment's contributions hot in L2 while the index
+// stream flows through with evict-first loads.  Row partial sums are added in
+// ascending segment order, so every sum still has a fixed order and results
+// are reproducible run to run.
+//
+// An alternative iteration (options.algorithm = GAP_ALGO_BINNED,
+// propagation blocking) is at the end of this file.
 #include <cuda_bf16.h>
 
 #include <mutex>
@@ -1095,7 +1103,7 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
     }
   }
   const bool seg = t.segments > 1;
-  // rows with in-degree <= small (bins 1-3 stay empty): one vertex-order kernel
+  // rows with in-degree <= small: one vertex-order kernel (bins 1-3 stay empty)
   int64_t small = o.small_max_degree > 0 ? (o.small_max_degree < 512 ? o.small_max_degree : 512)
                                          : (seg ? SMALL_MAX_SEG : SMALL_MAX);
   if (seg && small > 255) small = 255;  // packed per-segment counts are bytes
