@@ -180,12 +180,19 @@ typedef struct {
                              contributions, deterministic or > 2^27 vertices returns
                              GAP_ERR_UNSUPPORTED.  With BINNED, phase_ms[PULL0] is the
                              scatter and phase_ms[PULL1] the binned sums */
-  uint32_t pad_;
+  uint32_t group_lanes;   /* lanes per row of bin 4: 8 or 32 (0 = 32 for whole rows,
+                             8 when L2 blocking is active) */
+  int64_t group_max_degree; /* upper in-degree of bin 4 (0 = 2048, or 512 when L2
+                               blocking is active); an empty bin when <= the bin-0 bound */
+  int64_t cta_max_degree;   /* upper in-degree of bin 5 (0 = 32768); larger rows are hubs
+                               pulled in chunks */
+  int64_t hub_chunk_arcs;   /* arcs per hub chunk, in [1024, 2^24] (0 = 32768, or 4096
+                               when L2 blocking is active) */
 } gap_pr_options;
 
 /* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on
  * (threshold 10000), not deterministic, no L2 window, graph loop, no timing,
- * default segment size. */
+ * default segment size, pull algorithm, built-in bin bounds (all 0). */
 GAP_API void gap_pr_options_default(gap_pr_options* o);
 
 /* gap_pr_run with options; `scores` is float* (F32) or double* (F64). */

@@ -5,11 +5,12 @@ the fixed table that ``tuning.py`` loads.
 Tuned here:
   batch path    heavy_min_degree (rows above it are split into chunk tasks),
                 chunk_arcs, block_threads (CTA shape), blocks_per_sm;
-  single graph  segment_bytes (L2 blocking of the contribution array) and
-                small_max_degree (the bin-0 threshold of the vertex-order
-                kernel).
+  single graph  segment_bytes (L2 blocking of the contribution array), the
+                degree-bin bounds (small_max_degree: bin 0, the vertex-order
+                kernel; group_max_degree: bin 4; cta_max_degree: bin 5, above
+                it hubs), the lanes per row of bin 4 and the hub chunk size.
 Tuning set: the uneven batch generator with its own seed (not the evaluation
-batch's), and Kronecker / uniform-random graphs at scale 24 with their own
+batch's), and Kronecker / uniform-random graphs at scale 25 with their own
 seeds.  Each candidate is timed with CUDA events (median of several trials,
 inputs larger than L2).  Greedy coordinate search: one parameter at a time,
 starting from the built-in values, two passes.
@@ -27,7 +28,7 @@ import time
 D = 0.85
 TOL = 1e-4
 TUNE_BATCH_SEED = 0xA7  # the evaluation batch uses gapgen.batch_specs' default seed
-TUNE_GRAPH_SEEDS = {"kron": 0xA24, "urand": 0xA25}
+TUNE_GRAPH_SEEDS = {"kron": 0xA24, "urand": 0xA25}  # the evaluation graphs use 0x26
 
 BATCH_SPACE = {
     "heavy_min_degree": [64, 128, 256, 512, 1024],
@@ -35,9 +36,13 @@ BATCH_SPACE = {
     "block_threads": [128, 256, 512],
     "blocks_per_sm": [0, 2, 4],
 }
-PAGERANK_SPACE = {
-    "segment_bytes": [8 << 20, 16 << 20, 32 << 20, 64 << 20, -1],  # -1: never segment
-    "small_max_degree": [0, 32, 64, 128, 255],  # 0: the built-in bound
+PAGERANK_SPACE = {  # 0: the library's built-in value
+    "segment_bytes": [0, 8 << 20, 16 << 20, 64 << 20, -1],  # -1: never segment
+    "small_max_degree": [0, 32, 64, 128, 255],
+    "group_max_degree": [0, 256, 1024, 2048, 4096],
+    "cta_max_degree": [0, 8192, 16384, 65536],
+    "hub_chunk_arcs": [0, 2048, 8192, 32768],
+    "group_lanes": [0, 8, 32],
 }
 
 
@@ -123,8 +128,7 @@ def tune_pagerank(gap, gapgen, torch, reps, scale, log):
             total += timed(run, reps)
         return total
 
-    o = gap.gap_pr_options_default()
-    start = {"segment_bytes": o.segment_bytes, "small_max_degree": o.small_max_degree}
+    start = {k: 0 for k in PAGERANK_SPACE}
     base = cost(start)
     best, c = coordinate_search(PAGERANK_SPACE, start, cost, log=log)
     for g in gs:
@@ -136,7 +140,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None, help="table file (default tuning/<device>.json)")
     ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--scale", type=int, default=25)
     ap.add_argument("--skip", default="", help="comma list: batch,pagerank")
     a = ap.parse_args(argv)
     import torch

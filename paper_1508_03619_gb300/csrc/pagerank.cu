@@ -1111,18 +1111,22 @@ static Tuning make_tuning(const gap_pr_options& o, int64_t n, size_t c_elem_byte
   t.bin[BIN_1] = {small, 1, 0};
   t.bin[BIN_2] = {small, 4, 0};
   t.bin[BIN_3] = {small, 8, 0};
+  const int64_t grp_hi = o.group_max_degree > 0 ? o.group_max_degree : (seg ? (small > 512 ? small : 512) : 2048);
+  const int64_t cta_hi = o.cta_max_degree > 0 ? o.cta_max_degree : 32768;
+  const int grp_lanes = o.group_lanes ? (int)o.group_lanes : (seg ? 8 : 32);
   if (seg) {
-    t.bin[BIN_4] = {small > 512 ? small : 512, 8, 1};
-    t.bin[BIN_5] = {32768, 32, 1};
+    t.bin[BIN_4] = {grp_hi, grp_lanes, 1};
+    t.bin[BIN_5] = {cta_hi, 32, 1};
   } else {
-    t.bin[BIN_4] = {2048, 32, 0};
-    t.bin[BIN_5] = {32768, LANES_CTA, 0};
+    t.bin[BIN_4] = {grp_hi, grp_lanes, 0};
+    t.bin[BIN_5] = {cta_hi, LANES_CTA, 0};
     // rows above the compensation threshold must reach the CTA / hub kernels
     if (o.kahan_hubs && o.hub_threshold > 0 && o.hub_threshold < t.bin[BIN_4].hi)
       t.bin[BIN_4].hi = o.hub_threshold > t.bin[BIN_3].hi ? o.hub_threshold : t.bin[BIN_3].hi;
   }
   t.bin[BIN_HUB] = {INT64_MAX, LANES_HUB, seg ? 1 : 0};
   if (seg) t.hub_chunk = HUB_CHUNK_SEG;  // segment sub-rows are S times shorter
+  if (o.hub_chunk_arcs > 0) t.hub_chunk = o.hub_chunk_arcs;
   return t;
 }
 
@@ -2008,7 +2012,10 @@ void gap_pr_options_default(gap_pr_options* o) {
   o->segment_bytes = 0;
   o->small_max_degree = 0;
   o->algorithm = GAP_ALGO_PULL;
-  o->pad_ = 0;
+  o->group_lanes = 0;
+  o->group_max_degree = 0;
+  o->cta_max_degree = 0;
+  o->hub_chunk_arcs = 0;
 }
 
 gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters, const gap_pr_options* opt,
@@ -2029,6 +2036,11 @@ gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max
     return GAP_ERR_UNSUPPORTED;
   }
   if (o.algorithm != GAP_ALGO_PULL && o.algorithm != GAP_ALGO_BINNED) { set_error("bad algorithm"); return GAP_ERR_INVALID_ARG; }
+  if ((o.group_lanes != 0 && o.group_lanes != 8 && o.group_lanes != 32) || o.group_max_degree < 0 ||
+      o.cta_max_degree < 0 || (o.hub_chunk_arcs != 0 && (o.hub_chunk_arcs < 1024 || o.hub_chunk_arcs > (1 << 24)))) {
+    set_error("bad bin options (group_lanes 8 or 32, degrees >= 0, hub_chunk_arcs in [1024, 2^24])");
+    return GAP_ERR_INVALID_ARG;
+  }
   if (o.algorithm == GAP_ALGO_BINNED &&
       (o.precision != GAP_PREC_F32 || o.contrib != GAP_CONTRIB_F32 || o.deterministic)) {
     set_error("the binned algorithm runs FP32 scores with FP32 contributions only");

@@ -71,7 +71,8 @@ class gap_pr_options(ctypes.Structure):
                 ("l2_window", ctypes.c_uint32), ("loop", ctypes.c_uint32),
                 ("timing", ctypes.c_uint32), ("segment_bytes", ctypes.c_int64),
                 ("small_max_degree", ctypes.c_int64), ("algorithm", ctypes.c_uint32),
-                ("pad_", ctypes.c_uint32)]
+                ("group_lanes", ctypes.c_uint32), ("group_max_degree", ctypes.c_int64),
+                ("cta_max_degree", ctypes.c_int64), ("hub_chunk_arcs", ctypes.c_int64)]
 
 
 class gap_pr_stats_t(ctypes.Structure):

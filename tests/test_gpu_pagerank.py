@@ -129,6 +129,33 @@ def test_bin_boundaries_and_hubs(cuda_device, seg):
 
 
 @pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
+def test_reshaped_bins_keep_parity(cuda_device, seg):
+    """Bin bounds, lanes and hub chunk size are tuning knobs: any setting the
+    autotuner may pick keeps the FP32 and FP64 parity bars."""
+    n, src, dst = threshold_graph()
+    off, idx = oracle_graph(n, src, dst, False)
+    xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 12)
+    g = gpu_graph(n, src, dst, False)
+    sb = seg_bytes_for(n) if seg else 0
+    try:
+        for knobs in ({"group_max_degree": 16, "cta_max_degree": 100, "hub_chunk_arcs": 1024,
+                       "group_lanes": 8},
+                      {"group_max_degree": 4096, "cta_max_degree": 65536, "hub_chunk_arcs": 8192,
+                       "group_lanes": 32},
+                      {"small_max_degree": 32, "group_max_degree": 8}):
+            x, st, _ = run_gpu(g, 0.0, 12, segment_bytes=sb, **knobs)
+            assert_fp32_parity(x, xo)
+            assert sum(b["arcs"] for b in st["bins"]) == g.m
+            x64, _, _ = run_gpu(g, 0.0, 12, f64=True, segment_bytes=sb, **knobs)
+            assert np.abs(x64 - xo).sum() <= FP64_L1
+        with pytest.raises(gap.GapError) as e:
+            run_gpu(g, 0.0, 2, group_lanes=16)
+        assert e.value.status == gap.GAP_ERR_INVALID_ARG
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
 def test_loop_modes_agree(cuda_device, seg):
     n, src, dst, sym = CASES[1][1:]
     g = gpu_graph(n, src, dst, sym)

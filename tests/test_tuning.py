@@ -47,5 +47,6 @@ def test_committed_tables_are_well_formed():
             assert b["heavy_min_degree"] >= 32 and 32 <= b["chunk_arcs"] <= 1 << 24
             assert b["block_threads"] in (128, 256, 512) and b["blocks_per_sm"] >= 0
         if "pagerank" in t:
-            assert set(t["pagerank"]) <= {"segment_bytes", "small_max_degree"}
+            assert set(t["pagerank"]) <= {"segment_bytes", "small_max_degree", "group_max_degree",
+                                          "cta_max_degree", "hub_chunk_arcs", "group_lanes"}
         assert "tuning_set" in t
