@@ -45,9 +45,11 @@ TOL = 1e-4
 MAX_ITERS = 100
 FALLBACK_HBM_GBS = 6800.0
 
-# ncu DRAM bytes (read + write) per launch, from one capture of the launch list
-# (profiles/pull_segmented_kron26.md); only kernels unchanged since then.
-NCU_TRAFFIC = {"k_pull_group_seg<32>": 0.8855e9}
+# ncu DRAM bytes (read + write) per launch on kron26 with the GB300 tuning table,
+# from one capture of the launch list (profiles/pull_segmented_kron26.md); only
+# kernels and bin bounds unchanged since then.
+NCU_TRAFFIC = {"k_pull_small_coo<float,8,32>": 1.431e9, "k_pull_group_seg<8>": 0.611e9,
+               "k_pull_hub_chunks": 0.252e9, "k_pull_group_seg<32>": 0.222e9}
 
 
 def parse():
@@ -184,7 +186,8 @@ def roofline_entry(sp, m, n, segments, contrib_bytes=4):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kname),
             "kernel": f"{kname} (bin {q}: in-degree <= {b['max_degree']}, "
-                      f"{'segmented' if b['segmented'] else 'whole rows'})",
+                      + ("packed COO, one pass per source segment)" if lanes == -1 and segments > 1 else
+                         "segmented)" if b["segmented"] else "whole rows)"),
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
             else "fallback 6.8 TB/s",
             "alg_bytes_per_launch": per_launch_alg, "launch_ms": per_launch_ms,
