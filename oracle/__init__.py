@@ -59,8 +59,9 @@ def _load():
         lib.oracle_pr_verify.argtypes = [i64, vp, vp, dbl, vp, ctypes.POINTER(dbl)]
         lib.oracle_ppr.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, i32, vp, vp]
         lib.oracle_pr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, i64, vp, vp]
+        lib.oracle_ppr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, vp, i32, i64, vp, vp]
         for f in (lib.oracle_build_csr, lib.oracle_pagerank, lib.oracle_pr_verify, lib.oracle_ppr,
-                  lib.oracle_pr_rows):
+                  lib.oracle_pr_rows, lib.oracle_ppr_rows):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -139,6 +140,24 @@ def pr_rows(in_offsets, in_idx, outdeg, x, rows, d: float = DAMPING):
                                 _ptr(rows), _ptr(out))
     if rc != 0:
         raise ValueError(f"oracle_pr_rows failed ({rc})")
+    return out
+
+
+def ppr_rows(in_offsets, in_idx, outdeg, x, seeds, rows, d: float = DAMPING):
+    """The personalized update evaluated for the listed rows only (pull over
+    the CSC): returns y'[rows] for the score vector x (FP64)."""
+    in_offsets = np.ascontiguousarray(in_offsets, dtype=np.int64)
+    in_idx = np.ascontiguousarray(in_idx, dtype=np.int32)
+    outdeg = np.ascontiguousarray(outdeg, dtype=np.int32)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    n = len(in_offsets) - 1
+    out = np.empty(len(rows), np.float64)
+    rc = _load().oracle_ppr_rows(n, _ptr(in_offsets), _ptr(in_idx), _ptr(outdeg), d, _ptr(x), _ptr(seeds),
+                                 len(seeds), len(rows), _ptr(rows), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_ppr_rows failed ({rc})")
     return out
 
 

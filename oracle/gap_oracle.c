@@ -212,6 +212,52 @@ int oracle_pr_rows(int64_t n, const int64_t* in_off, const int32_t* in_idx, cons
 }
 
 /*
+ * The personalized update (see oracle_ppr) for listed rows only, one by one:
+ *   out[i] = (1-d) * t[v] + d * sum_{u in N-(v)} x[u] / |N+(u)|,
+ * t uniform over the distinct seeds.  As oracle_pr_rows, it lets a sample of
+ * rows check the one-more-iteration change of a score vector on graphs too
+ * large for a serial run.  Returns 0, or -1 on a bad argument.
+ */
+int oracle_ppr_rows(int64_t n, const int64_t* in_off, const int32_t* in_idx, const int32_t* outdeg, double d,
+                    const double* x, const int32_t* seeds, int32_t nseeds, int64_t nrows, const int64_t* rows,
+                    double* out) {
+  if (n <= 0 || nrows < 0 || nseeds <= 0) return -1;
+  /* distinct seeds: sort a copy */
+  int32_t* sd = (int32_t*)malloc(sizeof(int32_t) * (size_t)nseeds);
+  if (!sd) return -1;
+  memcpy(sd, seeds, sizeof(int32_t) * (size_t)nseeds);
+  qsort(sd, (size_t)nseeds, sizeof(int32_t), cmp_i32);
+  int32_t distinct = 0;
+  for (int32_t i = 0; i < nseeds; ++i) {
+    if (sd[i] < 0 || sd[i] >= n) { free(sd); return -1; }
+    if (i == 0 || sd[i] != sd[i - 1]) sd[distinct++] = sd[i];
+  }
+  const double tval = 1.0 / (double)distinct;
+  for (int64_t i = 0; i < nrows; ++i) {
+    const int64_t v = rows[i];
+    if (v < 0 || v >= n) { free(sd); return -1; }
+    int seed = 0; /* binary search among the distinct seeds */
+    int32_t lo = 0, hi = distinct - 1;
+    while (lo <= hi) {
+      const int32_t mid = (lo + hi) / 2;
+      if (sd[mid] == v) { seed = 1; break; }
+      if (sd[mid] < v) lo = mid + 1; else hi = mid - 1;
+    }
+    double s = 0.0;
+    for (int64_t j = in_off[v]; j < in_off[v + 1]; ++j) {
+      const int32_t u = in_idx[j];
+      if (u < 0 || u >= n) { free(sd); return -1; }
+      if (outdeg[u] > 0) s += x[u] / (double)outdeg[u];
+    }
+    const double b = seed ? (1.0 - d) * tval : 0.0;
+    double prod = d * s;
+    out[i] = b + prod;
+  }
+  free(sd);
+  return 0;
+}
+
+/*
  * Personalized PageRank (not in the paper; the serving workload's variant of
  * the §2.1 equation): the teleport term (1-d)/n becomes (1-d) * t[v] with t
  * uniform over the seed set S (t[v] = 1/|S| for v in S, else 0).  Repeated

@@ -60,3 +60,47 @@ def test_full_size_fp32(cuda_device, kind):
         assert float((x64 - x.double()).abs().sum().item()) <= 1e-4
     finally:
         g.close()
+
+
+def test_full_size_ppr(cuda_device):
+    """Personalized PageRank on the serving graph (Chung-Lu, 2^24 vertices, 5e8
+    draws): each query converges, keeps mass <= 1, and meets the one-more-
+    iteration criterion estimated on 2^17 rows (plus its seeds) recomputed by
+    the oracle (oracle.ppr_rows) from the GPU's scores; a query run through the
+    continuous-batching server equals the batch entry point bit for bit."""
+    import torch
+    n = 1 << 24
+    src, dst = gapgen.chung_lu_device(n, 500_000_000, 2.1, 0x5C)
+    g = gap.Graph.from_edges(n, src, dst, symmetrize=False)
+    del src, dst
+    torch.cuda.empty_cache()
+    try:
+        in_off, in_idx = g.export_csr(1)
+        outdeg = g.export_outdeg()
+        rng = np.random.default_rng(0x5E)
+        cand = np.flatnonzero(outdeg > 0)
+        queries = [rng.choice(cand, size=k).astype(np.int32) for k in (1, 17, 64)]
+        offs = np.concatenate([[0], np.cumsum([len(q) for q in queries])]).astype(np.int64)
+        seeds = np.concatenate(queries).astype(np.int32)
+        out = torch.empty(len(queries) * n, dtype=torch.float32, device="cuda:0")
+        st = gap.gap_ppr_batch(g.handle, offs, seeds, D, 1e-4, 100, out)
+        xs = out.view(len(queries), n)
+        rows = rng.choice(n, 1 << 17, replace=False)
+        for j, q in enumerate(queries):
+            assert st[j]["converged"] and st[j]["final_delta"] < 1e-4
+            x = xs[j].cpu().numpy().astype(np.float64)
+            assert x.min() >= 0 and x.sum() <= 1 + 1e-5
+            y = oracle.ppr_rows(in_off, in_idx, outdeg, x, q, rows, D)
+            est = n * float(np.abs(y - x[rows]).mean())
+            ys = oracle.ppr_rows(in_off, in_idx, outdeg, x, q, np.unique(q).astype(np.int64), D)
+            assert est + float(np.abs(ys - x[np.unique(q)]).sum()) < 1e-4, (j, est)
+        srv = gap.PprServer(g.handle, max_cols=8, damping=D, tol=1e-4, max_iters=100)
+        try:
+            one = torch.empty(n, dtype=torch.float32, device="cuda:0")
+            info = srv.wait(srv.submit(queries[1], one))
+            assert info["iterations"] == st[1]["iterations"]
+            assert torch.equal(one, xs[1])
+        finally:
+            srv.close()
+    finally:
+        g.close()

@@ -349,3 +349,22 @@ def test_pr_rows_is_one_pull_iteration():
     assert np.array_equal(oracle.pr_rows(in_off, in_idx, outdeg, x5, sub), y[sub])
     # sampled estimate of the verifier's summed change is unbiased: full sample = exact
     assert abs(np.abs(y - x5).sum() - oracle.verify(off, idx, x5)) <= 1e-15
+
+
+def test_ppr_rows_is_one_ppr_iteration():
+    """The sampled-row personalized update equals the next iterate of the
+    oracle's PPR run on every row (repeated seeds count once)."""
+    rng = np.random.default_rng(12)
+    n = 250
+    src = rng.integers(0, 200, 1500).astype(np.int32)
+    dst = rng.integers(0, n, 1500).astype(np.int32)
+    off, idx = oracle.build_csr(n, src, dst)
+    in_off, in_idx = oracle.build_csc(n, src, dst)
+    outdeg = np.diff(off).astype(np.int32)
+    seeds = np.array([3, 17, 3, 240, 17, 99], np.int32)
+    x4, _, _ = oracle.ppr(off, idx, seeds, tol=0.0, max_iters=4)
+    x5, _, _ = oracle.ppr(off, idx, seeds, tol=0.0, max_iters=5)
+    y = oracle.ppr_rows(in_off, in_idx, outdeg, x4, seeds, np.arange(n))
+    assert np.max(np.abs(y - x5)) <= 1e-15
+    # the teleport lands on the 4 distinct seeds only
+    assert np.count_nonzero(oracle.ppr_rows(in_off, in_idx, outdeg, np.zeros(n), seeds, np.arange(n))) == 4
