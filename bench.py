@@ -48,6 +48,10 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM bytes (read + write) per launch on kron26 with the GB300 tuning table,
 # from one capture of the launch list (profiles/pull_segmented_kron26.md); only
 # kernels and bin bounds unchanged since then.
+# ncu DRAM bytes of one k_batch_persistent launch on the 256-graph batch with this
+# tuning (profiles/batch_persistent_256.md)
+BATCH_NCU_TRAFFIC = 18.19e9
+BATCH_NCU_TUNING = {"heavy_min_degree": 512, "chunk_arcs": 2048, "block_threads": 512, "blocks_per_sm": 0}
 NCU_TRAFFIC = {"k_pull_small_coo<float,8,32>": 1.431e9, "k_pull_group_seg<8>": 0.611e9,
                "k_pull_hub_chunks": 0.252e9, "k_pull_group_seg<32>": 0.222e9}
 
@@ -489,7 +493,7 @@ def measure_batch(a, dev, steps, warmup):
         "gpu_launches_per_step": st[0]["kernel_launches"],
         "tuning": tu if tu is not None else gap.gap_batch_tuning_default().to_dict(),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": BATCH_NCU_TRAFFIC if tu == BATCH_NCU_TUNING else None,
                      "kernel": "k_batch_persistent (all iterations of all graphs, one launch)",
                      "alg_bytes_per_launch": alg, "launch_ms": kern_ms,
                      "peak_source": f"{kind} hbm_gbs"},

@@ -332,20 +332,35 @@ typedef struct {
   int32_t pad;
 } gap_ppr_query_info_t;
 
+/* The graph must outlive the server.  Errors: INVALID_ARG (NULL graph or out,
+ * max_cols outside [1, 128], damping outside [0,1], tol < 0, max_iters < 1),
+ * OOM (not even 4 columns fit), CUDA. */
 GAP_API gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_reserve, double damping,
                                          double tol, int32_t max_iters, gap_ppr_server_t** out);
-/* Queue a query: seeds (host, 1..4096 ids in [0,n), copied), out = n FP32
- * scores (host or device, caller-owned, written when the query completes). */
+/* Queue a query: seeds (host, 1..4096 ids in [0,n), copied; repeats count
+ * once), out = n FP32 scores (host or device, caller-owned, must stay valid
+ * until the query is reported done).  *ticket identifies the query.
+ * Errors: INVALID_ARG (NULL pointer, nseeds out of range, a seed outside
+ * [0,n)); after a device error in the worker, that error (the server then
+ * accepts nothing more). */
 GAP_API gap_status gap_ppr_submit(gap_ppr_server_t* s, const int32_t* seeds, int32_t nseeds, float* out,
                                   int64_t* ticket);
-/* Non-blocking: *done = 1 once out holds the scores (info filled then). */
+/* Non-blocking: *done = 1 once out holds the scores (info filled then); a
+ * ticket reported done is released, so a later poll or wait on it returns
+ * INVALID_ARG (unknown ticket).  While not done: GAP_OK, or the worker's
+ * device error. */
 GAP_API gap_status gap_ppr_poll(gap_ppr_server_t* s, int64_t ticket, int32_t* done, gap_ppr_query_info_t* info);
-/* Block until the query completed. */
+/* Block until the query completed (then the ticket is released), or until the
+ * worker stopped on a device error (returned). */
 GAP_API gap_status gap_ppr_wait(gap_ppr_server_t* s, int64_t ticket, gap_ppr_query_info_t* info);
-/* Columns, completed queries, engine iterations so far, queries waiting. */
+/* Columns, completed queries, engine iterations so far, queries waiting.
+ * Returns the worker's status (GAP_OK or its device error). */
 GAP_API gap_status gap_ppr_server_info(gap_ppr_server_t* s, int32_t* columns, int64_t* completed, int64_t* steps,
                                        int32_t* waiting);
-/* Stop the worker (queries not yet completed are abandoned) and free everything. */
+/* Stop the worker (queries not yet completed are abandoned: their out
+ * buffers are not written afterwards) and free everything.  submit, poll,
+ * wait and info may be called from any threads concurrently; destroy must not
+ * overlap them. */
 GAP_API void gap_ppr_server_destroy(gap_ppr_server_t* s);
 
 /* ------------------------------------------------- no-allocation variant --- */

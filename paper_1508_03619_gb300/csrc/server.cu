@@ -320,8 +320,13 @@ gap_status gap_ppr_poll(gap_ppr_server_t* S, int64_t ticket, int32_t* done, gap_
   Request* r = nullptr;
   GAP_TRY(lookup(S, ticket, &r));
   *done = r->done;
-  if (r->done && info) *info = r->info;
-  if (!r->done && S->worker_status != GAP_OK) return S->worker_status;
+  if (r->done) {  // reported once: the ticket is released
+    if (info) *info = r->info;
+    S->all.erase(ticket);
+    delete r;
+    return GAP_OK;
+  }
+  if (S->worker_status != GAP_OK) return S->worker_status;
   return GAP_OK;
 }
 
@@ -337,6 +342,8 @@ gap_status gap_ppr_wait(gap_ppr_server_t* S, int64_t ticket, gap_ppr_query_info_
   S->cv_done.wait(lk, [&] { return r->done || S->worker_status != GAP_OK; });
   if (!r->done) return S->worker_status;
   if (info) *info = r->info;
+  S->all.erase(ticket);  // the ticket is released
+  delete r;
   return GAP_OK;
 }
 

@@ -404,7 +404,10 @@ class PprServer:
         info = gap_ppr_query_info_t()
         _check(load().gap_ppr_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(info)),
                "gap_ppr_poll")
-        return (info.to_dict() if done.value else None)
+        if done.value:  # the ticket is released once reported done
+            self._keep.pop(ticket, None)
+            return info.to_dict()
+        return None
 
     def wait(self, ticket):
         info = gap_ppr_query_info_t()

@@ -70,3 +70,30 @@ def test_server_bad_input_and_destroy_with_pending(cuda_device):
     finally:
         srv.close()  # abandons what is still queued; must not hang
         g.close()
+
+
+def test_server_releases_tickets(cuda_device):
+    """A ticket reported done (by wait or poll) is released: asking again is an
+    error, so a long-running server holds only queries in flight."""
+    n = 1000
+    src, dst = gapgen.urand(n, 8000, 0x63)
+    g = gpu_graph(n, src, dst)
+    srv = gap.PprServer(g.handle, max_cols=4, damping=D, tol=1e-4, max_iters=100)
+    try:
+        t1 = srv.submit(np.array([1, 2], np.int32), np.zeros(n, np.float32))
+        t2 = srv.submit(np.array([3], np.int32), np.zeros(n, np.float32))
+        assert srv.wait(t1)["converged"]
+        with pytest.raises(gap.GapError) as e:
+            srv.wait(t1)
+        assert e.value.status == gap.GAP_ERR_INVALID_ARG
+        info = None
+        while info is None:
+            info = srv.poll(t2)
+            time.sleep(0.001)
+        assert info["converged"]
+        with pytest.raises(gap.GapError):
+            srv.poll(t2)
+        assert not srv._keep
+    finally:
+        srv.close()
+        g.close()
