@@ -47,7 +47,8 @@ EXPORTED = (
     "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
-    "gap_batch_tuning_default", "gap_pr_run_batch", "gap_pr_run_batch_ex", "gap_ppr_batch", "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
+    "gap_batch_tuning_default", "gap_pr_run_batch", "gap_pr_run_batch_ex", "gap_ppr_batch",
+    "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
     "gap_ppr_server_info", "gap_ppr_server_destroy",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
@@ -281,13 +282,14 @@ def gap_pr_options_default() -> gap_pr_options:
     return o
 
 
-def _check_scores(h, scores, itemsize: int, where: str):
+def _check_scores(h, scores, itemsize: int, where: str, n=None):
     """The C ABI cannot see buffer sizes: for tensors and arrays, check here that
     the output holds n elements of the run's precision (raw integer addresses
-    are passed through unchecked)."""
+    are passed through unchecked).  `n` may be given when the caller knows it."""
     if scores is None or isinstance(scores, int):
         return
-    n = gap_graph_info(h)[0]
+    if n is None:
+        n = gap_graph_info(h)[0]
     if hasattr(scores, "element_size"):
         size, numel = scores.element_size(), scores.numel()
         floating = scores.is_floating_point()
@@ -337,16 +339,22 @@ def gap_batch_tuning_default():
 def gap_pr_run_batch(handles, scores, damping: float, tol: float, max_iters: int, stats=True,
                      stream=None, tuning=None):
     """PageRank on len(handles) graphs in one persistent launch (see gap.h);
-    scores[i] is a float32 device tensor of graph i's n floats.  `tuning` is a
-    gap_batch_tuning or a dict of its fields (None = built-in).  Returns the
-    per-graph stats dicts when `stats`."""
+    handles are gap_graph_t handles or Graph objects, scores[i] a float32
+    device tensor of graph i's n floats.  `tuning` is a gap_batch_tuning or a
+    dict of its fields (None = built-in).  Returns the per-graph stats dicts
+    when `stats`."""
     count = len(handles)
     if len(scores) != count:
         raise ValueError(f"gap_pr_run_batch: {count} graphs but {len(scores)} score arrays")
+    raw = []
     for i, (h, sc) in enumerate(zip(handles, scores)):
-        _check_scores(h, sc, 4, f"gap_pr_run_batch[{i}]")
-    hs = (ctypes.c_void_p * max(count, 1))(*[h if isinstance(h, ctypes.c_void_p) else _ptr(h)
-                                              for h in handles])
+        if isinstance(h, Graph):  # n is known: no library call per graph
+            _check_scores(h.handle, sc, 4, "gap_pr_run_batch", n=h.n)
+            raw.append(h.handle)
+        else:
+            _check_scores(h, sc, 4, "gap_pr_run_batch")
+            raw.append(h)
+    hs = (ctypes.c_void_p * max(count, 1))(*[h if isinstance(h, ctypes.c_void_p) else _ptr(h) for h in raw])
     ps = (ctypes.c_void_p * max(count, 1))(*[_ptr(sc) for sc in scores])
     st = (gap_pr_stats_t * max(count, 1))() if stats else None
     if tuning is None:
