@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--ppr-seconds", type=float, default=6.0, help="arrival window per load level")
     ap.add_argument("--ppr-scale", type=int, default=24)
     ap.add_argument("--ppr-edges", type=float, default=5e8)
+    ap.add_argument("--ppr-cols", type=int, default=128, help="server columns (power of two, <= 128)")
     return ap.parse_args()
 
 
@@ -562,7 +563,7 @@ def measure_ppr(a, dev):
     res["one_at_a_time_iterations"] = its1
     del one
 
-    srv = gap.PprServer(g.handle, max_cols=128, hbm_reserve=16 << 30, damping=DAMPING, tol=TOL,
+    srv = gap.PprServer(g.handle, max_cols=a.ppr_cols, hbm_reserve=16 << 30, damping=DAMPING, tol=TOL,
                         max_iters=MAX_ITERS)
     cols = srv.info()["columns"]
     ring = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3 * cols)]
@@ -628,6 +629,7 @@ def measure_ppr(a, dev):
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))})
     res["poisson"] = loads
     res["batching_gain"] = sat / res["one_at_a_time_qps"]
+    res["server"] = srv.info()  # engine widths and how often the server changed width
     srv.close()
     g.close()
     del ring

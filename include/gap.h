@@ -357,6 +357,23 @@ GAP_API gap_status gap_ppr_wait(gap_ppr_server_t* s, int64_t ticket, gap_ppr_que
  * Returns the worker's status (GAP_OK or its device error). */
 GAP_API gap_status gap_ppr_server_info(gap_ppr_server_t* s, int32_t* columns, int64_t* completed, int64_t* steps,
                                        int32_t* waiting);
+/* Serving state, with the engine widths: the worker runs a narrow engine (a
+ * quarter of the columns, from 16 columns up) while running plus waiting
+ * queries fit in it, and moves the running columns to the wide engine when
+ * they do not (back once they fit in half the narrow width); a move changes
+ * no result. */
+typedef struct {
+  int32_t columns;        /* wide engine columns */
+  int32_t narrow_columns; /* narrow engine columns (0: the server has no narrow engine) */
+  int32_t narrow;         /* 1 while the narrow engine runs */
+  int32_t live;           /* queries in columns */
+  int32_t waiting;        /* queries queued */
+  int32_t pad;
+  int64_t switches;       /* width changes so far */
+  int64_t completed;
+  int64_t steps;          /* engine iterations so far */
+} gap_ppr_server_info_t;
+GAP_API gap_status gap_ppr_server_info_ex(gap_ppr_server_t* s, gap_ppr_server_info_t* out);
 /* Stop the worker (queries not yet completed are abandoned: their out
  * buffers are not written afterwards) and free everything.  submit, poll,
  * wait and info may be called from any threads concurrently; destroy must not

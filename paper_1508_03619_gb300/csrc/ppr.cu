@@ -318,6 +318,55 @@ __global__ void k_ppr_ctrl_init(PprCtrl* ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) memset(ctrl, 0, sizeof(PprCtrl));
 }
 
+// Move columns between two engines over the same graph (a server changing its
+// width): for each pair (from, to), the scores and the contributions the next
+// iteration reads, and the seed bit.  The next iteration rewrites every other
+// contribution, so nothing else of a column lives in the big arrays.
+__global__ void k_ppr_move_cols(const float* __restrict__ sx, const float* __restrict__ scin,
+                                const uint32_t* __restrict__ smask, int KPs, int mws, float* dx, float* dcin,
+                                uint32_t* dmask, int KPd, int mwd, int64_t n, const int2* __restrict__ map,
+                                int count) {
+  const int64_t total = n * count;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t / count;
+    const int2 mv = map[t % count];
+    dx[v * KPd + mv.y] = sx[v * KPs + mv.x];
+    dcin[v * KPd + mv.y] = scin[v * KPs + mv.x];
+    const bool seed = (smask[v * mws + (mv.x >> 5)] >> (mv.x & 31)) & 1u;
+    uint32_t* w = &dmask[v * mwd + (mv.y >> 5)];
+    if (seed) atomicOr(w, 1u << (mv.y & 31));
+    else atomicAnd(w, ~(1u << (mv.y & 31)));
+  }
+}
+
+// The per-column control state of the moved columns (iterations, delta
+// history, teleport, active flag); every other column of the target stops.
+__global__ void k_ppr_move_ctrl(const PprCtrl* __restrict__ sc, PprCtrl* dc, int KPd, const int2* __restrict__ map,
+                                int count) {
+  for (int c = threadIdx.x; c < KPd; c += blockDim.x) {
+    dc->col[c].active = 0;
+    dc->active[c] = 0;
+    dc->acc[c] = 0ull;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int2 mv = map[i];
+    dc->col[mv.y] = sc->col[mv.x];
+    dc->active[mv.y] = sc->active[mv.x];
+    dc->base[mv.y] = sc->base[mv.x];
+  }
+  if (threadIdx.x == 0) dc->any_active = count > 0;
+}
+
+__global__ void k_ppr_stop_all(PprCtrl* c, int KP) {
+  for (int i = threadIdx.x; i < KP; i += blockDim.x) {
+    c->col[i].active = 0;
+    c->active[i] = 0;
+    c->acc[i] = 0ull;
+  }
+  if (threadIdx.x == 0) c->any_active = 0;
+}
+
 // ---- host side ----------------------------------------------------------------
 
 gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStream_t s) {
@@ -451,6 +500,29 @@ gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStre
 gap_status ppr_engine_extract(PprEngine* e, int col, float* out, cudaStream_t s) {
   k_ppr_extract<<<stride_grid(e->g->n, 256, 4), 256, 0, s>>>(e->xbuf.as<float>(), e->g->n, e->KP, col, out);
   GAP_LAUNCH_CHECK();
+  return GAP_OK;
+}
+
+gap_status ppr_engine_move_columns(PprEngine* src, PprEngine* dst, const int32_t* from, const int32_t* to, int count,
+                                   cudaStream_t s) {
+  Scratch dmap;
+  std::vector<int2> hm(count > 0 ? count : 1);
+  for (int i = 0; i < count; ++i) hm[i] = make_int2(from[i], to[i]);
+  GAP_TRY(dmap.get(sizeof(int2) * hm.size(), s));
+  GAP_CUDA(cudaMemcpyAsync(dmap.p, hm.data(), sizeof(int2) * hm.size(), cudaMemcpyHostToDevice, s));
+  const int64_t n = src->g->n;
+  if (count > 0) {
+    k_ppr_move_cols<<<stride_grid(n * count, 256, 8), 256, 0, s>>>(
+        src->xbuf.as<float>(), ppr_c(src, src->parity), src->mask.as<uint32_t>(), src->KP, src->mask_words,
+        dst->xbuf.as<float>(), ppr_c(dst, dst->parity), dst->mask.as<uint32_t>(), dst->KP, dst->mask_words, n,
+        dmap.as<int2>(), count);
+    GAP_LAUNCH_CHECK();
+  }
+  k_ppr_move_ctrl<<<1, 128, 0, s>>>(src->ctrl.as<PprCtrl>(), dst->ctrl.as<PprCtrl>(), dst->KP, dmap.as<int2>(), count);
+  GAP_LAUNCH_CHECK();
+  k_ppr_stop_all<<<1, 128, 0, s>>>(src->ctrl.as<PprCtrl>(), src->KP);
+  GAP_LAUNCH_CHECK();
+  GAP_CUDA(cudaStreamSynchronize(s));  // the host map must outlive the copy
   return GAP_OK;
 }
 

@@ -52,6 +52,10 @@ gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStre
                            cudaGraphConditionalHandle h, int use_h);
 gap_status ppr_engine_extract(PprEngine* e, int col, float* out, cudaStream_t s);
 void ppr_engine_release(PprEngine* e);  // scratch released in stream order
+// Move live columns from[i] of src to columns to[i] of dst (same graph); all
+// other columns of dst stop, and every column of src stops.
+gap_status ppr_engine_move_columns(PprEngine* src, PprEngine* dst, const int32_t* from, const int32_t* to, int count,
+                                   cudaStream_t s);
 int ppr_width_for(int q);
 
 }  // namespace gap

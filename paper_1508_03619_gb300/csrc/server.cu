@@ -7,7 +7,22 @@
 // the free HBM (minus a caller-given reserve).  Because a column's arithmetic
 // does not depend on its slot or on the other columns (see ppr.cu), a query's
 // result is the same whether it ran alone or in a busy mix.
+//
+// Two widths: an iteration of the wide engine costs about the same whether 4
+// or 128 of its columns are live (each warp has four arcs in flight either
+// way), so a narrow engine (a quarter of the columns, more rows in flight per
+// warp) serves a light load with much lower latency.  The worker prefers the
+// narrow engine while the arrival rate of the last second stays below ~70 %
+// of the narrow engine's measured capacity (columns / (iterations per query x
+// seconds per iteration)).  It moves the live columns up when that no longer
+// holds and they do not fit, or when the queue exceeds twice the narrow width;
+// when the narrow engine becomes preferred again it admits new queries only
+// into the low columns of the wide engine until the high ones drained, then
+// moves down.  A move carries a column's scores, the contributions its next
+// iteration reads, its seed bit and its control state, so its result is
+// unchanged.
 #include <algorithm>
+#include <cstring>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -57,7 +72,15 @@ struct gap_ppr_server {
   double d = 0.85, tol = 1e-4;
   int32_t max_iters = 100;
   int32_t cols = 0;
-  gap::PprEngine eng;
+  gap::PprEngine eng;   // wide: `cols` columns
+  gap::PprEngine neng;  // narrow: `ncols` columns (0: no narrow engine)
+  int32_t ncols = 0;
+  int32_t narrow = 0;   // 1 while the narrow engine runs
+  int64_t switches = 0;
+  bool prefer_narrow = true;
+  std::deque<std::chrono::steady_clock::time_point> arrivals;  // submits of the last second
+  double t_iter[2] = {0.0, 0.0};  // measured seconds per iteration: [0] wide, [1] narrow
+  double iters_per_query = 0.0;   // measured
   cudaStream_t s = nullptr;
   std::thread worker;
   std::mutex mu;
@@ -77,11 +100,68 @@ struct gap_ppr_server {
 
 namespace gap {
 
+static PprEngine* srv_engine(gap_ppr_server* S) { return S->narrow ? &S->neng : &S->eng; }
+
+// Narrow <-> wide.  Caller holds S->mu, between iterations.
+static void srv_update_preference(gap_ppr_server* S) {
+  const auto now = std::chrono::steady_clock::now();
+  while (!S->arrivals.empty() && now - S->arrivals.front() > std::chrono::seconds(1)) S->arrivals.pop_front();
+  const double rate = (double)S->arrivals.size();  // arrivals per second
+  if (S->t_iter[1] <= 0.0 || S->iters_per_query <= 0.0) {
+    S->prefer_narrow = true;  // nothing measured yet: the queue rule below decides
+    return;
+  }
+  const double cap = S->ncols / (S->iters_per_query * S->t_iter[1]);
+  if (S->prefer_narrow && rate > 0.85 * cap) S->prefer_narrow = false;
+  else if (!S->prefer_narrow && rate < 0.7 * cap) S->prefer_narrow = true;
+}
+
+static gap_status srv_switch(gap_ppr_server* S) {
+  if (S->ncols == 0) return GAP_OK;
+  srv_update_preference(S);
+  int live = 0, live_high = 0;
+  for (int c = 0; c < S->cols; ++c) {
+    live += S->slot[c] != nullptr;
+    live_high += c >= S->ncols && S->slot[c] != nullptr;
+  }
+  const int waiting = (int)S->pending.size();
+  std::vector<int32_t> from, to;
+  if (S->narrow) {
+    const bool overflow = live + waiting > S->ncols;
+    if ((overflow && !S->prefer_narrow) || waiting > 2 * S->ncols) {  // up: same column numbers
+      for (int c = 0; c < S->ncols; ++c)
+        if (S->slot[c]) {
+          from.push_back(c);
+          to.push_back(c);
+        }
+      GAP_TRY(ppr_engine_move_columns(&S->neng, &S->eng, from.data(), to.data(), (int)from.size(), S->s));
+      S->narrow = 0;
+      ++S->switches;
+    }
+  } else if (S->prefer_narrow && live_high == 0 && waiting <= 2 * S->ncols) {  // down
+    for (int c = 0; c < S->ncols; ++c)
+      if (S->slot[c]) {
+        from.push_back(c);
+        to.push_back(c);
+      }
+    GAP_TRY(ppr_engine_move_columns(&S->eng, &S->neng, from.data(), to.data(), (int)from.size(), S->s));
+    S->narrow = 1;
+    ++S->switches;
+  }
+  return GAP_OK;
+}
+
 static gap_status srv_admit(gap_ppr_server* S) {
   // caller holds S->mu; fills free columns with waiting queries
+  GAP_TRY(srv_switch(S));
+  PprEngine* E = srv_engine(S);
+  // a wide engine that is draining toward the narrow one admits into its low columns only
+  const int width = (S->narrow || (S->ncols && S->prefer_narrow && S->pending.size() <= 2u * S->ncols))
+                        ? S->ncols
+                        : S->cols;
   std::vector<int32_t> newcols;
   std::vector<Request*> newreq;
-  for (int c = 0; c < S->cols && !S->pending.empty(); ++c) {
+  for (int c = 0; c < width && !S->pending.empty(); ++c) {
     if (S->slot[c]) continue;
     Request* r = S->pending.front();
     S->pending.pop_front();
@@ -93,14 +173,14 @@ static gap_status srv_admit(gap_ppr_server* S) {
   GAP_CUDA(cudaMemcpyAsync(S->cols_dev, newcols.data(), sizeof(int32_t) * newcols.size(), cudaMemcpyHostToDevice, S->s));
   const int64_t n = S->g->n;
   k_srv_clear<<<stride_grid(n * (int64_t)newcols.size(), 256, 8), 256, 0, S->s>>>(
-      S->eng.xbuf.as<float>(), S->eng.cbuf.as<float>(), S->eng.cbuf.as<float>() + (size_t)n * S->eng.KP,
-      S->eng.mask.as<uint32_t>(), n, S->eng.KP, S->eng.mask_words, S->cols_dev, (int)newcols.size());
+      E->xbuf.as<float>(), E->cbuf.as<float>(), E->cbuf.as<float>() + (size_t)n * E->KP, E->mask.as<uint32_t>(), n,
+      E->KP, E->mask_words, S->cols_dev, (int)newcols.size());
   GAP_LAUNCH_CHECK();
   for (size_t i = 0; i < newcols.size(); ++i) {
     Request* r = newreq[i];
     int32_t* sd = S->seed_dev + (size_t)newcols[i] * SERVER_MAX_SEEDS;
     GAP_CUDA(cudaMemcpyAsync(sd, r->seeds.data(), sizeof(int32_t) * r->seeds.size(), cudaMemcpyHostToDevice, S->s));
-    GAP_TRY(ppr_engine_set_column(&S->eng, newcols[i], sd, (int32_t)r->seeds.size(), r->distinct, S->s,
+    GAP_TRY(ppr_engine_set_column(E, newcols[i], sd, (int32_t)r->seeds.size(), r->distinct, S->s,
                                   /*clear=*/false));
   }
   // host seed vectors must stay alive until the copies ran
@@ -110,14 +190,16 @@ static gap_status srv_admit(gap_ppr_server* S) {
 
 static gap_status srv_retire(gap_ppr_server* S) {
   // after a step: columns that stopped are copied out and freed
-  GAP_CUDA(cudaMemcpyAsync(S->hctrl, S->eng.ctrl.p, sizeof(PprCtrl), cudaMemcpyDeviceToHost, S->s));
+  PprEngine* E = srv_engine(S);
+  GAP_CUDA(cudaMemcpyAsync(S->hctrl, E->ctrl.p, sizeof(PprCtrl), cudaMemcpyDeviceToHost, S->s));
   GAP_CUDA(cudaStreamSynchronize(S->s));
   const int64_t n = S->g->n;
-  for (int c = 0; c < S->cols; ++c) {
+  const int width = S->narrow ? S->ncols : S->cols;
+  for (int c = 0; c < width; ++c) {
     Request* r = S->slot[c];
     if (!r || S->hctrl->col[c].active) continue;
     float* dst = r->out_dev ? r->out : S->stage;
-    GAP_TRY(ppr_engine_extract(&S->eng, c, dst, S->s));
+    GAP_TRY(ppr_engine_extract(E, c, dst, S->s));
     if (!r->out_dev) GAP_CUDA(cudaMemcpyAsync(r->out, S->stage, sizeof(float) * n, cudaMemcpyDefault, S->s));
     GAP_CUDA(cudaStreamSynchronize(S->s));
     const PprColumn& col = S->hctrl->col[c];
@@ -129,6 +211,7 @@ static gap_status srv_retire(gap_ppr_server* S) {
     r->info.latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
     r->info.column = c;
     r->done = 1;
+    S->iters_per_query = S->iters_per_query > 0.0 ? 0.9 * S->iters_per_query + 0.1 * col.iterations : col.iterations;
     S->slot[c] = nullptr;
     ++S->completed;
   }
@@ -156,8 +239,15 @@ static void srv_loop(gap_ppr_server* S) {
         return;
       }
     }
-    gap_status st = ppr_engine_step(&S->eng, S->tol, S->max_iters, S->s, 0, 0);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int mode = S->narrow;
+    gap_status st = ppr_engine_step(srv_engine(S), S->tol, S->max_iters, S->s, 0, 0);
     if (st == GAP_OK) st = srv_retire(S);
+    if (st == GAP_OK) {
+      const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->t_iter[mode] = S->t_iter[mode] > 0.0 ? 0.9 * S->t_iter[mode] + 0.1 * dt : dt;
+    }
     if (st != GAP_OK) {
       std::lock_guard<std::mutex> lk(S->mu);
       S->worker_status = st;
@@ -180,6 +270,7 @@ static void srv_free(gap_ppr_server* S) {
   S->all.clear();
   // the engine's scratch is released on its stream by its destructors
   ppr_engine_release(&S->eng);
+  ppr_engine_release(&S->neng);
   if (S->s) {
     cudaStreamSynchronize(S->s);
     cudaStreamDestroy(S->s);
@@ -207,11 +298,17 @@ gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_re
   size_t free_b = 0, total_b = 0;
   GAP_CUDA(cudaMemGetInfo(&free_b, &total_b));
   int kp = ppr_width_for(max_cols);
-  auto need = [&](int k) {
+  auto engine_bytes = [&](int k) {
     const double cells = (double)g->n * k;
     const double chunks = (double)chunk_capacity(g->m, PPR_HEAVY, PPR_CHUNK);
-    return cells * 12.0 + (double)g->n * 4.0 * ((k + 31) / 32) + (double)g->n * 4.0 + (double)k * SERVER_MAX_SEEDS * 4.0 +
-           chunks * (sizeof(ChunkDesc) + 4.0 + 4.0 * k) + (64 << 20);
+    return cells * 12.0 + (double)g->n * 4.0 * ((k + 31) / 32) + chunks * (sizeof(ChunkDesc) + 4.0 + 4.0 * k);
+  };
+  // the narrow engine: a quarter of the columns (at least 4), from 16 columns up
+  auto narrow_for = [&](int k) { return k >= 16 ? std::max(4, k / 4) : 0; };
+  auto need = [&](int k) {
+    const int nk = narrow_for(std::min(max_cols, k));
+    return engine_bytes(k) + (nk ? engine_bytes(ppr_width_for(nk)) : 0.0) + (double)g->n * 4.0 +
+           (double)k * SERVER_MAX_SEEDS * 4.0 + (64 << 20);
   };
   while (kp > 4 && need(kp) + (double)hbm_reserve > (double)free_b) kp /= 2;
   if (need(kp) + (double)hbm_reserve > (double)free_b) {
@@ -224,10 +321,13 @@ gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_re
   S->tol = tol;
   S->max_iters = max_iters;
   S->cols = std::min<int32_t>(max_cols, kp);
+  S->ncols = narrow_for(S->cols);
+  S->narrow = S->ncols > 0;
   gap_status st = GAP_OK;
   do {
     if (cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking) != cudaSuccess) { st = GAP_ERR_CUDA; break; }
     if ((st = ppr_engine_init(&S->eng, g, kp, damping, S->s)) != GAP_OK) break;
+    if (S->ncols && (st = ppr_engine_init(&S->neng, g, ppr_width_for(S->ncols), damping, S->s)) != GAP_OK) break;
     if (cudaMalloc(&S->seed_dev, sizeof(int32_t) * SERVER_MAX_SEEDS * kp) != cudaSuccess ||
         cudaMalloc(&S->cols_dev, sizeof(int32_t) * kp) != cudaSuccess ||
         cudaMalloc(&S->stage, sizeof(float) * g->n) != cudaSuccess ||
@@ -264,6 +364,27 @@ gap_status gap_ppr_server_info(gap_ppr_server_t* S, int32_t* columns, int64_t* c
   return S->worker_status;
 }
 
+gap_status gap_ppr_server_info_ex(gap_ppr_server_t* S, gap_ppr_server_info_t* out) {
+  clear_error();
+  if (!S || !out) {
+    set_error("gap_ppr_server_info_ex: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  memset(out, 0, sizeof(*out));
+  out->columns = S->cols;
+  out->narrow_columns = S->ncols;
+  out->narrow = S->narrow;
+  int live = 0;
+  for (Request* r : S->slot) live += r != nullptr;
+  out->live = live;
+  out->waiting = (int32_t)S->pending.size();
+  out->switches = S->switches;
+  out->completed = S->completed;
+  out->steps = S->steps;
+  return S->worker_status;
+}
+
 gap_status gap_ppr_submit(gap_ppr_server_t* S, const int32_t* seeds, int32_t nseeds, float* out, int64_t* ticket) {
   clear_error();
   if (!S || !seeds || !out || !ticket || nseeds < 1 || nseeds > SERVER_MAX_SEEDS) {
@@ -294,6 +415,8 @@ gap_status gap_ppr_submit(gap_ppr_server_t* S, const int32_t* seeds, int32_t nse
     r->ticket = S->next_ticket++;
     S->all[r->ticket] = r;
     S->pending.push_back(r);
+    S->arrivals.push_back(r->t_submit);
+    if (S->arrivals.size() > 100000) S->arrivals.pop_front();
   }
   S->cv_work.notify_one();
   *ticket = r->ticket;

@@ -49,7 +49,7 @@ EXPORTED = (
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
     "gap_batch_tuning_default", "gap_pr_run_batch", "gap_pr_run_batch_ex", "gap_ppr_batch",
     "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
-    "gap_ppr_server_info", "gap_ppr_server_destroy",
+    "gap_ppr_server_info", "gap_ppr_server_info_ex", "gap_ppr_server_destroy",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
@@ -115,6 +115,15 @@ class gap_ppr_query_info_t(ctypes.Structure):
                 "final_delta": self.final_delta, "latency_ms": self.latency_ms, "column": self.column}
 
 
+class gap_ppr_server_info_t(ctypes.Structure):
+    _fields_ = [("columns", ctypes.c_int32), ("narrow_columns", ctypes.c_int32), ("narrow", ctypes.c_int32),
+                ("live", ctypes.c_int32), ("waiting", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("switches", ctypes.c_int64), ("completed", ctypes.c_int64), ("steps", ctypes.c_int64)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class GapError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {status_string(status)} ({status}): {msg}")
@@ -168,6 +177,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_ppr_wait": ([vp, i64, ctypes.POINTER(gap_ppr_query_info_t)], st),
         "gap_ppr_server_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64),
                                  ctypes.POINTER(i32)], st),
+        "gap_ppr_server_info_ex": ([vp, ctypes.POINTER(gap_ppr_server_info_t)], st),
         "gap_ppr_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -424,10 +434,9 @@ class PprServer:
         return info.to_dict()
 
     def info(self):
-        c, done, steps, w = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
-        _check(load().gap_ppr_server_info(self.handle, ctypes.byref(c), ctypes.byref(done),
-                                          ctypes.byref(steps), ctypes.byref(w)), "gap_ppr_server_info")
-        return {"columns": c.value, "completed": done.value, "steps": steps.value, "waiting": w.value}
+        i = gap_ppr_server_info_t()
+        _check(load().gap_ppr_server_info_ex(self.handle, ctypes.byref(i)), "gap_ppr_server_info_ex")
+        return i.to_dict()
 
     def close(self):
         if self.handle is not None and self.handle.value:

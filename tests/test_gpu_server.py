@@ -97,3 +97,46 @@ def test_server_releases_tickets(cuda_device):
     finally:
         srv.close()
         g.close()
+
+
+def test_server_width_changes_keep_results(cuda_device):
+    """A 16-column server runs a 4-column engine while the load is light, moves
+    the running columns to the 16-column engine when a burst queues far beyond
+    the narrow width, and back once it drained: every query's scores and
+    iteration count equal the same query run alone, bit for bit."""
+    import torch
+    n = 1 << 12
+    src, dst = gapgen.kron(12, 16, 0x64)
+    off, idx = oracle_graph(n, src, dst, True)
+    cand = np.flatnonzero(np.diff(off) > 0)
+    rng = np.random.default_rng(6)
+    g = gpu_graph(n, src, dst, True)
+    srv = gap.PprServer(g.handle, max_cols=16, damping=D, tol=1e-6, max_iters=100)
+    try:
+        i0 = srv.info()
+        assert i0["columns"] == 16 and i0["narrow_columns"] == 4 and i0["narrow"] == 1
+        queries, outs, tickets = [], [], []
+
+        def submit(k):
+            for _ in range(k):
+                seeds = rng.choice(cand, size=int(rng.integers(1, 20))).astype(np.int32)
+                out = torch.zeros(n, dtype=torch.float32, device="cuda:0")
+                queries.append(seeds)
+                outs.append(out)
+                tickets.append(srv.submit(seeds, out))
+
+        submit(2)            # narrow engine
+        time.sleep(0.01)
+        submit(30)           # a queue far beyond twice the narrow width: the running queries move up
+        infos = [srv.wait(t) for t in tickets]
+        submit(2)            # drained: back to the narrow engine
+        infos += [srv.wait(t) for t in tickets[32:]]
+        s = srv.info()
+        assert s["switches"] >= 2 and s["completed"] == 34 and s["narrow"] == 1
+        for seeds, out, info in zip(queries, outs, infos):
+            ref, st = alone(g, seeds, tol=1e-6)
+            assert info["iterations"] == st["iterations"] and info["converged"]
+            assert np.array_equal(out.cpu().numpy(), ref)
+    finally:
+        srv.close()
+        g.close()
