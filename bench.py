@@ -190,6 +190,7 @@ def roofline_entry(sp, m, n, segments, contrib_bytes=4):
     total_ms = sum(sp["phase_ms"].values())
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kname),
+            "useful_byte_efficiency": (per_launch_alg / NCU_TRAFFIC[kname]) if kname in NCU_TRAFFIC else None,
             "kernel": f"{kname} (bin {q}: in-degree <= {b['max_degree']}, "
                       + ("packed COO, one pass per source segment)" if lanes == -1 and segments > 1 else
                          "segmented)" if b["segmented"] else "whole rows)"),
@@ -207,7 +208,10 @@ def roofline_entry(sp, m, n, segments, contrib_bytes=4):
 
 def cpu_baseline(a, seconds=12.0):
     """The oracle (single-threaded FP64 push PageRank) on a bounded sample of
-    the workload: the same generator at a smaller scale, fixed iterations."""
+    the workload: the same generator at a smaller scale, fixed iterations.  Also
+    a multi-core FP64 pull loop (OpenMP, all host cores) on the same sample."""
+    import numpy as np
+
     import gapgen
     import oracle
     scale = min(a.scale, 21)
@@ -222,9 +226,19 @@ def cpu_baseline(a, seconds=12.0):
     t0 = time.perf_counter()
     _, k, _ = oracle.pagerank(off, idx, DAMPING, 0.0, iters)
     dt = time.perf_counter() - t0
-    return {"value": m * k / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"kron scale {scale} (n={n}, m={m}), {k} FP64 push iterations, single thread, "
-                      f"{dt:.1f} s"}
+    out = {"value": m * k / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"kron scale {scale} (n={n}, m={m}), {k} FP64 push iterations, single thread, "
+                     f"{dt:.1f} s"}
+    # the symmetrized sample's CSR is its CSC
+    outdeg = np.diff(off).astype(np.int32)
+    oracle.cpu_pagerank_pull(off, idx, outdeg, DAMPING, 0.0, 1)
+    t0 = time.perf_counter()
+    _, kp, threads = oracle.cpu_pagerank_pull(off, idx, outdeg, DAMPING, TOL, MAX_ITERS)
+    dtp = time.perf_counter() - t0
+    out["openmp_pull"] = {"value": m * kp / dtp / 1e9, "unit": UNIT, "cores": threads,
+                          "sample": f"same graph, FP64 pull over the CSC to tol 1e-4 ({kp} iterations), "
+                                    f"{threads} OpenMP threads, {dtp:.2f} s"}
+    return out
 
 
 def run_reference(a, ws, rank):

@@ -31,6 +31,9 @@ _SRC = os.path.join(_HERE, "gap_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lib = None
+_OMP_SRC = os.path.join(_HERE, "cpu_pull_omp.c")
+_OMP_LIB = os.path.join(_LIBDIR, "libcpupull.so")
+_omp = None
 
 DAMPING = 0.85
 TOL = 1e-4
@@ -44,6 +47,14 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                                _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
+    if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_OMP_SRC):
+        tmp = _OMP_LIB + f".tmp{os.getpid()}"
+        base = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", _OMP_SRC, "-o", tmp]
+        try:  # the multi-core baseline; one thread where OpenMP is missing
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
+        os.replace(tmp, _OMP_LIB)
     return _LIB
 
 
@@ -159,6 +170,29 @@ def ppr_rows(in_offsets, in_idx, outdeg, x, seeds, rows, d: float = DAMPING):
     if rc != 0:
         raise ValueError(f"oracle_ppr_rows failed ({rc})")
     return out
+
+
+def cpu_pagerank_pull(in_offsets, in_idx, outdeg, d: float = DAMPING, tol: float = TOL, max_iters: int = 100):
+    """Multi-core CPU baseline (not the oracle): pull PageRank over the CSC
+    with OpenMP threads, FP64.  Returns (x, iterations, threads)."""
+    global _omp
+    if _omp is None:
+        build()
+        lib = ctypes.CDLL(_OMP_LIB)
+        lib.cpu_pagerank_pull.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p]
+        lib.cpu_pagerank_pull.restype = ctypes.c_int
+        lib.cpu_pull_threads.restype = ctypes.c_int
+        _omp = lib
+    in_offsets = np.ascontiguousarray(in_offsets, dtype=np.int64)
+    in_idx = np.ascontiguousarray(in_idx, dtype=np.int32)
+    outdeg = np.ascontiguousarray(outdeg, dtype=np.int32)
+    n = len(in_offsets) - 1
+    x = np.empty(n, np.float64)
+    k = _omp.cpu_pagerank_pull(n, _ptr(in_offsets), _ptr(in_idx), _ptr(outdeg), d, tol, max_iters, _ptr(x))
+    if k < 0:
+        raise ValueError(f"cpu_pagerank_pull failed ({k})")
+    return x, int(k), int(_omp.cpu_pull_threads())
 
 
 def ppr(offsets, idx, seeds, d: float = DAMPING, tol: float = TOL, max_iters: int = 100):

@@ -368,3 +368,17 @@ def test_ppr_rows_is_one_ppr_iteration():
     assert np.max(np.abs(y - x5)) <= 1e-15
     # the teleport lands on the 4 distinct seeds only
     assert np.count_nonzero(oracle.ppr_rows(in_off, in_idx, outdeg, np.zeros(n), seeds, np.arange(n))) == 4
+
+
+def test_cpu_pull_baseline_agrees_with_oracle():
+    """The multi-core CPU baseline (pull over the CSC) computes the same
+    iterates as the oracle, to FP64 rounding."""
+    import gapgen
+    n = 1 << 12
+    src, dst = gapgen.kron(12, 16, 13)
+    off, idx = oracle.build_csr(n, src, dst, symmetrize=True)
+    in_off, in_idx = oracle.build_csc(n, src, dst, symmetrize=True)
+    x, k, threads = oracle.cpu_pagerank_pull(in_off, in_idx, np.diff(off).astype(np.int32), tol=0.0, max_iters=20)
+    xo, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=20)
+    assert k == 20 and threads >= 1
+    assert np.abs(x - xo).sum() <= 1e-12
