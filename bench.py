@@ -52,8 +52,7 @@ FALLBACK_HBM_GBS = 6800.0
 # tuning (profiles/batch_persistent_256.md)
 BATCH_NCU_TRAFFIC = 18.19e9
 BATCH_NCU_TUNING = {"heavy_min_degree": 512, "chunk_arcs": 2048, "block_threads": 512, "blocks_per_sm": 0}
-NCU_TRAFFIC = {"k_pull_small_coo<float,8,32>": 1.431e9, "k_pull_group_seg<8>": 0.611e9,
-               "k_pull_hub_chunks": 0.252e9, "k_pull_group_seg<32>": 0.222e9}
+NCU_TRAFFIC = {"k_pull_small_coo<float,8,32>": 1.431e9}
 
 
 def parse():

@@ -10,8 +10,8 @@ Tuned here:
                 kernel; group_max_degree: bin 4; cta_max_degree: bin 5, above
                 it hubs), the lanes per row of bin 4 and the hub chunk size.
 Tuning set: the uneven batch generator with its own seed (not the evaluation
-batch's), and Kronecker / uniform-random graphs at scale 25 with their own
-seeds.  Each candidate is timed with CUDA events (median of several trials,
+batch's), and Kronecker / uniform-random graphs at scale 26 (the benchmark's
+size) with their own seeds.  Each candidate is timed with CUDA events (median of several trials,
 inputs larger than L2).  Greedy coordinate search: one parameter at a time,
 starting from the built-in values, two passes.
 
@@ -140,7 +140,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None, help="table file (default tuning/<device>.json)")
     ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--scale", type=int, default=25)
+    ap.add_argument("--scale", type=int, default=26)
     ap.add_argument("--skip", default="", help="comma list: batch,pagerank")
     a = ap.parse_args(argv)
     import torch
