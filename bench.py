@@ -45,14 +45,14 @@ TOL = 1e-4
 MAX_ITERS = 100
 FALLBACK_HBM_GBS = 6800.0
 
-# ncu DRAM bytes (read + write) per launch on kron26 with the GB300 tuning table,
-# from one capture of the launch list (profiles/pull_segmented_kron26.md); only
-# kernels and bin bounds unchanged since then.
 # ncu DRAM bytes of one k_batch_persistent launch on the 256-graph batch with this
 # tuning (profiles/batch_persistent_256.md)
 BATCH_NCU_TRAFFIC = 18.19e9
 BATCH_NCU_TUNING = {"heavy_min_degree": 512, "chunk_arcs": 2048, "block_threads": 512, "blocks_per_sm": 0}
-NCU_TRAFFIC = {"k_pull_small_coo<float,8,32>": 1.431e9}
+# ncu DRAM bytes (read + write) per launch on kron26 with the GB300 tuning table,
+# from one capture of the launch list (profiles/pull_segmented_kron26.md); only
+# kernels and bin bounds unchanged since then.
+NCU_TRAFFIC = {}
 
 
 def parse():

@@ -70,8 +70,9 @@ GAP_API int32_t gap_version(void);
 
 /* ---------------------------------------------------------- allocator --- */
 /* Optional scratch allocator.  alloc(bytes, stream, ctx) returns device memory
- * usable on `stream` (or NULL on failure); free(ptr, bytes, stream, ctx) releases
- * it in stream order.  Passing NULL restores the default (cudaMallocAsync /
+ * usable on `stream`, aligned to 256 bytes like cudaMalloc's (or NULL on
+ * failure; a misaligned block is freed again and the run fails with
+ * GAP_ERR_INVALID_ARG); free(ptr, bytes, stream, ctx) releases it in stream order.  Passing NULL restores the default (cudaMallocAsync /
  * cudaFreeAsync).  Process-wide; not thread-safe against concurrent runs. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* ctx);

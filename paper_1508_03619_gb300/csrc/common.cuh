@@ -59,6 +59,11 @@ struct Scratch {
       set_error("scratch allocation of %zu bytes failed", bytes);
       return GAP_ERR_OOM;
     }
+    if (reinterpret_cast<uintptr_t>(p) & 255u) {  // kernels load 16-byte vectors at 32-byte offsets
+      release();
+      set_error("the scratch allocator returned memory not aligned to 256 bytes");
+      return GAP_ERR_INVALID_ARG;
+    }
     return GAP_OK;
   }
   void release() {

@@ -524,16 +524,38 @@ __global__ void __launch_bounds__(PR_THREADS, 4) k_pull_small_coo(PrArgs<Acc> a,
     const int64_t a1 = t1 < T ? tof[t1] : send;
     int carry_r = -1;
     Acc carry_v = Acc(0);
-    for (int64_t base = a0; base < a1; base += 32 * K) {
+    // batches start K-aligned (32 B), so a lane's K arcs come in K/4 16-byte
+    // loads per array; the arcs before a0 in lane 0's first group belong to
+    // the previous chunk and stand in as zero-valued arcs of the first row
+    for (int64_t base = a0 & ~(int64_t)(K - 1); base < a1; base += 32 * K) {
       const int64_t lb = base + (int64_t)lane * K;
-      const int nact = a1 - lb >= K ? K : (a1 - lb > 0 ? (int)(a1 - lb) : 0);
+      const int klo = lb < a0 ? (int)(a0 - lb) : 0;
+      const int nall = a1 - lb >= K ? K : (a1 - lb > 0 ? (int)(a1 - lb) : 0);
+      const int nact = klo < nall ? nall : 0;
       int rk[K];
+      int32_t uk[K];
       Acc vk[K];
+      if (nact > 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+          const int4 r4 = __ldcs(reinterpret_cast<const int4*>(prow + lb) + q);
+          const int4 u4 = __ldcs(reinterpret_cast<const int4*>(packed + lb) + q);
+          rk[4 * q] = r4.x, rk[4 * q + 1] = r4.y, rk[4 * q + 2] = r4.z, rk[4 * q + 3] = r4.w;
+          uk[4 * q] = u4.x, uk[4 * q + 1] = u4.y, uk[4 * q + 2] = u4.z, uk[4 * q + 3] = u4.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) rk[k] = -1, uk[k] = 0;
+      }
+      int rfirst = -1;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k == klo) rfirst = rk[k];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const bool act = k < nact;
-        rk[k] = act ? __ldcs(prow + lb + k) : -1;
-        const int32_t u = act ? ld_idx(packed + lb + k) : 0;
+        const bool act = k >= klo && k < nact;
+        if (k < klo) rk[k] = rfirst;
+        const int32_t u = uk[k];
         if constexpr (std::is_same<Acc, double>::value) {
           vk[k] = act ? ld_c<double>(reinterpret_cast<const double*>(st.cin), u) : 0.0;
         } else {
@@ -1415,8 +1437,9 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     int64_t small_arcs = 0;
     GAP_CUDA(cudaMemcpyAsync(&small_arcs, sm_total.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GAP_CUDA(cudaStreamSynchronize(s));
-    GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
-    GAP_TRY(sm_prow.get(sizeof(int32_t) * (small_arcs > 0 ? small_arcs : 1), s));
+    // + SMALL_K: the COO passes read whole K-aligned groups past a chunk's end
+    GAP_TRY(sm_packed.get(sizeof(int32_t) * (small_arcs + SMALL_K), s));
+    GAP_TRY(sm_prow.get(sizeof(int32_t) * (small_arcs + SMALL_K), s));
     GAP_TRY(sm_tend.get(sizeof(int64_t) * S, s));
     k_small_pack<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, 0, s>>>(
         g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S, wbits, sm_cnt.as<uint8_t>(), sm_toff.as<int64_t>(), T,

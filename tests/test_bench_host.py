@@ -29,7 +29,8 @@ def _stats(segments, lanes0, dom_ms, launches):
     return {"phase_ms": phase_ms, "phase_launches": launches_d, "bins": bins, "iterations": 7}
 
 
-def test_roofline_entry_of_the_packed_small_row_pass():
+def test_roofline_entry_of_the_packed_small_row_pass(monkeypatch):
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", {"k_pull_small_coo<float,8,32>": 2.0e5})
     st = _stats(segments=8, lanes0=-1, dom_ms=5.6, launches=56)
     r = bench.roofline_entry(st, m=117000, n=1016, segments=8)
     assert r["kernel"].startswith("k_pull_small_coo<float,8,32> (bin 0")
