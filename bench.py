@@ -51,8 +51,9 @@ BATCH_NCU_TRAFFIC = 18.19e9
 BATCH_NCU_TUNING = {"heavy_min_degree": 512, "chunk_arcs": 2048, "block_threads": 512, "blocks_per_sm": 0}
 # ncu DRAM bytes (read + write) per launch on kron26 with the GB300 tuning table,
 # from one capture of the launch list (profiles/pull_segmented_kron26.md); only
-# kernels and bin bounds unchanged since then.
-NCU_TRAFFIC = {}
+# kernels and bin bounds unchanged since then (the small-row COO pass changed
+# after that capture, so it has no entry).
+NCU_TRAFFIC = {"k_pull_group_seg<32>": 0.600e9, "k_pull_group_seg<8>": 0.356e9, "k_pull_hub_chunks": 0.127e9}
 
 
 def parse():

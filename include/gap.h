@@ -124,6 +124,82 @@ GAP_API gap_status gap_graph_export_outdeg(gap_graph_t* g, int32_t* outdeg, void
 /* Release all device memory of the graph (after synchronizing its last run). */
 GAP_API void gap_graph_destroy(gap_graph_t* g);
 
+/* ---------------------------------------------------- graph files --- */
+/* §4 of the paper: the reference infrastructure loads graphs from files (METIS,
+ * Matrix Market, and a plain-text edge list as the easy fallback) and can
+ * serialize a built graph so that later runs load it directly, skipping the
+ * build.  Text files are parsed on the host into an edge list that the device
+ * builder takes like any other; the serialized form holds the in-direction CSR
+ * exactly as the handle stores it.
+ *
+ * Formats (GAP_FMT_AUTO picks by suffix, case-insensitive):
+ *   GAP_FMT_EDGE_LIST      .el .txt    one arc "u v" per line, 0-based ids in
+ *                                      [0, 2^31-2]; further columns (a weight)
+ *                                      ignored; '#' / '%' lines and blank lines
+ *                                      skipped; n = 1 + the largest id.
+ *   GAP_FMT_MATRIX_MARKET  .mtx        "%%MatrixMarket matrix coordinate <field>
+ *                                      <symmetry>"; entry (i, j) = arc i-1 -> j-1;
+ *                                      values ignored; n = max(rows, cols); a
+ *                                      symmetric / skew-symmetric / hermitian
+ *                                      matrix implies GAP_SYMMETRIZE.
+ *   GAP_FMT_METIS          .graph .metis  header "n m [fmt [ncon]]", then line i
+ *                                      lists the 1-based neighbours of vertex i
+ *                                      (arcs i-1 -> j-1; weights skipped; a blank
+ *                                      line is a vertex without neighbours); the
+ *                                      lists must hold 2m arcs.
+ *   GAP_FMT_SERIALIZED     .gcsc       written by gap_graph_save (64-byte header,
+ *                                      int64 offsets[n+1], int32 sources[m],
+ *                                      little-endian, with a payload checksum).
+ * Malformed files give GAP_ERR_INVALID_ARG with "path:line: what" in
+ * gap_last_error_message(). */
+#define GAP_FMT_AUTO 0
+#define GAP_FMT_EDGE_LIST 1
+#define GAP_FMT_MATRIX_MARKET 2
+#define GAP_FMT_METIS 3
+#define GAP_FMT_SERIALIZED 4
+
+typedef struct gap_edge_list gap_edge_list_t;
+
+/* Parse a text graph file (edge list, Matrix Market or METIS) into a host edge
+ * list owned by the returned handle.  Host only: needs no GPU.  Errors:
+ * INVALID_ARG (unreadable or malformed file, or a serialized file), OOM. */
+GAP_API gap_status gap_edge_list_read(const char* path, int32_t format, gap_edge_list_t** out);
+
+/* n, the number of arcs read, and the construction flags the format implies
+ * (GAP_SYMMETRIZE for a symmetric Matrix Market file, else 0). */
+GAP_API gap_status gap_edge_list_info(const gap_edge_list_t* e, int64_t* n, int64_t* m,
+                                      uint32_t* implied_flags);
+
+/* Host arrays src[m], dst[m] of the arcs in file order; valid until
+ * gap_edge_list_destroy. */
+GAP_API gap_status gap_edge_list_arrays(const gap_edge_list_t* e, const int32_t** src,
+                                        const int32_t** dst);
+
+GAP_API void gap_edge_list_destroy(gap_edge_list_t* e);
+
+/* Build a graph from a file.  Text formats: gap_edge_list_read, then
+ * gap_graph_create_from_edges with `flags | implied flags` (GAP_INPUT_ON_DEVICE
+ * is rejected).  Serialized: `flags` is ignored; the two arrays are streamed to
+ * the device through a 64 MB pinned buffer, the checksum is verified, the
+ * structure is checked on the device (offsets monotone from 0 to m, sources in
+ * [0, n) and sorted within each row) and the out-degrees are recounted; the
+ * out-direction CSR is built on first request.  Synchronous.  Errors:
+ * INVALID_ARG (unreadable, malformed, damaged or inconsistent file), OOM, CUDA. */
+GAP_API gap_status gap_graph_load(const char* path, int32_t format, uint32_t flags, void* stream,
+                                  gap_graph_t** out);
+
+/* Write g in GAP_FMT_SERIALIZED to `path` (replaced if it exists; removed again
+ * if writing fails), after g's last run finished.  Synchronous; needs 64 MB of
+ * pinned host memory and reads the arrays from the device twice (checksum,
+ * then data).  Errors: INVALID_ARG (NULL, or the file cannot be written), OOM,
+ * CUDA. */
+GAP_API gap_status gap_graph_save(gap_graph_t* g, const char* path, void* stream);
+
+/* The construction flags g was built with (GAP_SYMMETRIZE | GAP_DEDUP |
+ * GAP_DROP_SELF_LOOPS; for a loaded serialized graph, those recorded in the
+ * file). */
+GAP_API gap_status gap_graph_build_flags(const gap_graph_t* g, uint32_t* flags);
+
 /* ----------------------------------------------------------- PageRank --- */
 /* One PageRank trial (§2.3: allocation of every non-graph structure, degree
  * binning and all iterations happen inside the call).  d = damping (0.85 in the

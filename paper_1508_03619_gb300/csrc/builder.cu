@@ -426,6 +426,7 @@ static gap_status build_from_device_edges(int64_t n, int64_t m, const int32_t* d
   g->n = n;
   g->key_bits = b;
   g->symmetric = symmetrize;
+  g->build_flags = flags & (GAP_SYMMETRIZE | GAP_DEDUP | GAP_DROP_SELF_LOOPS);
   cudaGetDevice(&g->device);
   gap_status st = GAP_OK;
   do {
@@ -497,6 +498,105 @@ static gap_status build_from_device_edges(int64_t n, int64_t m, const int32_t* d
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
   cudaGetLastError();
+  *out = g;
+  return GAP_OK;
+}
+
+// Structure check of an adopted CSC, one thread per row: 0 <= off[v] <=
+// off[v+1] <= m, every source in [0, n), sources non-decreasing within a row
+// (the order the builder writes and the segment passes rely on).  Counts the
+// out-degrees as it goes.  Only in-bounds addresses are ever touched.
+__global__ void k_check_csc(const int64_t* __restrict__ off, const int32_t* __restrict__ idx, int64_t n,
+                            int64_t m, int32_t* __restrict__ outdeg, unsigned* __restrict__ err) {
+  unsigned bad = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = off[v], e = off[v + 1];
+    if (b < 0 || b > e || e > m) {
+      bad |= 1u;
+      continue;
+    }
+    int32_t prev = INT32_MIN;
+    for (int64_t i = b; i < e; ++i) {
+      const int32_t u = idx[i];
+      if (u < 0 || (int64_t)u >= n) {
+        bad |= 2u;
+        continue;
+      }
+      if (u < prev) bad |= 4u;
+      prev = u;
+      atomicAdd(outdeg + u, 1);
+    }
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+gap_status graph_from_csc(int64_t n, int64_t m, int64_t* d_off, int32_t* d_idx, uint32_t build_flags,
+                          cudaStream_t s, gap_graph** out) {
+  gap_graph* g = new gap_graph();
+  g->n = n;
+  g->m = m;
+  g->in_off = d_off;
+  g->in_idx = d_idx;
+  g->key_bits = bits_for(n - 1 > 0 ? n - 1 : 1);
+  g->symmetric = 0;  // not trusted from outside: the out-direction CSR is built on request
+  g->build_flags = build_flags;
+  cudaGetDevice(&g->device);
+  gap_status st = GAP_OK;
+  do {
+    Scratch misc;
+    if ((st = misc.get(64, s)) != GAP_OK) break;
+    unsigned long long* dangling = misc.as<unsigned long long>();
+    unsigned long long* maxdeg = dangling + 1;
+    unsigned* err = reinterpret_cast<unsigned*>(dangling + 2);
+    if (cudaMalloc(&g->outdeg, sizeof(int32_t) * n) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("graph allocation failed");
+      st = GAP_ERR_OOM;
+      break;
+    }
+    if (cudaMemsetAsync(g->outdeg, 0, sizeof(int32_t) * n, s) != cudaSuccess ||
+        cudaMemsetAsync(misc.p, 0, 64, s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
+      break;
+    }
+    k_check_csc<<<stride_grid(n, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(g->in_off, g->in_idx, n, m, g->outdeg, err);
+    if (cudaGetLastError() != cudaSuccess) { st = cuda_fail(cudaErrorLaunchFailure, "k_check_csc", __FILE__, __LINE__); break; }
+    unsigned herr = 0;
+    if (cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "graph check", __FILE__, __LINE__);
+      break;
+    }
+    if (herr) {
+      set_error("not a valid in-direction CSR:%s%s%s", (herr & 1u) ? " offsets not monotone in [0, m];" : "",
+                (herr & 2u) ? " a source outside [0, n);" : "", (herr & 4u) ? " a row not sorted by source;" : "");
+      st = GAP_ERR_INVALID_ARG;
+      break;
+    }
+    k_degree_stats<<<stride_grid(n, BLD_THREADS, 4), BLD_THREADS, 0, s>>>(g->in_off, g->outdeg, n, dangling, maxdeg);
+    if (cudaGetLastError() != cudaSuccess) { st = cuda_fail(cudaErrorLaunchFailure, "k_degree_stats", __FILE__, __LINE__); break; }
+    unsigned long long ds[2];
+    if (cudaMemcpyAsync(ds, dangling, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "graph check", __FILE__, __LINE__);
+      break;
+    }
+    g->n_dangling = (int64_t)ds[0];
+    g->max_in_degree = (int64_t)ds[1];
+    if (cudaMallocHost(&g->stats_host, sizeof(gap_pr_stats_t)) != cudaSuccess ||
+        cudaMallocHost(&g->flag_host, sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned host allocation failed");
+      st = GAP_ERR_OOM;
+      break;
+    }
+    memset(g->stats_host, 0, sizeof(gap_pr_stats_t));
+  } while (0);
+  if (st != GAP_OK) {
+    cudaStreamSynchronize(s);
+    graph_free(g);
+    return st;
+  }
   *out = g;
   return GAP_OK;
 }

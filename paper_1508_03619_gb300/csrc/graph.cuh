@@ -19,6 +19,7 @@ struct gap_graph {
   int64_t max_in_degree = 0;
   int key_bits = 1;  // bits per vertex id in sort keys
   int symmetric = 0;  // built with GAP_SYMMETRIZE: the out-direction CSR equals the in-direction one
+  uint32_t build_flags = 0;  // GAP_SYMMETRIZE | GAP_DEDUP | GAP_DROP_SELF_LOOPS used at construction
   int64_t* in_off = nullptr;
   int32_t* in_idx = nullptr;
   int32_t* outdeg = nullptr;
@@ -53,5 +54,13 @@ gap_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t count, int bits
 // for a symmetrized graph, else built once on the device (kept by the handle,
 // like the in-direction CSR).
 gap_status graph_out_csr(gap_graph* g, cudaStream_t s, const int64_t** off, const int32_t** idx);
+
+// A graph around an in-direction CSR already in device memory (d_off int64[n+1],
+// d_idx int32[m], both from cudaMalloc; the handle owns them from this call on,
+// and frees them if it fails).  Checks the structure on the device (offsets
+// monotone in [0, m], sources in [0, n) and sorted within each row), counts the
+// out-degrees and the degree statistics.  Used by the serialized-graph loader.
+gap_status graph_from_csc(int64_t n, int64_t m, int64_t* d_off, int32_t* d_idx, uint32_t build_flags,
+                          cudaStream_t s, gap_graph** out);
 
 }  // namespace gap

@@ -27,6 +27,12 @@ GAP_DEDUP = 0x2
 GAP_DROP_SELF_LOOPS = 0x4
 GAP_INPUT_ON_DEVICE = 0x8
 
+GAP_FMT_AUTO = 0
+GAP_FMT_EDGE_LIST = 1
+GAP_FMT_MATRIX_MARKET = 2
+GAP_FMT_METIS = 3
+GAP_FMT_SERIALIZED = 4
+
 GAP_PREC_F32 = 0
 GAP_PREC_F64 = 1
 GAP_CONTRIB_F32 = 0
@@ -50,6 +56,8 @@ EXPORTED = (
     "gap_batch_tuning_default", "gap_pr_run_batch", "gap_pr_run_batch_ex", "gap_ppr_batch",
     "gap_ppr_server_create", "gap_ppr_submit", "gap_ppr_poll", "gap_ppr_wait",
     "gap_ppr_server_info", "gap_ppr_server_info_ex", "gap_ppr_server_destroy",
+    "gap_edge_list_read", "gap_edge_list_info", "gap_edge_list_arrays", "gap_edge_list_destroy",
+    "gap_graph_load", "gap_graph_save", "gap_graph_build_flags",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
@@ -179,6 +187,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(i32)], st),
         "gap_ppr_server_info_ex": ([vp, ctypes.POINTER(gap_ppr_server_info_t)], st),
         "gap_ppr_server_destroy": ([vp], None),
+        "gap_edge_list_read": ([ctypes.c_char_p, i32, ctypes.POINTER(vp)], st),
+        "gap_edge_list_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(u32)], st),
+        "gap_edge_list_arrays": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp)], st),
+        "gap_edge_list_destroy": ([vp], None),
+        "gap_graph_load": ([ctypes.c_char_p, i32, u32, vp, ctypes.POINTER(vp)], st),
+        "gap_graph_save": ([vp, ctypes.c_char_p, vp], st),
+        "gap_graph_build_flags": ([vp, ctypes.POINTER(u32)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -282,6 +297,50 @@ def gap_graph_export_outdeg(h, outdeg, stream=None):
 def gap_graph_destroy(h):
     if h is not None and h.value:
         load().gap_graph_destroy(h)
+
+
+# ------------------------------------------------------------ graph files ---
+
+def _path(path) -> bytes:
+    return os.fsencode(path)
+
+
+def gap_edge_list_read(path, fmt: int = GAP_FMT_AUTO):
+    """Parse a text graph file on the host.  Returns (n, src, dst, implied_flags)
+    with src/dst int32 numpy arrays (copies; the library's list is released)."""
+    import numpy as np
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.gap_edge_list_read(_path(path), fmt, ctypes.byref(h)), "gap_edge_list_read")
+    try:
+        n, m, fl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint32()
+        _check(lib.gap_edge_list_info(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(fl)), "gap_edge_list_info")
+        ps, pd = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib.gap_edge_list_arrays(h, ctypes.byref(ps), ctypes.byref(pd)), "gap_edge_list_arrays")
+        src = np.empty(m.value, dtype=np.int32)
+        dst = np.empty(m.value, dtype=np.int32)
+        if m.value:
+            ctypes.memmove(src.ctypes.data, ps.value, 4 * m.value)
+            ctypes.memmove(dst.ctypes.data, pd.value, 4 * m.value)
+        return n.value, src, dst, fl.value
+    finally:
+        lib.gap_edge_list_destroy(h)
+
+
+def gap_graph_load(path, fmt: int = GAP_FMT_AUTO, flags: int = 0, stream=None):
+    out = ctypes.c_void_p()
+    _check(load().gap_graph_load(_path(path), fmt, flags, _stream(stream), ctypes.byref(out)), "gap_graph_load")
+    return out
+
+
+def gap_graph_save(h, path, stream=None):
+    _check(load().gap_graph_save(h, _path(path), _stream(stream)), "gap_graph_save")
+
+
+def gap_graph_build_flags(h) -> int:
+    f = ctypes.c_uint32()
+    _check(load().gap_graph_build_flags(h, ctypes.byref(f)), "gap_graph_build_flags")
+    return f.value
 
 
 # --------------------------------------------------------------- PageRank ---
@@ -482,6 +541,22 @@ class Graph:
         flags = ((GAP_SYMMETRIZE if symmetrize else 0) | (GAP_DEDUP if dedup else 0)
                  | (GAP_DROP_SELF_LOOPS if drop_self_loops else 0))
         return cls(gap_graph_create(n, row_offsets, col_idx, flags, stream))
+
+    @classmethod
+    def load(cls, path, fmt: int = GAP_FMT_AUTO, symmetrize=False, dedup=True, drop_self_loops=True,
+             stream=None):
+        """A graph from a file (edge list, Matrix Market, METIS or serialized);
+        the cleaning flags apply to text formats only."""
+        flags = ((GAP_SYMMETRIZE if symmetrize else 0) | (GAP_DEDUP if dedup else 0)
+                 | (GAP_DROP_SELF_LOOPS if drop_self_loops else 0))
+        return cls(gap_graph_load(path, fmt, flags, stream))
+
+    def save(self, path, stream=None):
+        gap_graph_save(self.handle, path, stream)
+
+    @property
+    def build_flags(self) -> int:
+        return gap_graph_build_flags(self.handle)
 
     def export_csr(self, direction: int = 1):
         import numpy as np
