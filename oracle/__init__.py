@@ -12,6 +12,9 @@ Plain, slow, single-threaded FP64 code (``gap_oracle.c``, built with
   the summed absolute change (correct when below 1e-4).
 * :func:`ppr` — personalized PageRank (not in the paper): teleport (1-d)/|S|
   on a seed set S instead of (1-d)/n.
+* :func:`cc` — §2.1 Connected Components (weak), labelled by each component's
+  smallest vertex id (union-find); :func:`cc_verify` — the §3 CC verifier
+  (one traversal per label).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path.
@@ -71,8 +74,10 @@ def _load():
         lib.oracle_ppr.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, i32, vp, vp]
         lib.oracle_pr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, i64, vp, vp]
         lib.oracle_ppr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, vp, i32, i64, vp, vp]
+        lib.oracle_cc.argtypes = [i64, vp, vp, vp]
+        lib.oracle_cc_verify.argtypes = [i64, vp, vp, vp]
         for f in (lib.oracle_build_csr, lib.oracle_pagerank, lib.oracle_pr_verify, lib.oracle_ppr,
-                  lib.oracle_pr_rows, lib.oracle_ppr_rows):
+                  lib.oracle_pr_rows, lib.oracle_ppr_rows, lib.oracle_cc, lib.oracle_cc_verify):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -209,3 +214,31 @@ def ppr(offsets, idx, seeds, d: float = DAMPING, tol: float = TOL, max_iters: in
     if k < 0:
         raise ValueError(f"oracle_ppr failed ({k})")
     return x, int(k), hist[:k].copy()
+
+
+def cc(offsets, idx):
+    """Weakly connected components of the graph in CSR (either direction):
+    int32 labels, each the smallest vertex id of its component (§2.1)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = len(offsets) - 1
+    labels = np.empty(max(n, 1), np.int32)
+    rc = _load().oracle_cc(n, _ptr(offsets), _ptr(idx), _ptr(labels))
+    if rc != 0:
+        raise ValueError(f"oracle_cc failed ({rc})")
+    return labels[:n]
+
+
+def cc_verify(offsets, idx, labels) -> bool:
+    """The §3 CC verifier: one traversal per label over the undirected graph;
+    True when labels name exactly the weakly connected components."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    n = len(offsets) - 1
+    if len(labels) != n:
+        raise ValueError("labels must have n entries")
+    rc = _load().oracle_cc_verify(n, _ptr(offsets), _ptr(idx), _ptr(labels))
+    if rc < 0:
+        raise ValueError(f"oracle_cc_verify failed ({rc})")
+    return rc == 1

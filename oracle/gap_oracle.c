@@ -16,6 +16,9 @@
  *   - §2.3: duplicate edges and self-loops may be removed, neighbour lists
  *     may be reordered; the graph is held in CSR.
  *   - §3 PageRank verifier: serial, push direction, one extra iteration.
+ *   - §2.1 Connected Components: vertices get the same label exactly when an
+ *     undirected path joins them (weakly connected components of a digraph);
+ *     §3 CC verifier: one traversal per label.
  * Readings where the paper is silent (dangling vertices drop their mass,
  * x0 = 1/n, strict '<', the newest iterate is returned) are listed at each
  * function below.
@@ -300,4 +303,109 @@ int oracle_ppr(int64_t n, const int64_t* off, const int32_t* idx, double d, doub
   }
   free(t); free(bv); free(y); free(c); free(s);
   return k;
+}
+
+/* ------------------------------------------------ connected components --- */
+
+/* Root of x in the union-find forest, halving the path on the way. */
+static int32_t uf_find(int32_t* parent, int32_t x) {
+  while (parent[x] != x) {
+    parent[x] = parent[parent[x]];
+    x = parent[x];
+  }
+  return x;
+}
+
+/*
+ * §2.1 Connected Components: label every vertex by its weakly connected
+ * component (arcs read as undirected edges).  Textbook union-find: every arc
+ * u->v of the CSR unites the sets of u and v; a union makes the smaller root
+ * the parent, so each set's root is its smallest vertex id, and the label of
+ * v is that root.  (The paper asks only for one distinct label per component;
+ * the smallest member id is one such labelling, and it is unique, so a GPU
+ * result can be compared with this one element by element.)
+ * labels: int32[n] (out).  Returns 0, or -2 on allocation failure.
+ */
+int oracle_cc(int64_t n, const int64_t* off, const int32_t* idx, int32_t* labels) {
+  for (int64_t v = 0; v < n; ++v) labels[v] = (int32_t)v;
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t j = off[u]; j < off[u + 1]; ++j) {
+      int32_t ru = uf_find(labels, (int32_t)u), rv = uf_find(labels, idx[j]);
+      if (ru == rv) continue;
+      if (ru < rv) labels[rv] = ru;
+      else labels[ru] = rv;
+    }
+  }
+  for (int64_t v = 0; v < n; ++v) labels[v] = uf_find(labels, (int32_t)v);
+  return 0;
+}
+
+/*
+ * §3 CC verifier: for each distinct label, one breadth-first traversal over
+ * the undirected graph (out- and in-arcs) from a vertex carrying it; the
+ * traversal must meet no other label, and after all traversals every vertex
+ * must have been reached (two components sharing a label leave one of them
+ * unreached).  Any labelling can be checked, not only smallest-id labels.
+ * Returns 1 if `labels` passes, 0 if not, -1 on a label outside [0, n),
+ * -2 on allocation failure.
+ */
+int oracle_cc_verify(int64_t n, const int64_t* off, const int32_t* idx, const int32_t* labels) {
+  for (int64_t v = 0; v < n; ++v)
+    if (labels[v] < 0 || labels[v] >= n) return -1;
+  const int64_t m = off[n];
+  /* reverse arcs: in-direction CSR */
+  int64_t* roff = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int32_t* ridx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* first = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  uint8_t* seen = (uint8_t*)calloc((size_t)n + 1, 1);
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int ok = 1;
+  if (!roff || !ridx || !cur || !first || !seen || !queue) {
+    ok = -2;
+    goto done;
+  }
+  for (int64_t j = 0; j < m; ++j) roff[idx[j] + 1] += 1;
+  for (int64_t v = 0; v < n; ++v) roff[v + 1] += roff[v];
+  for (int64_t v = 0; v < n; ++v) cur[v] = roff[v];
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t j = off[u]; j < off[u + 1]; ++j) ridx[cur[idx[j]]++] = (int32_t)u;
+  /* one start vertex per label: the first vertex carrying it */
+  for (int64_t v = 0; v < n; ++v) first[v] = -1;
+  for (int64_t v = 0; v < n; ++v)
+    if (first[labels[v]] < 0) first[labels[v]] = (int32_t)v;
+  for (int64_t l = 0; l < n && ok == 1; ++l) {
+    if (first[l] < 0) continue;
+    int64_t head = 0, tail = 0;
+    queue[tail++] = first[l];
+    seen[first[l]] = 1;
+    while (head < tail && ok == 1) {
+      const int32_t u = queue[head++];
+      for (int dir = 0; dir < 2 && ok == 1; ++dir) {
+        const int64_t* o = dir ? roff : off;
+        const int32_t* x = dir ? ridx : idx;
+        for (int64_t j = o[u]; j < o[u + 1]; ++j) {
+          const int32_t w = x[j];
+          if (labels[w] != labels[u]) {
+            ok = 0;
+            break;
+          }
+          if (!seen[w]) {
+            seen[w] = 1;
+            queue[tail++] = w;
+          }
+        }
+      }
+    }
+  }
+  for (int64_t v = 0; v < n && ok == 1; ++v)
+    if (!seen[v]) ok = 0;
+done:
+  free(roff);
+  free(ridx);
+  free(cur);
+  free(first);
+  free(seen);
+  free(queue);
+  return ok;
 }

@@ -382,3 +382,134 @@ def test_cpu_pull_baseline_agrees_with_oracle():
     xo, _, _ = oracle.pagerank(off, idx, tol=0.0, max_iters=20)
     assert k == 20 and threads >= 1
     assert np.abs(x - xo).sum() <= 1e-12
+
+
+# ------------------------------------------------- connected components ---
+# §2.1 CC: same label exactly when an undirected path joins two vertices; the
+# oracle labels each component by its smallest vertex id.
+
+def _min_id_labels(n, comp):
+    """Relabel any component numbering by the smallest member id."""
+    mins = np.full(comp.max() + 1 if n else 0, np.iinfo(np.int64).max, np.int64)
+    np.minimum.at(mins, comp, np.arange(n))
+    return mins[comp].astype(np.int32)
+
+
+def _bfs_components(n, arcs):
+    """Brute force: undirected adjacency sets, BFS from every unlabelled vertex
+    in ascending order (so the first vertex reached is the smallest)."""
+    adj = [set() for _ in range(n)]
+    for u, v in arcs:
+        adj[u].add(v)
+        adj[v].add(u)
+    lab = [-1] * n
+    for s in range(n):
+        if lab[s] >= 0:
+            continue
+        lab[s] = s
+        frontier = [s]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for w in adj[u]:
+                    if lab[w] < 0:
+                        lab[w] = s
+                        nxt.append(w)
+            frontier = nxt
+    return np.array(lab, np.int32)
+
+
+def test_cc_closed_forms():
+    n = 9
+    # no arcs: every vertex is its own component (zero-degree vertices get their own label)
+    off, idx = csr_from_arcs(n, [])
+    assert oracle.cc(off, idx).tolist() == list(range(n))
+    # a directed path is one weak component, whichever way it points
+    fwd = [(i, i + 1) for i in range(n - 1)]
+    bwd = [(i + 1, i) for i in range(n - 1)]
+    for arcs in (fwd, bwd):
+        off, idx = csr_from_arcs(n, arcs)
+        assert oracle.cc(off, idx).tolist() == [0] * n
+    # in-star onto the last vertex: arcs only point inwards, still one component
+    off, idx = csr_from_arcs(n, [(i, n - 1) for i in range(n - 1)])
+    assert oracle.cc(off, idx).tolist() == [0] * n
+    # two directed cycles {0,2,4,6,8} and {1,3,5,7} plus a self-loop on 7
+    arcs = [(0, 2), (2, 4), (4, 6), (6, 8), (8, 0), (7, 5), (5, 3), (3, 1), (1, 7), (7, 7)]
+    off, idx = csr_from_arcs(n, arcs)
+    assert oracle.cc(off, idx).tolist() == [0, 1, 0, 1, 0, 1, 0, 1, 0]
+
+
+def test_cc_matches_brute_force_on_every_small_digraph():
+    """All 2^12 digraphs on 4 vertices without self-loops, and random ones
+    on 7 vertices with multi-arcs and self-loops."""
+    pairs = [(u, v) for u in range(4) for v in range(4) if u != v]
+    for mask in range(1 << len(pairs)):
+        arcs = [p for b, p in enumerate(pairs) if mask >> b & 1]
+        off, idx = csr_from_arcs(4, arcs)
+        assert np.array_equal(oracle.cc(off, idx), _bfs_components(4, arcs)), arcs
+    rng = np.random.default_rng(0xCC)
+    for _ in range(300):
+        k = int(rng.integers(0, 12))
+        arcs = [tuple(map(int, rng.integers(0, 7, 2))) for _ in range(k)]
+        off, idx = csr_from_arcs(7, arcs)
+        assert np.array_equal(oracle.cc(off, idx), _bfs_components(7, arcs))
+
+
+@pytest.mark.parametrize("kind", ["urand_sparse", "kron_sym", "grid_deleted"])
+def test_cc_matches_scipy_weak_components(kind):
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    import gapgen
+    if kind == "urand_sparse":  # below the giant-component threshold: many components
+        n = 20000
+        src, dst = gapgen.urand(n, 9000, seed=0xC1)
+        off, idx = oracle.build_csr(n, src, dst)
+    elif kind == "kron_sym":
+        n = 1 << 14
+        src, dst = gapgen.kron(14, 4, seed=0xC2)
+        off, idx = oracle.build_csr(n, src, dst, symmetrize=True)
+    else:
+        src, dst = gapgen.grid(64, 96, 0.45, seed=0xC3)
+        n = 64 * 96
+        off, idx = oracle.build_csr(n, src, dst, symmetrize=True)
+    A = sp.csr_matrix((np.ones(len(idx)), idx, off), shape=(n, n))
+    k, comp = csg.connected_components(A, directed=True, connection="weak")
+    want = _min_id_labels(n, comp)
+    got = oracle.cc(off, idx)
+    assert k > 1
+    assert np.array_equal(got, want)
+    assert len(np.unique(got)) == k
+
+
+def test_cc_verifier_accepts_components_and_rejects_merges_and_splits():
+    import gapgen
+    n = 4000
+    src, dst = gapgen.urand(n, 2500, seed=0xC4)
+    off, idx = oracle.build_csr(n, src, dst)
+    lab = oracle.cc(off, idx)
+    assert oracle.cc_verify(off, idx, lab)
+    # any other member id per component is as good a label
+    uniq = np.unique(lab)
+    other = {}
+    for l in uniq:
+        members = np.flatnonzero(lab == l)
+        other[l] = members[-1]
+    relab = np.array([other[l] for l in lab], np.int32)
+    assert oracle.cc_verify(off, idx, relab)
+    # two components under one label: one of them is never reached
+    sizes = {l: int((lab == l).sum()) for l in uniq}
+    big = [l for l in uniq if sizes[l] > 1]
+    merged = lab.copy()
+    merged[lab == big[1]] = big[0]
+    assert not oracle.cc_verify(off, idx, merged)
+    # one component split in two labels: a traversal meets a different label
+    split = lab.copy()
+    members = np.flatnonzero(lab == big[0])
+    split[members[-1]] = members[-1]
+    assert not oracle.cc_verify(off, idx, split)
+    # isolated vertices under one shared label are also a merge
+    iso = np.flatnonzero((np.diff(off) == 0) & (np.bincount(idx, minlength=n) == 0))
+    assert len(iso) >= 2
+    shared = lab.copy()
+    shared[iso[1]] = iso[0]
+    assert not oracle.cc_verify(off, idx, shared)
