@@ -21,7 +21,9 @@ The same JSON line also carries (rank 0, N = 1, default --workload all):
   "ppr":   personalized-PageRank serving on a Chung-Lu graph (2^24 vertices,
            5e8 arc draws, exponent 2.1): saturated queries/s, Poisson arrivals
            at 0.25/0.5/0.9 of it with p50/p99 latency, and one-at-a-time
-           queries/s.
+           queries/s;
+  "cc":    Connected Components (paper §2.1 CC) trials on the same graph as the
+           main line: trial time, arcs per second and a bandwidth figure.
 --workload batch|ppr prints a line for that workload alone.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -437,6 +439,10 @@ def run_pagerank(a, ws, rank, local, dev, pg):
                         "in-arcs; 'ladder' switches to FP32 contributions once delta <= 2^-10")
         del xb
 
+    cc = None
+    if a.workload == "all":
+        cc = measure_cc(g, dev, stream, max(1, a.steps), max(3, a.warmup), a.graph != "urand")
+
     g.close()
     del scores, host_scores
     if not a.no_fp64:
@@ -457,10 +463,53 @@ def run_pagerank(a, ws, rank, local, dev, pg):
                               "the stats read between trials is outside these events"},
         "roofline": roofline, "fp64": fp64, "bf16": bf16,
     }
+    if cc is not None:
+        line["cc"] = cc
     if not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(a)
     return line
 
+
+
+# Bytes per vertex that one CC trial moves at the least (init 4; two sampling
+# rounds of offsets 8 + sampled index 4 + two label reads 8 + a hook 4; three
+# compress passes of 8; the final pass's offsets 8 + label 4; the count 4);
+# a directed graph's pass over the out-direction adds 12.
+CC_BYTES_PER_VERTEX = 92
+CC_BYTES_PER_VERTEX_OUT_PASS = 12
+
+
+def measure_cc(g, dev, stream, steps, warmup, symmetric):
+    """Connected Components trials on graph g (labels into a device buffer)."""
+    import torch
+
+    from paper_1508_03619_gb300 import gap
+    lab = torch.empty(g.n, dtype=torch.int32, device=dev)
+    for _ in range(max(1, warmup)):  # the first call builds a directed graph's out-direction
+        gap.gap_cc_run(g.handle, lab)
+    gap.gap_cc_stats(g.handle)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        gap.gap_cc_run(g.handle, lab)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    _, st = gap.gap_cc_stats(g.handle)
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    med = sorted(ms)[len(ms) // 2]
+    per_v = CC_BYTES_PER_VERTEX + (0 if symmetric else CC_BYTES_PER_VERTEX_OUT_PASS)
+    peak, kind = measured_hbm_peak()
+    achieved = per_v * g.n / (med / 1e3) / 1e9
+    del lab
+    return {"value": g.m / (med / 1e3) / 1e9, "unit": "Gedges/s (stored arcs / trial time)",
+            "ms_per_trial": {"all": ms, "min": min(ms), "median": med},
+            "components": st["components"], "giant_size": st["giant_size"],
+            "gpu_launches_per_trial": st["kernel_launches"],
+            "bandwidth": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "bytes_per_vertex": per_v,
+                          "peak_source": f"{kind} hbm_gbs",
+                          "note": "bytes a trial moves at the least over its median time; the giant "
+                                  "component's remaining arcs are skipped by the method"}}
 
 
 def batch_tuning():

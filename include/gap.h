@@ -458,6 +458,38 @@ GAP_API gap_status gap_ppr_server_info_ex(gap_ppr_server_t* s, gap_ppr_server_in
 GAP_API void gap_ppr_server_destroy(gap_ppr_server_t* s);
 
 /* ------------------------------------------------- no-allocation variant --- */
+/* -------------------------------------------- connected components --- */
+/* §2.1 Connected Components: every vertex gets the label of its weakly
+ * connected component (arcs read as undirected edges; a vertex without arcs
+ * is a component of its own).  Table 1: a |V|-sized array of 32-bit integers
+ * per trial.  The label of a component is its smallest vertex id, so the
+ * output is unique.  Method: hook-and-compress with neighbour sampling and
+ * the giant component skipped in the final pass (Afforest, a descendant of
+ * the Shiloach-Vishkin algorithm the paper's reference uses); every hook is
+ * a compare-and-swap on a root, all loops are bounded.
+ *
+ * One trial: allocation, all kernels, output.  `labels` int32[n], host or
+ * device (a device buffer is used as the working array), caller-owned.
+ * Stream-ordered and asynchronous like gap_pr_run; gap_cc_stats synchronizes.
+ * A directed graph (one not built with GAP_SYMMETRIZE) also uses its
+ * out-direction CSR, which the first call builds and the handle keeps as part
+ * of the graph (graph construction; time trials after a warm-up call).
+ * Errors: INVALID_ARG (NULL), OOM, CUDA. */
+typedef struct {
+  int64_t components;      /* number of distinct labels */
+  int64_t giant_size;      /* vertices in the component the sampling found most frequent */
+  int32_t giant_label;     /* that component's label */
+  int32_t sample_rounds;   /* neighbour-sampling rounds before the final pass */
+  int32_t kernel_launches; /* kernels the run launched */
+  int32_t device_error;    /* GAP_ERR_TIMEOUT if a bounded loop gave up (labels invalid), else 0 */
+} gap_cc_stats_t;
+
+GAP_API gap_status gap_cc_run(gap_graph_t* g, int32_t* labels, void* stream);
+
+/* Synchronize the last gap_cc_run on g and report it.  Returns its device
+ * error (GAP_ERR_TIMEOUT) if a bounded loop gave up, else GAP_OK. */
+GAP_API gap_status gap_cc_stats(gap_graph_t* g, gap_cc_stats_t* out);
+
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory during the call: code running while a CUDA
  * stream is being captured (cudaMalloc is not allowed there), processes whose

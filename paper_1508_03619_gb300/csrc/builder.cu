@@ -406,6 +406,7 @@ static void graph_free(gap_graph* g) {
   cudaFree(g->out_idx);
   if (g->stats_host) cudaFreeHost(g->stats_host);
   if (g->flag_host) cudaFreeHost(g->flag_host);
+  if (g->cc_host) cudaFreeHost(g->cc_host);
   delete g;
 }
 

@@ -37,6 +37,11 @@ struct gap_graph {
   int32_t last_segments = 1;             // bin plan of the last run
   int64_t last_l2_window = 0;            // bytes the last run marked persisting in L2
   int l2_reset_pending = 0;              // persisting lines to release once that run is done
+  // last connected-components run on this graph
+  void* cc_host = nullptr;  // pinned copy of the run's device control block
+  cudaStream_t cc_stream = nullptr;
+  int cc_has_run = 0;
+  int32_t cc_launches = 0;
   int64_t last_bin_hi[GAP_PR_BINS] = {};
   int32_t last_bin_lanes[GAP_PR_BINS] = {};
   int32_t last_bin_seg[GAP_PR_BINS] = {};

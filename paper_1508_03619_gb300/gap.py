@@ -58,6 +58,7 @@ EXPORTED = (
     "gap_ppr_server_info", "gap_ppr_server_info_ex", "gap_ppr_server_destroy",
     "gap_edge_list_read", "gap_edge_list_info", "gap_edge_list_arrays", "gap_edge_list_destroy",
     "gap_graph_load", "gap_graph_save", "gap_graph_build_flags",
+    "gap_cc_run", "gap_cc_stats",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
@@ -132,6 +133,15 @@ class gap_ppr_server_info_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class gap_cc_stats_t(ctypes.Structure):
+    _fields_ = [("components", ctypes.c_int64), ("giant_size", ctypes.c_int64),
+                ("giant_label", ctypes.c_int32), ("sample_rounds", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("device_error", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GapError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {status_string(status)} ({status}): {msg}")
@@ -194,6 +204,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_graph_load": ([ctypes.c_char_p, i32, u32, vp, ctypes.POINTER(vp)], st),
         "gap_graph_save": ([vp, ctypes.c_char_p, vp], st),
         "gap_graph_build_flags": ([vp, ctypes.POINTER(u32)], st),
+        "gap_cc_run": ([vp, vp, vp], st),
+        "gap_cc_stats": ([vp, ctypes.POINTER(gap_cc_stats_t)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -517,6 +529,29 @@ def gap_pr_stats(h):
     s = _check(load().gap_pr_stats(h, ctypes.byref(st)), "gap_pr_stats",
                ok=(GAP_OK, GAP_WARN_NOT_CONVERGED))
     return s, st.to_dict()
+
+
+# --------------------------------------------------- connected components ---
+
+def gap_cc_run(h, labels, stream=None, n=None):
+    """One CC trial into `labels` (int32, n elements, host or device)."""
+    if labels is not None and not isinstance(labels, int):
+        if n is None:
+            n = gap_graph_info(h)[0]
+        if hasattr(labels, "element_size"):
+            ok = labels.element_size() == 4 and not labels.is_floating_point() and labels.numel() >= n
+        else:
+            ok = labels.itemsize == 4 and labels.dtype.kind == "i" and labels.size >= n
+        if not ok:
+            raise ValueError(f"gap_cc_run: labels must be int32 with at least {n} elements")
+    return _check(load().gap_cc_run(h, _ptr(labels), _stream(stream)), "gap_cc_run")
+
+
+def gap_cc_stats(h):
+    st = gap_cc_stats_t()
+    status = load().gap_cc_stats(h, ctypes.byref(st))
+    _check(status, "gap_cc_stats")
+    return status, st.to_dict()
 
 
 # -------------------------------------------------------- convenience ---
