@@ -12,6 +12,8 @@ Plain, slow, single-threaded FP64 code (``gap_oracle.c``, built with
   the summed absolute change (correct when below 1e-4).
 * :func:`ppr` — personalized PageRank (not in the paper): teleport (1-d)/|S|
   on a seed set S instead of (1-d)/n.
+* :func:`bfs_depths` — §3 serial BFS depths; :func:`bfs_verify` — the §3 BFS
+  verifier of a parent array (§2.1 BFS definition).
 * :func:`cc` — §2.1 Connected Components (weak), labelled by each component's
   smallest vertex id (union-find); :func:`cc_verify` — the §3 CC verifier
   (one traversal per label).
@@ -75,6 +77,10 @@ def _load():
         lib.oracle_pr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, i64, vp, vp]
         lib.oracle_ppr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, vp, i32, i64, vp, vp]
         lib.oracle_cc.argtypes = [i64, vp, vp, vp]
+        lib.oracle_bfs_depths.argtypes = [i64, vp, vp, i32, vp]
+        lib.oracle_bfs_depths.restype = i64
+        lib.oracle_bfs_verify.argtypes = [i64, vp, vp, i32, vp]
+        lib.oracle_bfs_verify.restype = ctypes.c_int
         lib.oracle_cc_verify.argtypes = [i64, vp, vp, vp]
         for f in (lib.oracle_build_csr, lib.oracle_pagerank, lib.oracle_pr_verify, lib.oracle_ppr,
                   lib.oracle_pr_rows, lib.oracle_ppr_rows, lib.oracle_cc, lib.oracle_cc_verify):
@@ -241,4 +247,31 @@ def cc_verify(offsets, idx, labels) -> bool:
     rc = _load().oracle_cc_verify(n, _ptr(offsets), _ptr(idx), _ptr(labels))
     if rc < 0:
         raise ValueError(f"oracle_cc_verify failed ({rc})")
+    return rc == 1
+
+
+def bfs_depths(offsets, idx, source: int):
+    """Depths (int32, -1 unreachable) from `source` over the out-arcs of the CSR."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = len(offsets) - 1
+    depth = np.empty(max(n, 1), np.int32)
+    rc = _load().oracle_bfs_depths(n, _ptr(offsets), _ptr(idx), int(source), _ptr(depth))
+    if rc < 0:
+        raise ValueError(f"oracle_bfs_depths failed ({rc})")
+    return depth[:n]
+
+
+def bfs_verify(offsets, idx, source: int, parent) -> bool:
+    """The §3 BFS verifier: True when `parent` is a valid BFS parent array from
+    `source` (rows of the CSR sorted, as build_csr makes them)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    n = len(offsets) - 1
+    if len(parent) != n:
+        raise ValueError("parent must have n entries")
+    rc = _load().oracle_bfs_verify(n, _ptr(offsets), _ptr(idx), int(source), _ptr(parent))
+    if rc < 0:
+        raise ValueError(f"oracle_bfs_verify failed ({rc})")
     return rc == 1

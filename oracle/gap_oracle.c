@@ -16,6 +16,9 @@
  *   - §2.3: duplicate edges and self-loops may be removed, neighbour lists
  *     may be reordered; the graph is held in CSR.
  *   - §3 PageRank verifier: serial, push direction, one extra iteration.
+ *   - §2.1 Breadth-First Search: a parent array with parent[source] = source,
+ *     -1 for unreachable vertices, an arc parent[v] -> v, and depth[v] =
+ *     depth[parent[v]] + 1; §3 BFS verifier: serial BFS depths.
  *   - §2.1 Connected Components: vertices get the same label exactly when an
  *     undirected path joins them (weakly connected components of a digraph);
  *     §3 CC verifier: one traversal per label.
@@ -407,5 +410,76 @@ done:
   free(first);
   free(seen);
   free(queue);
+  return ok;
+}
+
+/* --------------------------------------------- breadth-first search --- */
+
+/*
+ * Depths from `source` by a plain FIFO breadth-first search over the out-arcs
+ * of the CSR (§3: the BFS verifier's trivial serial BFS).  depth: int32[n]
+ * (out), -1 where unreachable.  Returns the number of reached vertices, or -1
+ * on a bad source, -2 on allocation failure.
+ */
+int64_t oracle_bfs_depths(int64_t n, const int64_t* off, const int32_t* idx, int32_t source, int32_t* depth) {
+  if (source < 0 || source >= n) return -1;
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!queue) return -2;
+  for (int64_t v = 0; v < n; ++v) depth[v] = -1;
+  int64_t head = 0, tail = 0;
+  depth[source] = 0;
+  queue[tail++] = source;
+  while (head < tail) {
+    const int32_t u = queue[head++];
+    for (int64_t j = off[u]; j < off[u + 1]; ++j) {
+      const int32_t v = idx[j];
+      if (depth[v] < 0) {
+        depth[v] = depth[u] + 1;
+        queue[tail++] = v;
+      }
+    }
+  }
+  free(queue);
+  return tail;
+}
+
+/* Is there an arc u -> v?  Rows of the CSR are sorted ascending: binary search. */
+static int has_arc(const int64_t* off, const int32_t* idx, int32_t u, int32_t v) {
+  int64_t lo = off[u], hi = off[u + 1];
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (idx[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < off[u + 1] && idx[lo] == v;
+}
+
+/*
+ * §3 BFS verifier for a parent array (§2.1 BFS definition): parent[source] =
+ * source; parent[v] = -1 exactly where v is unreachable; otherwise the arc
+ * parent[v] -> v exists and depth[parent[v]] = depth[v] - 1, with depths
+ * from oracle_bfs_depths.  The CSR rows must be sorted (as oracle_build_csr
+ * makes them).  Returns 1 if `parent` passes, 0 if not, -1 on a bad source,
+ * -2 on allocation failure.
+ */
+int oracle_bfs_verify(int64_t n, const int64_t* off, const int32_t* idx, int32_t source, const int32_t* parent) {
+  int32_t* depth = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!depth) return -2;
+  const int64_t reached = oracle_bfs_depths(n, off, idx, source, depth);
+  if (reached < 0) {
+    free(depth);
+    return (int)reached;
+  }
+  int ok = parent[source] == source;
+  for (int64_t v = 0; v < n && ok; ++v) {
+    if (v == source) continue;
+    const int32_t p = parent[v];
+    if (depth[v] < 0) {
+      ok = p == -1;
+    } else {
+      ok = p >= 0 && p < n && has_arc(off, idx, p, (int32_t)v) && depth[p] == depth[v] - 1;
+    }
+  }
+  free(depth);
   return ok;
 }

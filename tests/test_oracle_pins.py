@@ -513,3 +513,99 @@ def test_cc_verifier_accepts_components_and_rejects_merges_and_splits():
     shared = lab.copy()
     shared[iso[1]] = iso[0]
     assert not oracle.cc_verify(off, idx, shared)
+
+
+# ------------------------------------------------- breadth-first search ---
+# §2.1 BFS: parent[source] = source, -1 where unreachable, an arc parent -> v,
+# depth[parent] = depth[v] - 1; §3: depths from a serial BFS.
+
+def test_bfs_depth_closed_forms():
+    n = 12
+    off, idx = csr_from_arcs(n, [(i, i + 1) for i in range(n - 1)])  # directed path
+    assert oracle.bfs_depths(off, idx, 0).tolist() == list(range(n))
+    k = 5
+    assert oracle.bfs_depths(off, idx, k).tolist() == [-1] * k + list(range(n - k))
+    off, idx = csr_from_arcs(n, [(0, i) for i in range(1, n)])  # out-star
+    assert oracle.bfs_depths(off, idx, 0).tolist() == [0] + [1] * (n - 1)
+    assert oracle.bfs_depths(off, idx, 3).tolist() == [-1, -1, -1, 0] + [-1] * (n - 4)
+    import gapgen
+    rows, cols = 9, 14  # full lattice: depth = Manhattan distance
+    src, dst = gapgen.grid(rows, cols, 0.0, seed=1)
+    off, idx = oracle.build_csr(rows * cols, src, dst, symmetrize=True)
+    s = 3 * cols + 7
+    d = oracle.bfs_depths(off, idx, s)
+    r, c = np.divmod(np.arange(rows * cols), cols)
+    assert np.array_equal(d, np.abs(r - 3) + np.abs(c - 7))
+
+
+@pytest.mark.parametrize("kind", ["urand_dir", "kron_sym"])
+def test_bfs_depths_match_scipy(kind):
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    import gapgen
+    if kind == "urand_dir":
+        n = 3000
+        s, d = gapgen.urand(n, 4000, seed=0xB1)
+        off, idx = oracle.build_csr(n, s, d)
+    else:
+        n = 1 << 12
+        s, d = gapgen.kron(12, 4, seed=0xB2)
+        off, idx = oracle.build_csr(n, s, d, symmetrize=True)
+    A = sp.csr_matrix((np.ones(len(idx)), idx, off), shape=(n, n))
+    for source in (0, 17, n - 1, int(np.argmax(np.diff(off)))):
+        dist = csg.shortest_path(A, directed=True, unweighted=True, indices=source)
+        want = np.where(np.isinf(dist), -1, dist).astype(np.int32)
+        assert np.array_equal(oracle.bfs_depths(off, idx, source), want)
+
+
+def _parents_from_depths(off, idx, depth, source, pick):
+    """A valid parent array built by hand from the depths: for every reached v,
+    the smallest (pick=min) or largest (pick=max) u with an arc u->v and
+    depth[u] = depth[v] - 1."""
+    n = len(off) - 1
+    cand = [[] for _ in range(n)]
+    for u in range(n):
+        for v in idx[off[u]:off[u + 1]]:
+            if depth[u] >= 0 and depth[v] == depth[u] + 1:
+                cand[v].append(u)
+    par = np.full(n, -1, np.int32)
+    for v in range(n):
+        if cand[v]:
+            par[v] = pick(cand[v])
+    par[source] = source
+    return par
+
+
+def test_bfs_verifier_accepts_every_valid_tree_and_rejects_each_broken_rule():
+    import gapgen
+    n = 2000
+    s, d = gapgen.urand(n, 3000, seed=0xB3)
+    off, idx = oracle.build_csr(n, s, d)
+    source = int(np.argmax(np.diff(off)))
+    depth = oracle.bfs_depths(off, idx, source)
+    lo = _parents_from_depths(off, idx, depth, source, min)
+    hi = _parents_from_depths(off, idx, depth, source, max)
+    assert (lo != hi).any()  # more than one correct answer exists here
+    assert oracle.bfs_verify(off, idx, source, lo) and oracle.bfs_verify(off, idx, source, hi)
+    reached = np.flatnonzero((depth > 1))
+    unreached = np.flatnonzero(depth < 0)
+    assert len(reached) and len(unreached)
+    v = int(reached[0])
+    bad = lo.copy(); bad[source] = -1                        # source is not its own parent
+    assert not oracle.bfs_verify(off, idx, source, bad)
+    bad = lo.copy(); bad[v] = -1                             # a reachable vertex left out
+    assert not oracle.bfs_verify(off, idx, source, bad)
+    bad = lo.copy(); bad[int(unreached[0])] = source         # an unreachable vertex given a parent
+    assert not oracle.bfs_verify(off, idx, source, bad)
+    same = [u for u in range(n) if depth[u] == depth[v] and u != v]
+    bad = lo.copy(); bad[v] = same[0]                        # parent at the same depth (and no arc)
+    assert not oracle.bfs_verify(off, idx, source, bad)
+    # parent one level up but without an arc to v
+    up = [u for u in range(n) if depth[u] == depth[v] - 1 and not np.isin(v, idx[off[u]:off[u + 1]])]
+    bad = lo.copy(); bad[v] = up[0]
+    assert not oracle.bfs_verify(off, idx, source, bad)
+    # an arc into v from a vertex one level deeper: an arc, but the wrong depth
+    deeper = [u for u in range(n) if depth[u] == depth[v] + 1 and np.isin(v, idx[off[u]:off[u + 1]])]
+    if deeper:
+        bad = lo.copy(); bad[v] = deeper[0]
+        assert not oracle.bfs_verify(off, idx, source, bad)
