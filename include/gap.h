@@ -490,6 +490,37 @@ GAP_API gap_status gap_cc_run(gap_graph_t* g, int32_t* labels, void* stream);
  * error (GAP_ERR_TIMEOUT) if a bounded loop gave up, else GAP_OK. */
 GAP_API gap_status gap_cc_stats(gap_graph_t* g, gap_cc_stats_t* out);
 
+/* -------------------------------------------- breadth-first search --- */
+/* §2.1 BFS: from `source`, a parent array with parent[source] = source,
+ * parent[v] = -1 where v is unreachable, and for every reached v an arc
+ * parent[v] -> v with depth[v] = depth[parent[v]] + 1 (any such array is
+ * correct; which parent a vertex gets depends on timing).  Table 1: a
+ * |V|-sized array of 32-bit vertex ids per trial; §2.3: 64 trials from
+ * random sources of non-zero degree.  Method (§3): direction-optimizing BFS
+ * (top-down steps over out-arcs with compare-and-swap claims, bottom-up steps
+ * over in-arcs against a frontier bitmap, switching on the published
+ * ALPHA = 15 / BETA = 18 rule).
+ *
+ * One trial: allocation, all steps, output.  `parent` int32[n], host or device
+ * (a device buffer is the working array), caller-owned.  The host reads two
+ * counters per step to choose the direction, so the call returns when the
+ * search has finished (the final pass may still be in flight on `stream`);
+ * gap_bfs_stats synchronizes.  A directed graph uses its out-direction CSR,
+ * which the first call builds and the handle keeps (graph construction).
+ * Errors: INVALID_ARG (NULL, source outside [0, n)), OOM, CUDA. */
+typedef struct {
+  int64_t reached;         /* vertices with a parent (the source included) */
+  int32_t levels;          /* search steps (depth of the deepest vertex + 1 step that found nothing) */
+  int32_t top_down_steps;
+  int32_t bottom_up_steps;
+  int32_t kernel_launches;
+} gap_bfs_stats_t;
+
+GAP_API gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, void* stream);
+
+/* Synchronize the last gap_bfs_run on g and report it. */
+GAP_API gap_status gap_bfs_stats(gap_graph_t* g, gap_bfs_stats_t* out);
+
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory during the call: code running while a CUDA
  * stream is being captured (cudaMalloc is not allowed there), processes whose

@@ -407,6 +407,7 @@ static void graph_free(gap_graph* g) {
   if (g->stats_host) cudaFreeHost(g->stats_host);
   if (g->flag_host) cudaFreeHost(g->flag_host);
   if (g->cc_host) cudaFreeHost(g->cc_host);
+  if (g->bfs_host) cudaFreeHost(g->bfs_host);
   delete g;
 }
 

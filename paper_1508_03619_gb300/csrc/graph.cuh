@@ -42,6 +42,11 @@ struct gap_graph {
   cudaStream_t cc_stream = nullptr;
   int cc_has_run = 0;
   int32_t cc_launches = 0;
+  // last breadth-first search on this graph
+  void* bfs_host = nullptr;  // pinned copy of the run's device counters
+  cudaStream_t bfs_stream = nullptr;
+  int bfs_has_run = 0;
+  int32_t bfs_launches = 0, bfs_levels = 0, bfs_td_steps = 0, bfs_bu_steps = 0;
   int64_t last_bin_hi[GAP_PR_BINS] = {};
   int32_t last_bin_lanes[GAP_PR_BINS] = {};
   int32_t last_bin_seg[GAP_PR_BINS] = {};

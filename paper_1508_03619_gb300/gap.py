@@ -58,7 +58,7 @@ EXPORTED = (
     "gap_ppr_server_info", "gap_ppr_server_info_ex", "gap_ppr_server_destroy",
     "gap_edge_list_read", "gap_edge_list_info", "gap_edge_list_arrays", "gap_edge_list_destroy",
     "gap_graph_load", "gap_graph_save", "gap_graph_build_flags",
-    "gap_cc_run", "gap_cc_stats",
+    "gap_cc_run", "gap_cc_stats", "gap_bfs_run", "gap_bfs_stats",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
@@ -142,6 +142,15 @@ class gap_cc_stats_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gap_bfs_stats_t(ctypes.Structure):
+    _fields_ = [("reached", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("top_down_steps", ctypes.c_int32), ("bottom_up_steps", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GapError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {status_string(status)} ({status}): {msg}")
@@ -206,6 +215,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_graph_build_flags": ([vp, ctypes.POINTER(u32)], st),
         "gap_cc_run": ([vp, vp, vp], st),
         "gap_cc_stats": ([vp, ctypes.POINTER(gap_cc_stats_t)], st),
+        "gap_bfs_run": ([vp, i32, vp, vp], st),
+        "gap_bfs_stats": ([vp, ctypes.POINTER(gap_bfs_stats_t)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -552,6 +563,50 @@ def gap_cc_stats(h):
     status = load().gap_cc_stats(h, ctypes.byref(st))
     _check(status, "gap_cc_stats")
     return status, st.to_dict()
+
+
+# --------------------------------------------------- breadth-first search ---
+
+def gap_bfs_run(h, source: int, parent, stream=None, n=None):
+    """One BFS trial from `source` into `parent` (int32, n elements, host or device)."""
+    if parent is not None and not isinstance(parent, int):
+        if n is None:
+            n = gap_graph_info(h)[0]
+        if hasattr(parent, "element_size"):
+            ok = parent.element_size() == 4 and not parent.is_floating_point() and parent.numel() >= n
+        else:
+            ok = parent.itemsize == 4 and parent.dtype.kind == "i" and parent.size >= n
+        if not ok:
+            raise ValueError(f"gap_bfs_run: parent must be int32 with at least {n} elements")
+    return _check(load().gap_bfs_run(h, int(source), _ptr(parent), _stream(stream)), "gap_bfs_run")
+
+
+def gap_bfs_stats(h):
+    st = gap_bfs_stats_t()
+    _check(load().gap_bfs_stats(h, ctypes.byref(st)), "gap_bfs_stats")
+    return st.to_dict()
+
+
+def bfs_sources(outdeg, count: int = 64, seed: int = 0x5EED):
+    """`count` source vertices of non-zero out-degree (§2.3), drawn by a
+    splitmix64 sequence from `seed`: deterministic for a graph and seed."""
+    import numpy as np
+    outdeg = np.asarray(outdeg)
+    n = len(outdeg)
+    if not (outdeg > 0).any():
+        raise ValueError("the graph has no vertex with out-arcs")
+    out, i = [], 0
+    mask = (1 << 64) - 1
+    while len(out) < count:
+        z = (seed + (i + 1) * 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z ^= z >> 31
+        v = z % n
+        if outdeg[v] > 0:
+            out.append(int(v))
+        i += 1
+    return out
 
 
 # -------------------------------------------------------- convenience ---

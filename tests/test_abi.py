@@ -43,7 +43,8 @@ def test_struct_layout_matches_c(tmp_path):
               ("gap_batch_tuning", gap.gap_batch_tuning),
               ("gap_ppr_query_info_t", gap.gap_ppr_query_info_t),
               ("gap_ppr_server_info_t", gap.gap_ppr_server_info_t),
-              ("gap_cc_stats_t", gap.gap_cc_stats_t)]
+              ("gap_cc_stats_t", gap.gap_cc_stats_t),
+              ("gap_bfs_stats_t", gap.gap_bfs_stats_t)]
     lines, want = [], []
     for cname, py in fields:
         lines.append(f'printf("%zu\\n", sizeof({cname}));')
