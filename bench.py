@@ -23,11 +23,14 @@ The same JSON line also carries (rank 0, N = 1, default --workload all):
            at 0.25/0.5/0.9 of it with p50/p99 latency, and one-at-a-time
            queries/s;
   "cc":    Connected Components (paper §2.1 CC) trials on the same graph as the
-           main line: trial time, arcs per second and a bandwidth figure.
---workload batch|ppr prints a line for that workload alone.
+           main line: trial time, arcs per second and a bandwidth figure;
+  "bfs":   direction-optimizing BFS (paper §2.1 BFS) from 64 sources of
+           non-zero degree on the same graph (§2.3): trial times and arcs per
+           second.
+--workload batch|ppr|cc|bfs prints a line for that workload alone.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--workload all|pagerank|batch|ppr]
+                       [--workload all|pagerank|batch|ppr|cc|bfs]
 """
 import argparse
 import json
@@ -74,7 +77,7 @@ def parse():
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="convergence loop driver (host: one launch per kernel, visible to ncu)")
     ap.add_argument("--segment-bytes", type=int, default=0, help="L2 blocking segment size (0 = default)")
-    ap.add_argument("--workload", default="all", choices=["all", "pagerank", "batch", "ppr"],
+    ap.add_argument("--workload", default="all", choices=["all", "pagerank", "batch", "ppr", "cc", "bfs"],
                     help="all: the PageRank line with batch and ppr entries")
     ap.add_argument("--ppr-seconds", type=float, default=6.0, help="arrival window per load level")
     ap.add_argument("--ppr-scale", type=int, default=24)
@@ -439,9 +442,10 @@ def run_pagerank(a, ws, rank, local, dev, pg):
                         "in-arcs; 'ladder' switches to FP32 contributions once delta <= 2^-10")
         del xb
 
-    cc = None
+    cc = bfs = None
     if a.workload == "all":
         cc = measure_cc(g, dev, stream, max(1, a.steps), max(3, a.warmup), a.graph != "urand")
+        bfs = measure_bfs(g, dev, stream, gap.bfs_sources(g.export_outdeg(), 64), max(3, a.warmup))
 
     g.close()
     del scores, host_scores
@@ -465,6 +469,8 @@ def run_pagerank(a, ws, rank, local, dev, pg):
     }
     if cc is not None:
         line["cc"] = cc
+    if bfs is not None:
+        line["bfs"] = bfs
     if not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(a)
     return line
@@ -510,6 +516,41 @@ def measure_cc(g, dev, stream, steps, warmup, symmetric):
                           "peak_source": f"{kind} hbm_gbs",
                           "note": "bytes a trial moves at the least over its median time; the giant "
                                   "component's remaining arcs are skipped by the method"}}
+
+
+def measure_bfs(g, dev, stream, sources, warmup):
+    """BFS trials on graph g, one per source (parents into a device buffer)."""
+    import torch
+
+    from paper_1508_03619_gb300 import gap
+    par = torch.empty(g.n, dtype=torch.int32, device=dev)
+    for s in sources[:max(1, warmup)]:  # the first call builds a directed graph's out-direction
+        gap.gap_bfs_run(g.handle, s, par)
+    gap.gap_bfs_stats(g.handle)
+    ms, reached, levels, td, bu, launches = [], [], [], [], [], 0
+    for s in sources:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gap.gap_bfs_run(g.handle, s, par)
+        e1.record(stream)
+        st = gap.gap_bfs_stats(g.handle)  # synchronizes; outside the events
+        ms.append(e0.elapsed_time(e1))
+        reached.append(st["reached"])
+        levels.append(st["levels"])
+        td.append(st["top_down_steps"])
+        bu.append(st["bottom_up_steps"])
+        launches += st["kernel_launches"]
+    del par
+    med = sorted(ms)[len(ms) // 2]
+    return {"value": g.m / (med / 1e3) / 1e9, "unit": "Gedges/s (stored arcs / median trial time)",
+            "trials": len(sources), "sources": "splitmix64 draws of vertices with out-arcs, seed 0x5EED",
+            "ms_per_trial": {"all": ms, "min": min(ms), "median": med},
+            "reached": {"min": min(reached), "max": max(reached)},
+            "levels": {"min": min(levels), "max": max(levels)},
+            "steps": {"top_down_mean": sum(td) / len(td), "bottom_up_mean": sum(bu) / len(bu)},
+            "gpu_launches_per_trial": launches / len(sources),
+            "note": "each trial ends when the host has seen the last step's counters; the host reads "
+                    "two counters per step to choose the direction"}
 
 
 def batch_tuning():
@@ -740,6 +781,31 @@ def main():
                     "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                     "data": "synthetic", "config": {"workload": b.pop("workload")},
                     "roofline": b.pop("roofline"), "batch": b}
+        elif a.workload in ("cc", "bfs"):
+            import gapgen
+            from paper_1508_03619_gb300 import gap
+            if a.graph == "urand":
+                src, dst = gapgen.urand_device(1 << a.scale, a.edge_factor << a.scale, a.seed, device=dev)
+            else:
+                src, dst = gapgen.kron_device(a.scale, a.edge_factor, a.seed, device=dev)
+            g = gap.Graph.from_edges(1 << a.scale, src, dst, symmetrize=a.graph != "urand")
+            del src, dst
+            torch.cuda.empty_cache()
+            stream = torch.cuda.current_stream(dev)
+            if a.workload == "cc":
+                r = measure_cc(g, dev, stream, max(1, a.steps), max(1, a.warmup), a.graph != "urand")
+            else:
+                r = measure_bfs(g, dev, stream, gap.bfs_sources(g.export_outdeg(), max(1, a.steps)),
+                                max(1, a.warmup))
+            cfg = workload_config(a)
+            g.close()
+            line = {"metric": METRIC, "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": 1,
+                    "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                    "config": {**cfg, "workload": cfg["workload"].split(" pull")[0]
+                               + (" connected components" if a.workload == "cc"
+                                  else f" BFS from {max(1, a.steps)} sources"), "kernel": a.workload},
+                    a.workload: r}
         else:
             p = measure_ppr(a, dev)
             line = {"metric": METRIC, "value": p["saturated_qps"], "unit": "queries/s", "n_gpus": 1,
