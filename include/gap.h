@@ -521,6 +521,18 @@ GAP_API gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, 
 /* Synchronize the last gap_bfs_run on g and report it. */
 GAP_API gap_status gap_bfs_stats(gap_graph_t* g, gap_bfs_stats_t* out);
 
+/* -------------------------------------------- failure-detection self-test --- */
+/* The paper has no counterpart.  Exercises the bounded wait of the grid
+ * barrier that the batch kernel uses (every barrier wait there gives up after
+ * 2 s and reports GAP_ERR_TIMEOUT instead of hanging): two resident blocks of a
+ * cooperative launch meet at a barrier that counts one block more than was
+ * launched, so the wait runs out after 50 ms by design.  *observed receives
+ * the status the kernel reported (GAP_ERR_TIMEOUT when the detection works,
+ * GAP_OK if the barrier wrongly completed); *waited_ms the kernel's duration.
+ * No fault is raised and the context stays usable.  Synchronous.
+ * Returns GAP_OK when the self-test ran; INVALID_ARG (NULL), OOM, CUDA. */
+GAP_API gap_status gap_selftest_barrier_timeout(int32_t* observed, double* waited_ms, void* stream);
+
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory during the call: code running while a CUDA
  * stream is being captured (cudaMalloc is not allowed there), processes whose

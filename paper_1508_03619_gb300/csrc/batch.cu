@@ -86,8 +86,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid barrier (generation counter) with a bounded wait.  Returns false when
-// the wait gave up or another block reported an error.
+// Grid barrier (generation counter) with a bounded wait of WAIT_NS.  Returns
+// false when the wait gave up or another block reported an error.
+template <unsigned long long WAIT_NS = BARRIER_WAIT_NS>
 __device__ bool grid_barrier(BatchCtrl* ctrl, unsigned int nblocks) {
   __shared__ int ok;
   __syncthreads();
@@ -106,7 +107,7 @@ __device__ bool grid_barrier(BatchCtrl* ctrl, unsigned int nblocks) {
       const unsigned long long t0 = global_ns();
       while (*gen == my_gen) {
         if (*err) { ok = 0; break; }
-        if (global_ns() - t0 > BARRIER_WAIT_NS) {
+        if (global_ns() - t0 > WAIT_NS) {
           atomicExch(&ctrl->error, GAP_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -420,6 +421,7 @@ extern "C" void gap_batch_tuning_default(gap_batch_tuning* t) {
 extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t count, double damping, double tol,
                                           int32_t max_iters, const gap_batch_tuning* tuning, float* const* scores,
                                           gap_pr_stats_t* stats, void* stream) {
+  NvtxRange nv_call("gap_pr_run_batch");
   clear_error();
   gap_batch_tuning tu;
   gap_batch_tuning_default(&tu);
@@ -641,4 +643,66 @@ extern "C" gap_status gap_pr_run_batch(gap_graph_t* const* graphs, int32_t count
                                        int32_t max_iters, float* const* scores, gap_pr_stats_t* stats,
                                        void* stream) {
   return gap_pr_run_batch_ex(graphs, count, damping, tol, max_iters, nullptr, scores, stats, stream);
+}
+
+// ---- failure-detection self-test of the grid barrier ------------------------
+// `blocks` resident blocks meet at a barrier that counts one block more than
+// was launched, so no generation ever completes: every wait runs out after
+// SELFTEST_WAIT_NS, the first block to give up records GAP_ERR_TIMEOUT and the
+// others leave on seeing it.  Nothing faults and nothing waits unbounded; the
+// same barrier code serves the batch kernel with its 2 s bound.
+namespace {
+constexpr unsigned long long SELFTEST_WAIT_NS = 50000000ull;  // 50 ms
+
+__global__ void k_barrier_timeout_selftest(BatchCtrl* ctrl, unsigned int expected, int32_t* passed) {
+  const bool ok = grid_barrier<SELFTEST_WAIT_NS>(ctrl, expected);
+  if (threadIdx.x == 0 && ok) atomicAdd(passed, 1);
+}
+}  // namespace
+
+extern "C" gap_status gap_selftest_barrier_timeout(int32_t* observed, double* waited_ms, void* stream) {
+  clear_error();
+  if (!observed || !waited_ms) {
+    set_error("gap_selftest_barrier_timeout: NULL argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch ctl;
+  GAP_TRY(ctl.get(sizeof(BatchCtrl) + 64, s));
+  BatchCtrl* ctrl = ctl.as<BatchCtrl>();
+  int32_t* passed = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ctl.p) + sizeof(BatchCtrl) + 32);
+  GAP_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(BatchCtrl) + 64, s));
+  const unsigned int blocks = 2;
+  unsigned int expected = blocks + 1;
+  cudaEvent_t e0, e1;
+  GAP_CUDA(cudaEventCreate(&e0));
+  GAP_CUDA(cudaEventCreate(&e1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {&ctrl, &expected, &passed};
+  gap_status st = GAP_OK;
+  cudaError_t e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = cudaLaunchKernelExC(&cfg, (const void*)k_barrier_timeout_selftest, args);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  BatchCtrl hc;
+  int32_t hp = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hp, passed, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e != cudaSuccess) st = cuda_fail(e, "barrier self-test", __FILE__, __LINE__);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != GAP_OK) return st;
+  *observed = hp ? GAP_OK : hc.error;
+  *waited_ms = ms;
+  return GAP_OK;
 }

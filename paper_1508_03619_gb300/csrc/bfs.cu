@@ -228,6 +228,7 @@ using namespace gap;
 extern "C" {
 
 gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, void* stream) {
+  NvtxRange nv_call("gap_bfs_run");
   clear_error();
   if (!g || !parent) {
     set_error("gap_bfs_run: NULL argument");
@@ -292,6 +293,7 @@ gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, void* st
   while (nf > 0) {
     if (scout > edges_to_check / BFS_ALPHA) {
       // turn bottom-up
+      NvtxRange nv_bu("bfs_bottom_up_phase");
       GAP_CUDA(cudaMemsetAsync(fa, 0, sizeof(uint32_t) * words, s));
       k_bfs_q2bm<<<stride_grid(nf, BFS_THREADS, 8), BFS_THREADS, 0, s>>>(qa, nf, fa);
       GAP_LAUNCH_CHECK();
@@ -320,6 +322,7 @@ gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, void* st
       scout = 1;  // the published heuristic: continue top-down after a bottom-up phase
     } else {
       // top-down step from qa (degrees da)
+      NvtxRange nv_td("bfs_top_down_step");
       edges_to_check -= scout;
       int64_t total = 0;
       GAP_TRY(exclusive_scan_u32(da, qoff_s.as<int64_t>(), nf, tmp_s.as<int64_t>(), nullptr, s));

@@ -414,6 +414,7 @@ static void graph_free(gap_graph* g) {
 // Build from device draws.  Arcs are keyed (head=dst, tail=src) for the CSC.
 static gap_status build_from_device_edges(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst,
                                           uint32_t flags, cudaStream_t s, gap_graph** out) {
+  NvtxRange nv_call("gap_graph_build");
   const int symmetrize = (flags & GAP_SYMMETRIZE) ? 1 : 0;
   const int dedup = (flags & GAP_DEDUP) ? 1 : 0;
   const int drop = (flags & GAP_DROP_SELF_LOOPS) ? 1 : 0;

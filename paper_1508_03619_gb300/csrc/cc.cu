@@ -211,6 +211,7 @@ using namespace gap;
 extern "C" {
 
 gap_status gap_cc_run(gap_graph_t* g, int32_t* labels, void* stream) {
+  NvtxRange nv_call("gap_cc_run");
   clear_error();
   if (!g || !labels) {
     set_error("gap_cc_run: NULL argument");

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -36,6 +37,23 @@ gap_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
     gap_status s_ = (expr);        \
     if (s_ != GAP_OK) return s_;   \
   } while (0)
+
+// ---- NVTX ranges --------------------------------------------------------------
+// Named host-side ranges around each entry point and trial phase, so a
+// profiler (ncu --nvtx, Nsight Systems) can select the kernels a phase
+// launched.  Header-only NVTX3: without an attached tool each push/pop is a
+// call through an empty function table.
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  void next(const char* name) {  // close this range and open the next phase's
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- scratch allocation ---------------------------------------------------
 void* scratch_alloc(size_t bytes, cudaStream_t s);

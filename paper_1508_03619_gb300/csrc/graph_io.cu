@@ -620,6 +620,7 @@ gap_status gap_edge_list_arrays(const gap_edge_list_t* e, const int32_t** src, c
 void gap_edge_list_destroy(gap_edge_list_t* e) { delete e; }
 
 gap_status gap_graph_load(const char* path, int32_t format, uint32_t flags, void* stream, gap_graph_t** out) {
+  NvtxRange nv_call("gap_graph_load");
   clear_error();
   if (!path || !out) {
     set_error("path or out is NULL");
@@ -651,6 +652,7 @@ gap_status gap_graph_load(const char* path, int32_t format, uint32_t flags, void
 }
 
 gap_status gap_graph_save(gap_graph_t* g, const char* path, void* stream) {
+  NvtxRange nv_call("gap_graph_save");
   clear_error();
   if (!g || !path) {
     set_error("graph or path is NULL");

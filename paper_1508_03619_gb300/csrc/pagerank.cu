@@ -1359,6 +1359,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   GAP_LAUNCH_CHECK();
   PhaseTimer tm;
   tm.init(o.timing != 0, s);
+  NvtxRange nv("pr_bin");
 
   // ---- degree binning (+ segment split points) ----
   int tok = tm.begin();
@@ -1377,6 +1378,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   tm.end(GAP_PHASE_BIN, tok);
   GAP_CUDA(cudaStreamSynchronize(s));
   tm.collect();
+  nv.next("pr_prep");
   tok = tm.begin();
   const int64_t nhubs = mt[NBINS] - mt[BIN_HUB];
   int64_t nchunks = mt[NBINS + 1];
@@ -1537,6 +1539,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   GAP_TRY(csum.get(sizeof(double) * (nchunks > 0 ? nchunks : 1), s));
 
   // ---- x0, c0 ----
+  nv.next("pr_init");
   const Acc x0 = (Acc)(1.0 / (double)n);
   tok = tm.begin();
   k_init<Acc><<<stride_grid(n, 256, 8), 256, 0, s>>>(n, x0, x, g->outdeg, c0, bf16 ? 1 : 0);
@@ -1624,8 +1627,10 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   cudaAccessPolicyWindow win;
   const size_t win_bytes = (o.l2_window && S == 1) ? l2_window_setup(cbuf.p, 2 * (bf16 ? xbytes / 2 : xbytes), &win)
                                                    : 0;
+  nv.next("pr_iterations");
   GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing != 0,
                      win_bytes ? &win : nullptr));
+  nv.next("pr_output");
 
   // ---- output + stats ----
   tok = tm.begin();
@@ -2043,6 +2048,7 @@ void gap_pr_options_default(gap_pr_options* o) {
 
 gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters, const gap_pr_options* opt,
                          void* scores, void* stream) {
+  NvtxRange nv_call("gap_pr_run");
   GAP_TRY(check_run_args(g, damping, tol, max_iters, scores));
   gap_pr_options o;
   gap_pr_options_default(&o);

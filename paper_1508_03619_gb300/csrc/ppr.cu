@@ -447,6 +447,7 @@ gap_status ppr_engine_set_column(PprEngine* e, int col, const int32_t* d_seeds, 
 // One iteration over all KP columns (frozen columns only refresh c').
 gap_status ppr_engine_step(PprEngine* e, double tol, int32_t max_iters, cudaStream_t s,
                            cudaGraphConditionalHandle h, int use_h) {
+  NvtxRange nv_call("ppr_engine_step");
   PprArgs a;
   a.off = e->g->in_off;
   a.idx = e->g->in_idx;
@@ -539,6 +540,7 @@ using namespace gap;
 extern "C" gap_status gap_ppr_batch(gap_graph_t* g, int32_t q, const int64_t* seed_offsets, const int32_t* seeds,
                                     double damping, double tol, int32_t max_iters, float* scores,
                                     gap_pr_stats_t* stats, void* stream) {
+  NvtxRange nv_call("gap_ppr_batch");
   clear_error();
   if (!g || q < 0 || (q > 0 && (!seed_offsets || !scores))) {
     set_error("gap_ppr_batch: bad argument");

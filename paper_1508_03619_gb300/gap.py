@@ -58,7 +58,7 @@ EXPORTED = (
     "gap_ppr_server_info", "gap_ppr_server_info_ex", "gap_ppr_server_destroy",
     "gap_edge_list_read", "gap_edge_list_info", "gap_edge_list_arrays", "gap_edge_list_destroy",
     "gap_graph_load", "gap_graph_save", "gap_graph_build_flags",
-    "gap_cc_run", "gap_cc_stats", "gap_bfs_run", "gap_bfs_stats",
+    "gap_cc_run", "gap_cc_stats", "gap_bfs_run", "gap_bfs_stats", "gap_selftest_barrier_timeout",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
@@ -217,6 +217,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_cc_stats": ([vp, ctypes.POINTER(gap_cc_stats_t)], st),
         "gap_bfs_run": ([vp, i32, vp, vp], st),
         "gap_bfs_stats": ([vp, ctypes.POINTER(gap_bfs_stats_t)], st),
+        "gap_selftest_barrier_timeout": ([ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -607,6 +608,32 @@ def bfs_sources(outdeg, count: int = 64, seed: int = 0x5EED):
             out.append(int(v))
         i += 1
     return out
+
+
+# ------------------------------------------------------- failure detection ---
+
+def gap_selftest_barrier_timeout(stream=None):
+    """Run the grid barrier's bounded-wait self-test; returns (observed status,
+    waited ms).  The status is GAP_ERR_TIMEOUT when detection works."""
+    obs, ms = ctypes.c_int32(), ctypes.c_double()
+    _check(load().gap_selftest_barrier_timeout(ctypes.byref(obs), ctypes.byref(ms), _stream(stream)),
+           "gap_selftest_barrier_timeout")
+    return obs.value, ms.value
+
+
+class gap_allocator(ctypes.Structure):
+    """The C gap_allocator: alloc(bytes, stream, ctx) / free(ptr, bytes, stream, ctx)."""
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    _fields_ = [("alloc", ALLOC), ("free", FREE), ("ctx", ctypes.c_void_p)]
+
+
+def gap_set_allocator(allocator):
+    """Install a gap_allocator (keep the object and its callbacks alive while
+    it is installed), or None for the default stream-ordered pool."""
+    lib = load()
+    return _check(lib.gap_set_allocator(None if allocator is None else ctypes.byref(allocator)),
+                  "gap_set_allocator")
 
 
 # -------------------------------------------------------- convenience ---

@@ -1,0 +1,138 @@
+"""Failure detection without a GPU fault.
+
+Faults are injected on the host: an allocator callback that runs out after a
+few blocks (every entry point must return GAP_ERR_OOM, free what it took and
+leave the library usable), and one that returns blocks off the 256-byte
+alignment the kernels need (GAP_ERR_INVALID_ARG, no kernel runs on them).
+On the device, the grid barrier's bounded wait is made to run out by design
+(a barrier that counts one block more than was launched): it must report
+GAP_ERR_TIMEOUT within its bound, and the context must stay usable."""
+import numpy as np
+import pytest
+
+import gapgen
+import oracle
+from gpu_helpers import D, assert_fp32_parity, gpu_graph
+from paper_1508_03619_gb300 import gap
+
+pytestmark = pytest.mark.gpu
+
+
+class TorchAllocator:
+    """Scratch blocks from torch's caching allocator (on the current stream,
+    which the library calls share), with fault injection: fail after
+    `budget` blocks, or hand out blocks `shift` bytes past the aligned start."""
+
+    def __init__(self, budget=None, shift=0):
+        import torch
+        self.torch = torch
+        self.budget = budget
+        self.shift = shift
+        self.live = {}
+        self.allocs = self.frees = self.refused = 0
+        self._a = gap.gap_allocator.ALLOC(self._alloc)
+        self._f = gap.gap_allocator.FREE(self._free)
+        self.c = gap.gap_allocator(self._a, self._f, None)
+
+    def _alloc(self, nbytes, stream, ctx):
+        if self.budget is not None and self.allocs >= self.budget:
+            self.refused += 1
+            return None
+        t = self.torch.empty(nbytes + self.shift + 256, dtype=self.torch.uint8, device="cuda")
+        p = t.data_ptr() + self.shift
+        self.live[p] = t
+        self.allocs += 1
+        return p
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        self.live.pop(ptr)
+        self.frees += 1
+
+    def __enter__(self):
+        gap.gap_set_allocator(self.c)
+        return self
+
+    def __exit__(self, *exc):
+        gap.gap_set_allocator(None)
+
+
+def _graph():
+    n = 1 << 12
+    s, d = gapgen.kron(12, 8, seed=0xF1)
+    return n, s, d
+
+
+def test_custom_allocator_runs_every_entry_point(cuda_device):
+    import torch
+    n, s, d = _graph()
+    off, idx = oracle.build_csr(n, s, d, symmetrize=True)
+    with gpu_graph(n, s, d, symmetrize=True) as g:
+        with TorchAllocator() as al:
+            x = torch.empty(n, dtype=torch.float32, device="cuda")
+            gap.gap_pr_run(g.handle, D, 0.0, 20, x)
+            gap.gap_pr_stats(g.handle)
+            lab = torch.empty(n, dtype=torch.int32, device="cuda")
+            gap.gap_cc_run(g.handle, lab)
+            gap.gap_cc_stats(g.handle)
+            par = torch.empty(n, dtype=torch.int32, device="cuda")
+            gap.gap_bfs_run(g.handle, 3, par)
+            gap.gap_bfs_stats(g.handle)
+            torch.cuda.synchronize()
+        assert al.allocs > 5 and al.allocs == al.frees and not al.live
+        xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 20)
+        assert_fp32_parity(x.cpu().numpy().astype(np.float64), xo)
+        assert np.array_equal(lab.cpu().numpy(), oracle.cc(off, idx))
+        assert oracle.bfs_verify(off, idx, 3, par.cpu().numpy())
+
+
+@pytest.mark.parametrize("budget", [0, 1, 3])
+def test_allocator_running_out_gives_oom_and_frees_what_it_took(cuda_device, budget):
+    import torch
+    n, s, d = _graph()
+    with gpu_graph(n, s, d, symmetrize=True) as g:
+        runs = [
+            lambda: gap.gap_pr_run(g.handle, D, 1e-4, 100, torch.empty(n, dtype=torch.float32, device="cuda")),
+            lambda: gap.gap_cc_run(g.handle, np.empty(n, np.int32)),  # host labels need device scratch
+            lambda: gap.gap_bfs_run(g.handle, 0, torch.empty(n, dtype=torch.int32, device="cuda")),
+        ]
+        for run in runs:
+            with TorchAllocator(budget=budget) as al:
+                with pytest.raises(gap.GapError) as ei:
+                    run()
+                torch.cuda.synchronize()
+            assert ei.value.status == gap.GAP_ERR_OOM, ei.value
+            assert al.refused >= 1 and al.allocs == al.frees and not al.live
+        # the default allocator is back and the library works
+        x = torch.empty(n, dtype=torch.float32, device="cuda")
+        assert gap.gap_pr_run(g.handle, D, 1e-4, 100, x) == gap.GAP_OK
+        status, st = gap.gap_pr_stats(g.handle)
+        assert status == gap.GAP_OK and st["converged"]
+
+
+def test_misaligned_allocator_is_refused(cuda_device):
+    import torch
+    n, s, d = _graph()
+    with gpu_graph(n, s, d, symmetrize=True) as g:
+        with TorchAllocator(shift=16) as al:
+            with pytest.raises(gap.GapError) as ei:
+                gap.gap_pr_run(g.handle, D, 1e-4, 100, torch.empty(n, dtype=torch.float32, device="cuda"))
+            torch.cuda.synchronize()
+        assert ei.value.status == gap.GAP_ERR_INVALID_ARG and "256" in str(ei.value)
+        assert al.allocs == al.frees and not al.live
+
+
+def test_grid_barrier_wait_runs_out_and_reports_timeout(cuda_device):
+    import torch
+    for _ in range(2):
+        observed, ms = gap.gap_selftest_barrier_timeout()
+        assert observed == gap.GAP_ERR_TIMEOUT
+        assert 45.0 <= ms < 2000.0  # gave up after its 50 ms bound, not at the 2 s production bound
+    # the context is intact: a batch (the kernel that uses this barrier) still runs
+    n, s, d = _graph()
+    off, idx = oracle.build_csr(n, s, d, symmetrize=True)
+    with gpu_graph(n, s, d, symmetrize=True) as g:
+        x = [torch.empty(n, dtype=torch.float32, device="cuda")]
+        st = gap.gap_pr_run_batch([g.handle], x, D, 0.0, 20)
+        xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 20)
+        assert st[0]["iterations"] == 20
+        assert_fp32_parity(x[0].cpu().numpy().astype(np.float64), xo)
