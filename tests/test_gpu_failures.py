@@ -85,23 +85,25 @@ def test_custom_allocator_runs_every_entry_point(cuda_device):
         assert oracle.bfs_verify(off, idx, 3, par.cpu().numpy())
 
 
-@pytest.mark.parametrize("budget", [0, 1, 3])
-def test_allocator_running_out_gives_oom_and_frees_what_it_took(cuda_device, budget):
+@pytest.mark.parametrize("which,budget", [("pr", 0), ("pr", 1), ("pr", 3), ("pr", 8),
+                                          ("cc", 0), ("cc", 1), ("bfs", 0), ("bfs", 3), ("bfs", 8)])
+def test_allocator_running_out_gives_oom_and_frees_what_it_took(cuda_device, which, budget):
+    """Each budget is below the blocks that entry point takes (a PageRank trial
+    about 20, CC with host labels 2, BFS 9), so the run fails part-way."""
     import torch
     n, s, d = _graph()
     with gpu_graph(n, s, d, symmetrize=True) as g:
-        runs = [
-            lambda: gap.gap_pr_run(g.handle, D, 1e-4, 100, torch.empty(n, dtype=torch.float32, device="cuda")),
-            lambda: gap.gap_cc_run(g.handle, np.empty(n, np.int32)),  # host labels need device scratch
-            lambda: gap.gap_bfs_run(g.handle, 0, torch.empty(n, dtype=torch.int32, device="cuda")),
-        ]
-        for run in runs:
-            with TorchAllocator(budget=budget) as al:
-                with pytest.raises(gap.GapError) as ei:
-                    run()
-                torch.cuda.synchronize()
-            assert ei.value.status == gap.GAP_ERR_OOM, ei.value
-            assert al.refused >= 1 and al.allocs == al.frees and not al.live
+        run = {
+            "pr": lambda: gap.gap_pr_run(g.handle, D, 1e-4, 100, torch.empty(n, dtype=torch.float32, device="cuda")),
+            "cc": lambda: gap.gap_cc_run(g.handle, np.empty(n, np.int32)),  # host labels need device scratch
+            "bfs": lambda: gap.gap_bfs_run(g.handle, 0, torch.empty(n, dtype=torch.int32, device="cuda")),
+        }[which]
+        with TorchAllocator(budget=budget) as al:
+            with pytest.raises(gap.GapError) as ei:
+                run()
+            torch.cuda.synchronize()
+        assert ei.value.status == gap.GAP_ERR_OOM, ei.value
+        assert al.refused >= 1 and al.allocs == al.frees and not al.live
         # the default allocator is back and the library works
         x = torch.empty(n, dtype=torch.float32, device="cuda")
         assert gap.gap_pr_run(g.handle, D, 1e-4, 100, x) == gap.GAP_OK
