@@ -3,7 +3,8 @@
 The fixture fingerprints the oracle's FP64 PageRank on the 4,096-vertex
 uniform-random digraph (65,536 draws, seed 0x1, self-loops and duplicates
 removed): the tolerance-mode run (d = 0.85, tol = 1e-4) and a 20-iteration
-fixed run.  It is regenerated only by this script, which calls nothing but
+fixed run, the §2.1 connected-components labels (smallest member id per weak
+component) and the §3 serial BFS depths from vertex 0.  It is regenerated only by this script, which calls nothing but
 ``oracle`` and the input generator; the test that reads it checks that the
 oracle (and the generator) give the same bits on every machine.
 """
@@ -30,6 +31,12 @@ def fingerprint():
         out[name] = {"iterations": k, "deltas": [float(d).hex() for d in deltas],
                      "x_sha256": hashlib.sha256(x.tobytes()).hexdigest(),
                      "sum_x": float(x.sum()).hex()}
+    lab = oracle.cc(off, idx)
+    out["cc"] = {"components": int(len(set(lab.tolist()))),
+                 "labels_sha256": hashlib.sha256(lab.tobytes()).hexdigest()}
+    depth = oracle.bfs_depths(off, idx, 0)
+    out["bfs_from_0"] = {"reached": int((depth >= 0).sum()), "max_depth": int(depth.max()),
+                         "depths_sha256": hashlib.sha256(depth.tobytes()).hexdigest()}
     return out
 
 
