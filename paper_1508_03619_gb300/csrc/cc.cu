@@ -6,12 +6,22 @@
 // hook-and-compress family in the form that skips most arcs (Afforest,
 // Sutton, Ben-Nun & Barak, IPDPS 2018):
 //   1. comp[v] = v.
-//   2. Two sampling rounds: every vertex links with its r-th in-neighbour,
-//      then every vertex jumps to its root (compress).
+//   2. Two sampling rounds, each followed by a compress (every vertex jumps to
+//      its root): in round 0 every vertex links with its first in-neighbour;
+//      in round 1 one vertex in eight (picked by a multiplicative hash of its
+//      id) links with its second.  After round 0 the graph is a few large
+//      trees, and a link across two of them reads and hooks the same root as
+//      every other such link, so a full second round spends most of its time
+//      queued on a handful of addresses; an eighth of the links still merges
+//      the large trees, and what it leaves is picked up in step 4.
 //   3. The most frequent root among 1024 fixed sample positions names the
 //      giant component.
-//   4. Vertices outside it link with all their remaining in-neighbours (and,
-//      for a directed graph, all their out-neighbours), then compress.
+//   4. Vertices outside it link with all their in-neighbours from position 1
+//      on (and, for a directed graph, all their out-neighbours), then
+//      compress.  This covers every arc with an endpoint outside the giant
+//      that round 0 did not link: an arc at position 0 of a row was linked in
+//      round 0, any other is seen from whichever endpoint is outside the giant
+//      (from its in-row, or, in a directed graph, from the tail's out-row).
 // A link always hooks the larger of two roots under the smaller, so a root is
 // the smallest vertex of its tree and the final label of every vertex is the
 // smallest vertex id of its component: the labelling is unique (any correct
@@ -33,6 +43,7 @@ constexpr int CC_THREADS = 256;
 constexpr int CC_SAMPLE_ROUNDS = 2;
 constexpr int CC_MODE_SAMPLES = 1024;
 constexpr int CC_RETRY_LIMIT = 1 << 22;
+constexpr int CC_LATER_ROUND_BITS = 3;  // 1 in 8 vertices take part in sampling rounds after the first
 
 struct CcDev {
   int32_t giant;  // most frequent root among the samples after the sampling rounds
@@ -75,7 +86,10 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_sample(const int64_t* __restr
                                                           int32_t* comp, int32_t* err) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = __ldg(off + v), e = __ldg(off + v + 1);
-    if (e - b > r) cc_link((int32_t)v, __ldcs(idx + b + r), comp, err);
+    // round 0: every vertex; later rounds: the eighth of the vertices picked
+    // by a multiplicative hash of their id
+    if (e - b > r && (r == 0 || ((uint64_t)v * 0x9E3779B97F4A7C15ull) >> (64 - CC_LATER_ROUND_BITS) == 0))
+      cc_link((int32_t)v, __ldcs(idx + b + r), comp, err);
   }
 }
 
@@ -150,8 +164,9 @@ __global__ void __launch_bounds__(CC_MODE_SAMPLES) k_cc_mode(const int32_t* comp
   }
 }
 
-// Final links over one CSR direction, from position `r` of every row, for the
-// vertices outside the giant component.  A warp takes 32 consecutive rows:
+// Final links over one CSR direction, from position `r` of every row (1 for
+// the in-direction, 0 for a directed graph's out-direction), for the vertices
+// outside the giant component.  A warp takes 32 consecutive rows:
 // rows of up to 32 remaining arcs are walked by their own lane, longer rows
 // by the whole warp, one after another.
 __global__ void __launch_bounds__(CC_THREADS) k_cc_final(const int64_t* __restrict__ off,
@@ -258,7 +273,7 @@ gap_status gap_cc_run(gap_graph_t* g, int32_t* labels, void* stream) {
   }
   k_cc_mode<<<1, CC_MODE_SAMPLES, 0, s>>>(comp, n, dev);
   GAP_LAUNCH_CHECK();
-  k_cc_final<<<grid, CC_THREADS, 0, s>>>(g->in_off, g->in_idx, n, CC_SAMPLE_ROUNDS, comp, dev, err);
+  k_cc_final<<<grid, CC_THREADS, 0, s>>>(g->in_off, g->in_idx, n, 1, comp, dev, err);
   GAP_LAUNCH_CHECK();
   launches += 2;
   if (!g->symmetric) {
