@@ -65,15 +65,19 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_init(const int64_t* __restr
   }
 }
 
-// Top-down step over the frontier q[0..nf) whose out-degrees have the
-// exclusive prefix qoff and the sum `total`.
+// Top-down step over the frontier q[0..nf) (nf >= 1) with out-degrees qd and
+// their exclusive prefix qoff.
 __global__ void __launch_bounds__(BFS_THREADS) k_bfs_td(const int64_t* __restrict__ out_off,
                                                         const int32_t* __restrict__ out_idx,
-                                                        const int32_t* __restrict__ q, const int64_t* __restrict__ qoff,
-                                                        int64_t nf, int64_t total, int32_t* parent,
-                                                        int32_t* __restrict__ qn, uint32_t* __restrict__ qdn,
-                                                        BfsDev* dev) {
+                                                        const int32_t* __restrict__ q, const uint32_t* __restrict__ qd,
+                                                        const int64_t* __restrict__ qoff, int64_t nf, int64_t total_hint,
+                                                        int32_t* parent, int32_t* __restrict__ qn,
+                                                        uint32_t* __restrict__ qdn, BfsDev* dev) {
   const unsigned FULL = 0xffffffffu;
+  // the frontier's arc total from the prefix itself (the host's figure sizes
+  // the grid; this one bounds every index the step reads)
+  const int64_t total_true = __ldg(qoff + nf - 1) + (int64_t)__ldg(qd + nf - 1);
+  const int64_t total = total_true < total_hint ? total_true : total_hint;
   const int lane = threadIdx.x & 31;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   unsigned long long scout = 0;
@@ -188,6 +192,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_bm2q(const uint32_t* __rest
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = ((int64_t)blockIdx.x * BFS_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * BFS_THREADS) >> 5;
+  unsigned long long arcs = 0;
   for (int64_t base = warp_id * 32; base < n; base += nwarps * 32) {
     const uint32_t w = __ldg(bm + (base >> 5));
     if (!w) continue;
@@ -198,10 +203,14 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_bm2q(const uint32_t* __rest
     if (in) {
       const int64_t v = base + lane;
       const unsigned long long slot = b + __popc(w & ((1u << lane) - 1u));
+      const uint32_t d = (uint32_t)(__ldg(out_off + v + 1) - __ldg(out_off + v));
       q[slot] = (int32_t)v;
-      qd[slot] = (uint32_t)(__ldg(out_off + v + 1) - __ldg(out_off + v));
+      qd[slot] = d;
+      arcs += d;
     }
   }
+  arcs = warp_sum(arcs);  // the queue's out-arcs: the next top-down step's work
+  if (lane == 0 && arcs) atomicAdd(&dev->scout, arcs);
 }
 
 // Negative (unvisited) entries become -1; counts the reached vertices.
@@ -289,6 +298,7 @@ gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, void* st
   };
   int64_t nf = 0, scout = 0;
   GAP_TRY(read_counts(&nf, &scout));
+  int64_t frontier_arcs = scout;  // out-arcs of the current queue
   int64_t edges_to_check = m;
   while (nf > 0) {
     if (scout > edges_to_check / BFS_ALPHA) {
@@ -318,35 +328,28 @@ gap_status gap_bfs_run(gap_graph_t* g, int32_t source, int32_t* parent, void* st
       k_bfs_bm2q<<<grid, BFS_THREADS, 0, s>>>(fa, n, out_off, qa, da, dev);
       GAP_LAUNCH_CHECK();
       ++launches;
-      GAP_TRY(read_counts(&nf, &scout));
+      GAP_TRY(read_counts(&nf, &frontier_arcs));
       scout = 1;  // the published heuristic: continue top-down after a bottom-up phase
     } else {
       // top-down step from qa (degrees da)
       NvtxRange nv_td("bfs_top_down_step");
       edges_to_check -= scout;
-      int64_t total = 0;
+      // the frontier's out-arcs: the scout count of the step that built it
+      // (or the conversion's sum after a bottom-up phase)
+      const int64_t total = frontier_arcs;
       GAP_TRY(exclusive_scan_u32(da, qoff_s.as<int64_t>(), nf, tmp_s.as<int64_t>(), nullptr, s));
       launches += 3;
-      // the frontier's arc total is the scout count of the step that built it
-      // (recounted here so a reset scout after a bottom-up phase does not matter)
-      {
-        int64_t last_off = 0;
-        uint32_t last_deg = 0;
-        GAP_CUDA(cudaMemcpyAsync(&last_off, qoff_s.as<int64_t>() + nf - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        GAP_CUDA(cudaMemcpyAsync(&last_deg, da + nf - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        GAP_CUDA(cudaStreamSynchronize(s));
-        total = last_off + last_deg;
-      }
       GAP_CUDA(cudaMemsetAsync(dev, 0, sizeof(BfsDev), s));
       if (total > 0) {
         k_bfs_td<<<stride_grid((total + TD_K - 1) / TD_K, BFS_THREADS, 8), BFS_THREADS, 0, s>>>(
-            out_off, out_idx, qa, qoff_s.as<int64_t>(), nf, total, par, qb, db, dev);
+            out_off, out_idx, qa, da, qoff_s.as<int64_t>(), nf, total, par, qb, db, dev);
         GAP_LAUNCH_CHECK();
         ++launches;
       }
       ++td_steps;
       ++levels;
       GAP_TRY(read_counts(&nf, &scout));
+      frontier_arcs = scout;
       int32_t* tq = qa;
       qa = qb;
       qb = tq;

@@ -8,12 +8,12 @@
 //   1. comp[v] = v.
 //   2. Two sampling rounds, each followed by a compress (every vertex jumps to
 //      its root): in round 0 every vertex links with its first in-neighbour;
-//      in round 1 one vertex in eight (picked by a multiplicative hash of its
-//      id) links with its second.  After round 0 the graph is a few large
+//      in round 1 one vertex in sixteen (picked by a multiplicative hash of
+//      its id) links with its second.  After round 0 the graph is a few large
 //      trees, and a link across two of them reads and hooks the same root as
 //      every other such link, so a full second round spends most of its time
-//      queued on a handful of addresses; an eighth of the links still merges
-//      the large trees, and what it leaves is picked up in step 4.
+//      queued on a handful of addresses; a sixteenth of the links still
+//      merges the large trees, and what it leaves is picked up in step 4.
 //   3. The most frequent root among 1024 fixed sample positions names the
 //      giant component.
 //   4. Vertices outside it link with all their in-neighbours from position 1
@@ -43,7 +43,7 @@ constexpr int CC_THREADS = 256;
 constexpr int CC_SAMPLE_ROUNDS = 2;
 constexpr int CC_MODE_SAMPLES = 1024;
 constexpr int CC_RETRY_LIMIT = 1 << 22;
-constexpr int CC_LATER_ROUND_BITS = 3;  // 1 in 8 vertices take part in sampling rounds after the first
+constexpr int CC_LATER_ROUND_BITS = 4;  // 1 in 16 vertices take part in sampling rounds after the first
 
 struct CcDev {
   int32_t giant;  // most frequent root among the samples after the sampling rounds
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_sample(const int64_t* __restr
                                                           int32_t* comp, int32_t* err) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = __ldg(off + v), e = __ldg(off + v + 1);
-    // round 0: every vertex; later rounds: the eighth of the vertices picked
-    // by a multiplicative hash of their id
+    // round 0: every vertex; later rounds: the sixteenth of the vertices
+    // picked by a multiplicative hash of their id
     if (e - b > r && (r == 0 || ((uint64_t)v * 0x9E3779B97F4A7C15ull) >> (64 - CC_LATER_ROUND_BITS) == 0))
       cc_link((int32_t)v, __ldcs(idx + b + r), comp, err);
   }
