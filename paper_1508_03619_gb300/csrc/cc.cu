@@ -93,19 +93,22 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_sample(const int64_t* __restr
   }
 }
 
-// Every vertex jumps to its root.  Values only ever move up their tree, so
-// concurrent jumps of other vertices are harmless.
+// Every vertex jumps to its root.  No hooks run during this kernel, so roots
+// stay roots and every other value only moves up its tree: a stale copy of an
+// entry is an older ancestor, never a false root.  The chase may therefore
+// read through L1, where the few large roots that most vertices reach stay
+// resident instead of being requested from one L2 line by every warp.
 __global__ void __launch_bounds__(CC_THREADS) k_cc_compress(int32_t* comp, int64_t n, int32_t* err) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c0 = ldc(comp + v);
-    int32_t c = c0, cc = ldc(comp + c0);
+    const int32_t c0 = __ldca(comp + v);
+    int32_t c = c0, cc = __ldca(comp + c0);
     for (int it = 0; cc != c; ++it) {
       if (it >= CC_RETRY_LIMIT) {
         atomicExch(err, 1);
         break;
       }
       c = cc;
-      cc = ldc(comp + c);
+      cc = __ldca(comp + c);
     }
     if (c != c0) comp[v] = c;
   }
