@@ -54,12 +54,16 @@ struct CcDev {
   int32_t pad;
 };
 
-// comp is written by other threads during a kernel: read it at L2, never
-// through the non-coherent path.
+// comp is written by other threads during the link kernels: the values their
+// decisions rest on are read at L2, never through the non-coherent path.
 __device__ __forceinline__ int32_t ldc(const int32_t* p) { return __ldcg(p); }
 
+// The starting points may come from L1: any value an entry ever held is an
+// ancestor in the same tree, so a stale one only means more climbing; every
+// value a decision rests on (the root test and the compare-and-swap) is read
+// coherently at L2.
 __device__ __forceinline__ void cc_link(int32_t u, int32_t v, int32_t* comp, int32_t* err) {
-  int32_t p1 = ldc(comp + u), p2 = ldc(comp + v);
+  int32_t p1 = __ldca(comp + u), p2 = __ldca(comp + v);
   for (int it = 0; p1 != p2; ++it) {
     if (it >= CC_RETRY_LIMIT) {
       atomicExch(err, 1);
