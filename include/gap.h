@@ -19,6 +19,10 @@
  *     is strict (delta < tol).  tol = 0 runs exactly max_iters iterations.
  *
  * Conventions for every entry point:
+ *   - Threads: calls on different graph handles may run from different host
+ *     threads at once; calls on one handle must not overlap (each handle keeps
+ *     one pinned buffer per kernel family for the stats of its last run), with
+ *     the PPR server's submit/poll/wait/info as the documented exception.
  *   - Pointers are plain host or device addresses (unified addressing decides
  *     which); sizes are element counts; vertex IDs are int32 (§2.3 allows 32-bit
  *     IDs), edge offsets int64 (§2.3 requires support for more than 2^32 edges).
