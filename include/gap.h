@@ -461,7 +461,6 @@ GAP_API gap_status gap_ppr_server_info_ex(gap_ppr_server_t* s, gap_ppr_server_in
  * overlap them. */
 GAP_API void gap_ppr_server_destroy(gap_ppr_server_t* s);
 
-/* ------------------------------------------------- no-allocation variant --- */
 /* -------------------------------------------- connected components --- */
 /* §2.1 Connected Components: every vertex gets the label of its weakly
  * connected component (arcs read as undirected edges; a vertex without arcs
@@ -537,6 +536,7 @@ GAP_API gap_status gap_bfs_stats(gap_graph_t* g, gap_bfs_stats_t* out);
  * Returns GAP_OK when the self-test ran; INVALID_ARG (NULL), OOM, CUDA. */
 GAP_API gap_status gap_selftest_barrier_timeout(int32_t* observed, double* waited_ms, void* stream);
 
+/* ------------------------------------------------- no-allocation variant --- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory during the call: code running while a CUDA
  * stream is being captured (cudaMalloc is not allowed there), processes whose
