@@ -20,9 +20,11 @@
  *
  * Conventions for every entry point:
  *   - Threads: calls on different graph handles may run from different host
- *     threads at once; calls on one handle must not overlap (each handle keeps
- *     one pinned buffer per kernel family for the stats of its last run), with
- *     the PPR server's submit/poll/wait/info as the documented exception.
+ *     threads at once; PageRank, CC or BFS calls on one handle must not
+ *     overlap each other (each handle keeps one pinned buffer per kernel family
+ *     for the stats of its last run).  A PPR server only reads its graph's
+ *     arrays, so other calls may use that graph while the server runs; the
+ *     server's own submit/poll/wait/info are safe from any thread.
  *   - Pointers are plain host or device addresses (unified addressing decides
  *     which); sizes are element counts; vertex IDs are int32 (§2.3 allows 32-bit
  *     IDs), edge offsets int64 (§2.3 requires support for more than 2^32 edges).
