@@ -78,7 +78,8 @@ def parse():
                     help="convergence loop driver (host: one launch per kernel, visible to ncu)")
     ap.add_argument("--segment-bytes", type=int, default=0, help="L2 blocking segment size (0 = default)")
     ap.add_argument("--workload", default="all", choices=["all", "pagerank", "batch", "ppr", "cc", "bfs"],
-                    help="all: the PageRank line with batch and ppr entries")
+                    help="all: the PageRank line with batch, ppr, cc and bfs entries; "
+                         "the others: one line for that workload alone")
     ap.add_argument("--ppr-seconds", type=float, default=6.0, help="arrival window per load level")
     ap.add_argument("--ppr-scale", type=int, default=24)
     ap.add_argument("--ppr-edges", type=float, default=5e8)

@@ -198,3 +198,17 @@ def test_load_flags_and_formats_checked_before_device_work(tmp_path):
     e.write_text("# nothing\n")
     with pytest.raises(gap.GapError, match="no vertex"):
         gap.gap_graph_load(e)
+
+
+def test_bfs_source_selector_is_deterministic_and_picks_vertices_with_out_arcs():
+    """§2.3: sources are random vertices of non-zero degree, drawn by a
+    deterministic selector (same graph and seed, same sources)."""
+    rng = np.random.default_rng(5)
+    outdeg = rng.integers(0, 3, 5000)
+    a = gap.bfs_sources(outdeg, 64)
+    assert a == gap.bfs_sources(outdeg, 64) and len(a) == 64
+    assert all(outdeg[v] > 0 for v in a)
+    assert gap.bfs_sources(outdeg, 64, seed=7) != a
+    assert len(set(a)) > 50  # spread over the graph, not one vertex repeated
+    with pytest.raises(ValueError):
+        gap.bfs_sources(np.zeros(10, np.int64), 4)
