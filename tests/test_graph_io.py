@@ -212,3 +212,18 @@ def test_bfs_source_selector_is_deterministic_and_picks_vertices_with_out_arcs()
     assert len(set(a)) > 50  # spread over the graph, not one vertex repeated
     with pytest.raises(ValueError):
         gap.bfs_sources(np.zeros(10, np.int64), 4)
+
+
+def test_line_longer_than_the_read_buffer(tmp_path):
+    """A METIS vertex line of ~27 MB (a hub with 3.5M neighbours) is longer
+    than the reader's 16 MB buffer, which must grow to hold it."""
+    n = 3_500_001
+    hub_line = " ".join(map(str, range(2, n + 1)))
+    assert len(hub_line) > (16 << 20)
+    text = f"{n} {n - 1}\n" + hub_line + "\n" + "1\n" * (n - 1)
+    p = tmp_path / "hub.graph"
+    p.write_text(text)
+    m_n, src, dst, _ = gap.gap_edge_list_read(p)
+    assert m_n == n and len(src) == 2 * (n - 1)
+    assert (src[: n - 1] == 0).all() and np.array_equal(dst[: n - 1], np.arange(1, n))
+    assert np.array_equal(src[n - 1:], np.arange(1, n)) and (dst[n - 1:] == 0).all()
