@@ -199,3 +199,25 @@ def test_bfs_full_size(cuda_device, kind):
     finally:
         g.close()
         torch.cuda.empty_cache()
+
+
+def test_bfs_and_cc_on_a_road_like_lattice(cuda_device):
+    """A 256 x 256 lattice with 5 % of its edges deleted (the road-like shape
+    of the batch workload): hundreds of thin levels, one step per level plus
+    the step that finds nothing, and connected components on the same graph."""
+    import torch
+    rows = cols = 256
+    s, d = gapgen.grid(rows, cols, 0.05, seed=0xB15)
+    n = rows * cols
+    off, idx = oracle.build_csr(n, s, d, symmetrize=True)
+    with gpu_graph(n, s, d, symmetrize=True) as g:
+        for src in (0, n // 2 + cols // 2, n - 1):
+            par, st = _run(g, src)
+            depth = oracle.bfs_depths(off, idx, src)
+            assert oracle.bfs_verify(off, idx, src, par)
+            assert st["levels"] == int(depth.max()) + 1 and st["levels"] > 250
+        lab = torch.empty(n, dtype=torch.int32, device="cuda")
+        gap.gap_cc_run(g.handle, lab)
+        _, cst = gap.gap_cc_stats(g.handle)
+        want = oracle.cc(off, idx)
+        assert np.array_equal(lab.cpu().numpy(), want) and cst["components"] == len(np.unique(want))

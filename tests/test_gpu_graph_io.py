@@ -141,3 +141,27 @@ def test_damaged_or_inconsistent_files_are_rejected(cuda_device, tmp_path):
     with gap.Graph.load(good) as g:
         x = _scores(g, 5)
         assert np.all(np.isfinite(x)) and np.all(x > 0)
+
+
+def test_loaded_graph_runs_cc_and_bfs_through_the_directed_paths(cuda_device, tmp_path):
+    """A loaded graph does not trust the file's symmetrize flag, so CC and BFS
+    take their directed code paths (out-direction built on first use) on
+    symmetric data; the results must not change."""
+    import torch
+    n = 1 << 13
+    src, dst = gapgen.kron(13, 8, seed=0x44)
+    off, idx = oracle.build_csr(n, src, dst, symmetrize=True)
+    with gpu_graph(n, src, dst, symmetrize=True) as g:
+        p = tmp_path / "k.gcsc"
+        g.save(p)
+    with gap.Graph.load(p) as h:
+        lab = torch.empty(n, dtype=torch.int32, device="cuda")
+        gap.gap_cc_run(h.handle, lab)
+        gap.gap_cc_stats(h.handle)
+        assert np.array_equal(lab.cpu().numpy(), oracle.cc(off, idx))
+        par = torch.empty(n, dtype=torch.int32, device="cuda")
+        for s in gap.bfs_sources(h.export_outdeg(), 4, seed=0x13):
+            gap.gap_bfs_run(h.handle, s, par)
+            st = gap.gap_bfs_stats(h.handle)
+            assert oracle.bfs_verify(off, idx, s, par.cpu().numpy())
+            assert st["reached"] == int((oracle.bfs_depths(off, idx, s) >= 0).sum())
