@@ -108,6 +108,26 @@ def test_server_create_rejects_null_graph():
         gap.GAP_ERR_INVALID_ARG
 
 
+def test_new_entry_points_reject_null_arguments_before_any_device_work():
+    lib = gap.load()
+    bad = gap.GAP_ERR_INVALID_ARG
+    x = np.zeros(4, np.int32)
+    assert lib.gap_cc_run(None, gap._ptr(x), None) == bad
+    assert lib.gap_cc_stats(None, ctypes.byref(gap.gap_cc_stats_t())) == bad
+    assert lib.gap_bfs_run(None, 0, gap._ptr(x), None) == bad
+    assert lib.gap_bfs_stats(None, ctypes.byref(gap.gap_bfs_stats_t())) == bad
+    assert lib.gap_selftest_barrier_timeout(None, None, None) == bad
+    assert lib.gap_graph_save(None, b"/nonexistent/x.gcsc", None) == bad
+    assert lib.gap_graph_load(None, 0, 0, None, None) == bad
+    assert lib.gap_edge_list_read(None, 0, None) == bad
+    assert lib.gap_edge_list_info(None, None, None, None) == bad
+    assert lib.gap_edge_list_arrays(None, None, None) == bad
+    f = ctypes.c_uint32()
+    assert lib.gap_graph_build_flags(None, ctypes.byref(f)) == bad
+    lib.gap_edge_list_destroy(None)  # a no-op
+    assert gap.last_error_message()
+
+
 def test_allocator_hook_validation():
     lib = gap.load()
     assert lib.gap_set_allocator(None) == gap.GAP_OK
