@@ -593,6 +593,9 @@ def test_bfs_verifier_accepts_every_valid_tree_and_rejects_each_broken_rule():
     v = int(reached[0])
     bad = lo.copy(); bad[source] = -1                        # source is not its own parent
     assert not oracle.bfs_verify(off, idx, source, bad)
+    for out_of_range in (n, -2):                             # a parent that is no vertex
+        bad = lo.copy(); bad[int(reached[-1])] = out_of_range
+        assert not oracle.bfs_verify(off, idx, source, bad)
     bad = lo.copy(); bad[v] = -1                             # a reachable vertex left out
     assert not oracle.bfs_verify(off, idx, source, bad)
     bad = lo.copy(); bad[int(unreached[0])] = source         # an unreachable vertex given a parent
