@@ -131,7 +131,7 @@ GAP_API gap_status gap_graph_export_outdeg(gap_graph_t* g, int32_t* outdeg, void
 GAP_API void gap_graph_destroy(gap_graph_t* g);
 
 /* ---------------------------------------------------- graph files --- */
-/* §4 of the paper: the reference infrastructure loads graphs from files (METIS,
+/* §3 of the paper: the reference infrastructure loads graphs from files (METIS,
  * Matrix Market, and a plain-text edge list as the easy fallback) and can
  * serialize a built graph so that later runs load it directly, skipping the
  * build.  Text files are parsed on the host into an edge list that the device
@@ -540,10 +540,11 @@ GAP_API gap_status gap_selftest_barrier_timeout(int32_t* observed, double* waite
 
 /* ------------------------------------------------- no-allocation variant --- */
 /* The paper has no counterpart to this entry point.  It serves callers that
- * cannot allocate device memory during the call: code running while a CUDA
- * stream is being captured (cudaMalloc is not allowed there), processes whose
- * device memory is entirely owned by a fixed memory plan or arena, and
- * latency-critical paths that must never wait on an allocator.
+ * cannot allocate device memory during the call: processes whose device
+ * memory is entirely owned by a fixed memory plan or arena (a server that
+ * reserved all of it up front, a host application with its own allocator that
+ * the library's allocator hook cannot reach), and latency-critical paths that
+ * must never wait on an allocator or run out of memory half-way through.
  *
  * Same result contract as gap_pr_run (FP32 scores, FP32 accumulation, FP64
  * convergence reduction), but all scratch lives in one static device array of
@@ -554,14 +555,16 @@ GAP_API gap_status gap_selftest_barrier_timeout(int32_t* observed, double* waite
  *  - `scores` must be device memory (n floats, caller-owned); the graph comes
  *    from gap_graph_create* as usual (created before, outside this call).
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
- *  - The convergence loop is driven from the host (one synchronization per
- *    iteration), so the call returns after the run finished; gap_pr_stats
- *    reports it afterwards.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    process; after a cudaDeviceReset this entry point must not be used again.
+ *  - The convergence loop is driven from the host (one stream synchronization
+ *    per iteration, and one at the end), so the call returns after the run and
+ *    its last reads of the shared array finished; gap_pr_stats reports it
+ *    afterwards.  Because it synchronizes, it must not be called on a stream
+ *    that is being captured into a CUDA graph.
  *  - All calls share the one array and each starts by rewriting everything it
- *    reads; calls that overlap on the GPU (e.g. on two streams at once) race
- *    and must not be issued. */
+ *    reads; calls that overlap on the GPU (from two host threads at once, on
+ *    any streams) race and must not be issued. */
 #define GAP_NOALLOC_MAX_VERTICES (1LL << 20)
 GAP_API gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double tol, int32_t max_iters,
                                       float* scores, void* stream);

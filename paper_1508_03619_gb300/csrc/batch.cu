@@ -14,7 +14,7 @@
 //                 last (counted with an atomic) adds the partials in chunk
 //                 order and updates the row.
 // A set-up pass per call (inside the timed region: the split is a run-time
-// decision on the input, §3.2) counts and lists the chunks of every graph.
+// decision on the input, §2.3) counts and lists the chunks of every graph.
 //
 // Per iteration every warp walks the tasks of the graphs still running
 // (grid-stride), and each task adds its |x' - x| to its graph's accumulator as

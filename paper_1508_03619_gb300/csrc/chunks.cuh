@@ -6,7 +6,7 @@
 // graph after graph, row after row, so the chunks of one row are contiguous
 // and `first` (the id of its first chunk) orders them.  The list is a
 // run-time decision on the input graph and is rebuilt by every call that
-// needs it (§3.2: no per-graph precomputed parameters).
+// needs it (§2.3: no per-graph precomputed parameters).
 #pragma once
 
 #include "graph.cuh"

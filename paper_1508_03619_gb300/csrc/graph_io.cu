@@ -1,5 +1,5 @@
 // graph_io.cu — reading graphs from files and serializing built graphs (paper
-// §4: the reference infrastructure loads METIS, Matrix Market and a plain-text
+// §3: the reference infrastructure loads METIS, Matrix Market and a plain-text
 // edge list, and can serialize a built graph so that later runs skip the build).
 //
 // Text formats are parsed on the host into an edge list (src[i] -> dst[i]),

@@ -2076,7 +2076,7 @@ gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max
     return GAP_ERR_UNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->has_run && g->last_stream != s) cudaStreamSynchronize(g->last_stream);  // stats buffer reuse
+  if (g->has_run && g->last_stream != s) GAP_CUDA(cudaStreamSynchronize(g->last_stream));  // stats buffer reuse
   if (o.algorithm == GAP_ALGO_BINNED)
     return run_trial_binned(g, damping, tol, max_iters, o, static_cast<float*>(scores), s);
   if (o.precision == GAP_PREC_F64)
@@ -2127,16 +2127,18 @@ gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out) {
 // ============================================================================
 // No-allocation variant of the PageRank trial.
 //
-// Some callers cannot allocate device memory while they call us: code that runs
-// while a CUDA stream is being captured (cudaMalloc is not allowed there),
-// processes whose device memory is entirely owned by a fixed memory plan or
-// arena, and latency-critical paths that must never wait on the allocator.
-// For them this variant keeps all of its scratch in one file-scope device
-// array.  It is limited to graphs of at most GAP_NOALLOC_MAX_VERTICES
-// vertices (fewer than 2^31 arcs) and writes FP32 scores into the caller's
-// device buffer.  Every row is pulled in vertex order by k_pull_small, and
-// the convergence loop is host-driven, so no graph, stream or event objects
-// are created either.
+// Some callers cannot allocate device memory while they call us: processes
+// whose device memory is entirely owned by a fixed memory plan or arena (an
+// inference server that reserved all of it up front, an embedding runtime
+// with its own allocator), and latency-critical paths that must never wait on
+// the allocator or risk running out of memory half-way through a call.  For
+// them this variant keeps all of its scratch in one file-scope device array.
+// It is limited to graphs of at most GAP_NOALLOC_MAX_VERTICES vertices (fewer
+// than 2^31 arcs) and writes FP32 scores into the caller's device buffer.
+// Every row is pulled in vertex order by k_pull_small, and the convergence
+// loop is host-driven (one stream synchronization per iteration), so no
+// graph, stream or event objects are created either; for the same reason the
+// call cannot be issued on a stream that is being captured.
 namespace gap {
 
 constexpr int64_t NOALLOC_C_BYTES = 2 * sizeof(float) * GAP_NOALLOC_MAX_VERTICES;  // c0, c1
@@ -2148,7 +2150,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Device address of g_noalloc_scratch per device.  In host code the symbol is
 // only a host-side stand-in, so the address is looked up once per device
-// (with that device current) by cudaGetSymbolAddress.
+// (with that device current) by cudaGetSymbolAddress, on the first call.  The
+// cached address belongs to the device's context of that moment: after a
+// cudaDeviceReset the module is loaded anew and this entry point must not be
+// used again in the process.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {};
 
@@ -2192,7 +2197,7 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
     return GAP_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->has_run && g->last_stream != s) cudaStreamSynchronize(g->last_stream);  // stats buffer reuse
+  if (g->has_run && g->last_stream != s) GAP_CUDA(cudaStreamSynchronize(g->last_stream));  // stats buffer reuse
   void* base = nullptr;
   GAP_TRY(noalloc_scratch(&base));
   const int64_t n = g->n;
@@ -2247,6 +2252,9 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
   k_mass_final<<<1, 1024, 0, s>>>(dctrl, partial, mg);
   GAP_LAUNCH_CHECK();
   GAP_CUDA(cudaMemcpyAsync(g->stats_host, &dctrl->st, sizeof(gap_pr_stats_t), cudaMemcpyDeviceToHost, s));
+  // the mass kernels and the stats copy still read the shared array: wait for
+  // them, so that a next call (any stream, any graph) finds the array free
+  GAP_CUDA(cudaStreamSynchronize(s));
   g->launches_per_iter = 2;
   g->launches_fixed = 4;
   g->last_segments = 1;

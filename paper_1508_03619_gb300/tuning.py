@@ -4,7 +4,7 @@ The autotuner (``python -m paper_1508_03619_gb300.autotune``) measures the
 launch and split parameters once per GPU model on a tuning set of synthetic
 graphs that is disjoint from the evaluation graphs, and writes one fixed JSON
 table per model under ``tuning/``.  The table holds hardware-specific values
-only (§3.2 allows tuning to the platform, not to an input graph): the same
+only (§2.3 allows tuning to the platform, not to an input graph): the same
 values are used for every graph on that GPU model, and the per-graph choices
 (degree bins, heavy rows) stay run-time decisions inside each trial.
 

@@ -1,4 +1,4 @@
-"""Graph files on the host (paper §4: the reference loads METIS, Matrix Market
+"""Graph files on the host (paper §3: the reference loads METIS, Matrix Market
 and a plain edge list, and serializes built graphs).  Parsing needs no GPU:
 each format is checked against hand-written expectations, against the
 oracle's CSR builder on seeded graphs written out as text, and on malformed
