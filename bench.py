@@ -51,14 +51,31 @@ MAX_ITERS = 100
 FALLBACK_HBM_GBS = 6800.0
 
 # ncu DRAM bytes of one k_batch_persistent launch on the 256-graph batch with this
-# tuning (profiles/batch_persistent_256.md)
-BATCH_NCU_TRAFFIC = 18.19e9
+# tuning (one capture of that launch; the batch is its own small case)
+BATCH_NCU_TRAFFIC = 18.207e9
 BATCH_NCU_TUNING = {"heavy_min_degree": 512, "chunk_arcs": 2048, "block_threads": 512, "blocks_per_sm": 0}
-# ncu DRAM bytes (read + write) per launch on kron26 with the GB300 tuning table,
-# from one capture of the launch list (profiles/pull_segmented_kron26.md); only
-# kernels and bin bounds unchanged since then (the small-row COO pass changed
-# after that capture, so it has no entry).
-NCU_TRAFFIC = {"k_pull_group_seg<32>": 0.600e9, "k_pull_group_seg<8>": 0.356e9, "k_pull_hub_chunks": 0.127e9}
+# ncu DRAM bytes (read + write) of one launch of each segmented pull kernel on the
+# small case (kron26 at edge factor 4: the benchmark's vertex count and source
+# segments, a quarter of its arcs), with the arcs that launch streams and the bytes
+# it streams per arc (column index; the packed COO pass also streams the row id).
+# Full-size traffic per launch = the captured bytes with the streamed part rescaled
+# to the full launch's arcs; the rest (one segment of contributions, row data, the
+# COO pass's running row sums) is per launch and does not grow with the arcs.
+NCU_SMALL = {  # kernel: (DRAM bytes, arcs in the launch, streamed bytes per arc)
+    "k_pull_group_seg<32>": (143.33e6, 184692430 / 8, 4),
+    "k_pull_group_seg<8>": (124.92e6, 97466713 / 8, 4),
+    "k_pull_small_coo<float,8,32>": (785.63e6, 234491820 / 8, 8),
+    "k_pull_hub_chunks": (38.70e6, 16262037 / 8, 4),
+}
+
+
+def scaled_traffic(kname, arcs_per_launch):
+    """DRAM bytes per launch of kernel kname at arcs_per_launch streamed arcs,
+    from its small-case capture (None when the kernel has no capture)."""
+    if kname not in NCU_SMALL:
+        return None
+    small, small_arcs, per_arc = NCU_SMALL[kname]
+    return small + per_arc * (arcs_per_launch - small_arcs)
 
 
 def parse():
@@ -74,6 +91,8 @@ def parse():
     ap.add_argument("--seed", type=lambda s: int(s, 0), default=0x26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the full-size FP64 oracle run behind error_vs_oracle")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="convergence loop driver (host: one launch per kernel, visible to ncu)")
     ap.add_argument("--segment-bytes", type=int, default=0, help="L2 blocking segment size (0 = default)")
@@ -203,9 +222,12 @@ def roofline_entry(sp, m, n, segments, contrib_bytes=4):
     iter_ms = loop_ms / iters
     iter_bytes = per_arc * m + per_row * n
     total_ms = sum(sp["phase_ms"].values())
+    traffic = scaled_traffic(kname, b["arcs"] * iters / launches)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kname),
-            "useful_byte_efficiency": (per_launch_alg / NCU_TRAFFIC[kname]) if kname in NCU_TRAFFIC else None,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on kron26 at "
+                              "edge factor 4, streamed arc bytes rescaled to this launch's arcs",
+            "useful_byte_efficiency": (per_launch_alg / traffic) if traffic else None,
             "kernel": f"{kname} (bin {q}: in-degree <= {b['max_degree']}, "
                       + ("packed COO, one pass per source segment)" if lanes == -1 and segments > 1 else
                          "segmented)" if b["segmented"] else "whole rows)"),
@@ -300,7 +322,107 @@ def combine_ranks(ms, arcs, pg, device):
     return float(t.item()), float(c.item())
 
 
-def run_pagerank(a, ws, rank, local, dev, pg):
+def oracle_cache_dir(a):
+    """Where the full-size oracle run of this workload is kept (outside the
+    repository), keyed by everything that fixes the graph and the method."""
+    root = os.environ.get("GAP_ORACLE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gap_oracle"))
+    key = f"{a.graph}{a.scale}-ef{a.edge_factor}-seed{a.seed:#x}-d{DAMPING}-tol{TOL}-v1"
+    return os.path.join(root, key)
+
+
+def oracle_leg(graph, scale, edge_factor, seed, outdir):
+    """The oracle on the full workload, run in a spawned child process while
+    the GPU is measured: the same host draws as the device generator makes,
+    the oracle's own CSR (row-partitioned builder, identical to the serial
+    one), then the single-threaded FP64 push iteration to tol, keeping the
+    iterates before, at and after the stop so the GPU's results can be held
+    against the oracle's iterate of the same count."""
+    import numpy as np
+
+    # lowest priority and two cores left free: the parent's host work (graph
+    # capture, launches, synchronizations) runs inside its timed trials
+    os.nice(19)
+    threads = max(1, (os.cpu_count() or 1) - 2)
+    os.environ["GAPGEN_THREADS"] = str(threads)
+    import gapgen
+    import oracle
+    t0 = time.perf_counter()
+    n = 1 << scale
+    if graph == "urand":
+        src, dst = gapgen.urand(n, edge_factor << scale, seed)
+        sym = False
+    else:
+        src, dst = gapgen.kron(scale, edge_factor, seed)
+        sym = True
+    off, idx = oracle.build_csr(n, src, dst, symmetrize=sym, threads=threads)
+    del src, dst
+    t1 = time.perf_counter()
+    prev = None
+    x, k, hist = oracle.pagerank(off, idx, DAMPING, 0.0, 1)
+    deltas = [float(hist[0])]
+    while deltas[-1] >= TOL and k < MAX_ITERS:
+        prev = x
+        x, _, h = oracle.pagerank_from(off, idx, x, 1, DAMPING)
+        k += 1
+        deltas.append(float(h[0]))
+    nxt, _, _ = oracle.pagerank_from(off, idx, x, 1, DAMPING)
+    t2 = time.perf_counter()
+    os.makedirs(outdir, exist_ok=True)
+    for name, arr in (("x_prev", prev), ("x_stop", x), ("x_next", nxt)):
+        if arr is not None:
+            np.save(os.path.join(outdir, name + ".npy"), arr)
+    with open(os.path.join(outdir, "meta.json"), "w") as f:
+        json.dump({"iterations": k, "deltas": deltas, "m": int(len(idx)), "build_s": t1 - t0,
+                   "iterate_s": t2 - t1, "threads_build": threads}, f)
+
+
+def start_oracle_leg(a):
+    """Spawn the oracle leg (nothing to do when its result is cached)."""
+    out = oracle_cache_dir(a)
+    if os.path.exists(os.path.join(out, "meta.json")):
+        return None, out
+    import multiprocessing as mp
+    p = mp.get_context("spawn").Process(target=oracle_leg, args=(a.graph, a.scale, a.edge_factor, a.seed, out))
+    p.start()
+    return p, out
+
+
+def error_vs_oracle(proc, out, gpu):
+    """L1 and max relative error of each GPU result (name -> (scores, its
+    iteration count)) against the oracle's iterate of the same count."""
+    import numpy as np
+    t0 = time.perf_counter()
+    if proc is not None:
+        proc.join()
+        if proc.exitcode != 0:
+            return {"error": f"oracle leg exited with {proc.exitcode}"}
+    with open(os.path.join(out, "meta.json")) as f:
+        meta = json.load(f)
+    k = meta["iterations"]
+    res = {"oracle": "FP64 single-threaded push iterations (paper §2.1 equation) on the oracle's own CSR "
+                     "from the same draws; errors against the oracle iterate with the GPU's iteration count",
+           "oracle_iterations": k, "oracle_final_delta": meta["deltas"][-1], "m": meta["m"],
+           "oracle_seconds": {"csr_build": meta["build_s"], "iterations": meta["iterate_s"],
+                              "build_threads": meta["threads_build"]},
+           "wait_s": None}
+    files = {k - 1: "x_prev", k: "x_stop", k + 1: "x_next"}
+    cache = {}
+    for name, (x, iters) in gpu.items():
+        f = files.get(iters)
+        if f is None or not os.path.exists(os.path.join(out, f + ".npy")):
+            res[name] = {"iterations": iters, "l1": None, "max_rel": None,
+                         "note": "iteration count more than one away from the oracle's"}
+            continue
+        if f not in cache:
+            cache[f] = np.load(os.path.join(out, f + ".npy"))
+        xo = cache[f]
+        diff = np.abs(x - xo)
+        res[name] = {"iterations": iters, "l1": float(diff.sum()), "max_rel": float(np.max(diff / xo))}
+    res["wait_s"] = time.perf_counter() - t0
+    return res
+
+
+def run_pagerank(a, ws, rank, local, dev, pg, oracle_proc=None):
     """The headline line: K PageRank trials on the kron (or urand) graph."""
     import torch
 
@@ -391,6 +513,7 @@ def run_pagerank(a, ws, rank, local, dev, pg):
     roofline = roofline_entry(sp, m, n, sp["segments"])
 
     # ---- FP64 GPU path on the same graph (metric: FP32 vs FP64 at L1 <= 1e-4) ----
+    gpu_results = {"fp32": (scores.double().cpu().numpy(), iters[-1])}
     fp64 = None
     if not a.no_fp64:
         o64 = options()
@@ -410,6 +533,7 @@ def run_pagerank(a, ws, rank, local, dev, pg):
         torch.cuda.synchronize(dev)
         v64 = m * it64 / (f0.elapsed_time(f1) / 1e3) / 1e9
         l1 = float((x64 - scores.double()).abs().sum().item())
+        gpu_results["fp64"] = (x64.cpu().numpy(), s64["iterations"])
         fp64 = {"value": v64, "unit": UNIT, "fp32_speedup": value / ws / v64 if v64 else None,
                 "l1_fp32_vs_fp64": l1, "iterations": s64["iterations"]}
 
@@ -435,6 +559,7 @@ def run_pagerank(a, ws, rank, local, dev, pg):
             b1.record(stream)
             torch.cuda.synchronize(dev)
             vb = m * itb / (b0.elapsed_time(b1) / 1e3) / 1e9
+            gpu_results["bf16_" + label] = (xb.double().cpu().numpy(), sb["iterations"])
             bf16[label] = {"value": vb, "unit": UNIT, "vs_fp32": vb / (value / ws),
                            "l1_vs_fp64": float((x64 - xb.double()).abs().sum().item()),
                            "iterations": sb["iterations"], "bf16_iterations": sb["bf16_iters"],
@@ -447,6 +572,10 @@ def run_pagerank(a, ws, rank, local, dev, pg):
     if a.workload == "all":
         cc = measure_cc(g, dev, stream, max(1, a.steps), max(3, a.warmup), a.graph != "urand")
         bfs = measure_bfs(g, dev, stream, gap.bfs_sources(g.export_outdeg(), 64), max(3, a.warmup))
+    oracle_err = None
+    if oracle_proc is not None:
+        oracle_err = error_vs_oracle(*oracle_proc, gpu_results)
+    del gpu_results
 
     g.close()
     del scores, host_scores
@@ -468,6 +597,8 @@ def run_pagerank(a, ws, rank, local, dev, pg):
                               "the stats read between trials is outside these events"},
         "roofline": roofline, "fp64": fp64, "bf16": bf16,
     }
+    if oracle_err is not None:
+        line["error_vs_oracle"] = oracle_err
     if cc is not None:
         line["cc"] = cc
     if bfs is not None:
@@ -758,6 +889,11 @@ def main():
         run_reference(a, ws, rank)
         return
 
+    oracle_proc = None
+    if (a.workload in ("all", "pagerank") and ws == 1 and rank == 0 and not a.no_oracle_check
+            and not a.no_fp64):
+        oracle_proc = start_oracle_leg(a)  # spawned before the first CUDA call
+
     import torch
 
     torch.cuda.set_device(local)
@@ -770,7 +906,7 @@ def main():
 
     line = None
     if a.workload in ("all", "pagerank"):
-        line = run_pagerank(a, ws, rank, local, dev, pg)
+        line = run_pagerank(a, ws, rank, local, dev, pg, oracle_proc)
         if line is not None and a.workload == "all" and ws == 1:
             line["batch"] = measure_batch(a, dev, max(1, a.steps), max(3, a.warmup))
             line["ppr"] = measure_ppr(a, dev)

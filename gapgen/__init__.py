@@ -92,6 +92,11 @@ def _load():
 
 
 def _threads() -> int:
+    """Generator threads: GAPGEN_THREADS if set, else every core (at most 64);
+    the draws do not depend on it."""
+    env = os.environ.get("GAPGEN_THREADS")
+    if env:
+        return max(1, min(64, int(env)))
     return max(1, min(64, os.cpu_count() or 1))
 
 

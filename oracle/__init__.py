@@ -33,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gap_oracle.c")
+_SRC_MT = os.path.join(_HERE, "csr_threaded.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lib = None
@@ -47,10 +48,11 @@ TOL = 1e-4
 def build(force: bool = False) -> str:
     """Compile liboracle.so in-tree (gcc -O2 -ffp-contract=off, single-threaded)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f)
+                                                 for f in (_SRC, _SRC_MT)):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               _SRC, "-o", tmp])
+                               "-pthread", _SRC, _SRC_MT, "-o", tmp])
         os.replace(tmp, _LIB)
     if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_OMP_SRC):
         tmp = _OMP_LIB + f".tmp{os.getpid()}"
@@ -72,6 +74,9 @@ def _load():
         lib.oracle_build_csr.argtypes = [i64, i64, vp, vp, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, vp, vp, ctypes.POINTER(i64)]
         lib.oracle_pagerank.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, vp]
+        lib.oracle_pagerank_from.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, vp]
+        lib.oracle_build_csr_threaded.argtypes = [i64, i64, vp, vp, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, vp, vp, ctypes.POINTER(i64), ctypes.c_int]
         lib.oracle_pr_verify.argtypes = [i64, vp, vp, dbl, vp, ctypes.POINTER(dbl)]
         lib.oracle_ppr.argtypes = [i64, vp, vp, dbl, dbl, i32, vp, i32, vp, vp]
         lib.oracle_pr_rows.argtypes = [i64, vp, vp, vp, dbl, vp, i64, vp, vp]
@@ -82,7 +87,8 @@ def _load():
         lib.oracle_bfs_verify.argtypes = [i64, vp, vp, i32, vp]
         lib.oracle_bfs_verify.restype = ctypes.c_int
         lib.oracle_cc_verify.argtypes = [i64, vp, vp, vp]
-        for f in (lib.oracle_build_csr, lib.oracle_pagerank, lib.oracle_pr_verify, lib.oracle_ppr,
+        for f in (lib.oracle_build_csr, lib.oracle_build_csr_threaded, lib.oracle_pagerank_from,
+                  lib.oracle_pagerank, lib.oracle_pr_verify, lib.oracle_ppr,
                   lib.oracle_pr_rows, lib.oracle_ppr_rows, lib.oracle_cc, lib.oracle_cc_verify):
             f.restype = ctypes.c_int
         _lib = lib
@@ -94,9 +100,10 @@ def _ptr(a: np.ndarray):
 
 
 def build_csr(n: int, src, dst, symmetrize: bool = False, dedup: bool = True,
-              drop_self_loops: bool = True):
+              drop_self_loops: bool = True, threads: int = 1):
     """Out-direction CSR (row u lists v for arcs u->v, ascending).  Returns
-    (offsets int64[n+1], idx int32[m])."""
+    (offsets int64[n+1], idx int32[m]).  threads > 1 runs the row-partitioned
+    twin of the builder (csr_threaded.c), whose output is identical."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     m = len(src)
@@ -106,11 +113,18 @@ def build_csr(n: int, src, dst, symmetrize: bool = False, dedup: bool = True,
     offsets = np.zeros(n + 1, np.int64)
     idx = np.empty(max(cap, 1), np.int32)
     m_out = ctypes.c_int64(0)
-    rc = _load().oracle_build_csr(n, m, _ptr(src), _ptr(dst), int(symmetrize), int(dedup),
-                                  int(drop_self_loops), _ptr(offsets), _ptr(idx),
-                                  ctypes.byref(m_out))
+    if threads > 1:
+        rc = _load().oracle_build_csr_threaded(n, m, _ptr(src), _ptr(dst), int(symmetrize), int(dedup),
+                                               int(drop_self_loops), _ptr(offsets), _ptr(idx),
+                                               ctypes.byref(m_out), int(threads))
+    else:
+        rc = _load().oracle_build_csr(n, m, _ptr(src), _ptr(dst), int(symmetrize), int(dedup),
+                                      int(drop_self_loops), _ptr(offsets), _ptr(idx),
+                                      ctypes.byref(m_out))
     if rc != 0:
         raise ValueError(f"oracle_build_csr failed ({rc})")
+    if threads > 1:  # large graphs: a view, not a second copy of the heads
+        return offsets, idx[: m_out.value]
     return offsets, idx[: m_out.value].copy()
 
 
@@ -133,6 +147,21 @@ def pagerank(offsets, idx, d: float = DAMPING, tol: float = TOL, max_iters: int 
     if k < 0:
         raise ValueError(f"oracle_pagerank failed ({k})")
     return x, int(k), hist[:k].copy()
+
+
+def pagerank_from(offsets, idx, x, iters: int, d: float = DAMPING, tol: float = 0.0):
+    """Continue the push iteration from the iterate x (FP64) for up to iters
+    more iterations (oracle_pagerank's steps and stop test).  Returns (x', k,
+    deltas); continuing x_k for j iterations gives pagerank's x_{k+j}."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.array(x, dtype=np.float64, copy=True)
+    n = len(offsets) - 1
+    hist = np.zeros(max(iters, 1), np.float64)
+    k = _load().oracle_pagerank_from(n, _ptr(offsets), _ptr(idx), d, tol, iters, _ptr(out), _ptr(hist))
+    if k < 0:
+        raise ValueError(f"oracle_pagerank_from failed ({k})")
+    return out, int(k), hist[:k].copy()
 
 
 def verify(offsets, idx, y, d: float = DAMPING) -> float:

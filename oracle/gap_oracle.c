@@ -168,6 +168,38 @@ int oracle_pagerank(int64_t n, const int64_t* off, const int32_t* idx, double d,
 }
 
 /*
+ * oracle_pagerank continued from a given score vector: on entry x holds an
+ * iterate x_k; up to max_iters further iterations are applied exactly as
+ * oracle_pagerank applies them (the same push iteration, the same strict stop
+ * test on each new delta).  So continuing x_k for j iterations gives
+ * oracle_pagerank's x_{k+j} bit for bit, which lets one serial run serve
+ * comparisons at several iteration counts.  Returns the iterations performed,
+ * or -1 / -2 as oracle_pagerank.
+ */
+int oracle_pagerank_from(int64_t n, const int64_t* off, const int32_t* idx, double d, double tol,
+                         int32_t max_iters, double* x, double* delta_hist) {
+  if (n <= 0 || max_iters < 0) return -1;
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* c = (double*)malloc(sizeof(double) * (size_t)n);
+  double* s = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!y || !c || !s) {
+    free(y); free(c); free(s);
+    return -2;
+  }
+  const double base = (1.0 - d) / (double)n;
+  int32_t k = 0;
+  while (k < max_iters) {
+    double delta = push_iteration(n, off, idx, d, base, NULL, x, y, c, s);
+    memcpy(x, y, sizeof(double) * (size_t)n);
+    if (delta_hist) delta_hist[k] = delta;
+    ++k;
+    if (delta < tol) break;
+  }
+  free(y); free(c); free(s);
+  return k;
+}
+
+/*
  * §3 verifier: one extra serial push iteration from a candidate score vector
  * y (e.g. a GPU result promoted to FP64); returns sum_v |y'[v] - y[v]| through
  * *delta.  The §2.1 criterion holds when *delta < 1e-4.

@@ -29,8 +29,17 @@ def _stats(segments, lanes0, dom_ms, launches):
     return {"phase_ms": phase_ms, "phase_launches": launches_d, "bins": bins, "iterations": 7}
 
 
+def test_scaled_traffic_rescales_the_streamed_bytes_only(monkeypatch):
+    """Small-case capture C bytes at a arcs, s streamed bytes per arc: a launch
+    of A arcs moves C + s (A - a) bytes (the rest is per launch)."""
+    monkeypatch.setattr(bench, "NCU_SMALL", {"k": (1.0e6, 1000, 8)})
+    assert bench.scaled_traffic("k", 1000) == pytest.approx(1.0e6)
+    assert bench.scaled_traffic("k", 5000) == pytest.approx(1.0e6 + 8 * 4000)
+    assert bench.scaled_traffic("other", 5000) is None
+
+
 def test_roofline_entry_of_the_packed_small_row_pass(monkeypatch):
-    monkeypatch.setattr(bench, "NCU_TRAFFIC", {"k_pull_small_coo<float,8,32>": 2.0e5})
+    monkeypatch.setattr(bench, "NCU_SMALL", {"k_pull_small_coo<float,8,32>": (2.0e5, 1000, 8)})
     st = _stats(segments=8, lanes0=-1, dom_ms=5.6, launches=56)
     r = bench.roofline_entry(st, m=117000, n=1016, segments=8)
     assert r["kernel"].startswith("k_pull_small_coo<float,8,32> (bin 0")
@@ -39,7 +48,7 @@ def test_roofline_entry_of_the_packed_small_row_pass(monkeypatch):
     assert r["launch_ms"] == pytest.approx(0.1)
     assert r["achieved"] == pytest.approx(alg / 1e-4 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.NCU_TRAFFIC["k_pull_small_coo<float,8,32>"]
+    assert r["traffic"] == pytest.approx(2.0e5 + 8 * (10000 * 7 / 56 - 1000))
     assert r["useful_byte_efficiency"] == pytest.approx(alg / r["traffic"])
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
 

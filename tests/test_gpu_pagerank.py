@@ -246,20 +246,50 @@ def test_kron22_full_config(cuda_device):
     g.close()
 
 
-def test_l2_window_changes_no_result(cuda_device):
-    """options.l2_window marks the contribution arrays persisting in L2 when
-    they fit; the scores and deltas are bit-identical to a run without it."""
-    n = 1 << 18
-    src, dst = gapgen.kron(18, 16, 0x81)
+def device_attribute(attr):
+    """cudaDeviceGetAttribute through the CUDA runtime library (device 0)."""
+    import ctypes
+    for name in ("libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    else:
+        pytest.skip("CUDA runtime library not found")
+    v = ctypes.c_int(0)
+    assert rt.cudaDeviceGetAttribute(ctypes.byref(v), attr, 0) == 0
+    return v.value
+
+
+CUDA_ATTR_MAX_PERSISTING_L2 = 108   # cudaDevAttrMaxPersistingL2CacheSize
+CUDA_ATTR_MAX_WINDOW = 109          # cudaDevAttrMaxAccessPolicyWindowSize
+
+
+def test_l2_window_engages_and_changes_no_result(cuda_device):
+    """options.l2_window marks the two contribution arrays persisting in L2 when
+    they fit the device's persisting carve-out and no L2 blocking runs.  At
+    2^20 vertices (8 MB of contributions) it engages on a device whose limits
+    allow it, and the scores meet the FP32 bars against the oracle and equal a
+    run without the window bit for bit (graph and host loops)."""
+    n = 1 << 20
+    src, dst = gapgen.kron(20, 16, 0x81)
+    off, idx = oracle_graph(n, src, dst, True)
+    xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 15)
     g = gpu_graph(n, src, dst, True)
     try:
+        fits = min(device_attribute(CUDA_ATTR_MAX_PERSISTING_L2), device_attribute(CUDA_ATTR_MAX_WINDOW)) >= 8 * n
         x0, st0, _ = run_gpu(g, 0.0, 15)
         x1, st1, _ = run_gpu(g, 0.0, 15, l2_window=1)
+        assert st0["l2_window_bytes"] == 0 and st1["segments"] == 1
+        assert st1["l2_window_bytes"] == (2 * 4 * n if fits else 0)
+        print(f"persisting L2 {device_attribute(CUDA_ATTR_MAX_PERSISTING_L2)} B, window max "
+              f"{device_attribute(CUDA_ATTR_MAX_WINDOW)} B: window {st1['l2_window_bytes']} B")
+        assert_fp32_parity(x1, xo)
         assert np.array_equal(x0, x1)
         assert st0["deltas"] == st1["deltas"]
-        assert st0["l2_window_bytes"] == 0
-        assert st1["l2_window_bytes"] in (0, 2 * 4 * n)  # 0 when the device has no persisting carve-out
         x2, st2, _ = run_gpu(g, 0.0, 15, l2_window=1, loop=gap.GAP_LOOP_HOST)
+        assert st2["l2_window_bytes"] == st1["l2_window_bytes"]
         assert np.array_equal(x0, x2)
     finally:
         g.close()

@@ -79,6 +79,50 @@ def test_csr_matches_brute_force(symmetrize, dedup, drop, seed):
     assert off[n] == len(idx) == sum(len(r) for r in rows)
 
 
+@pytest.mark.parametrize("threads", [2, 3, 7])
+@pytest.mark.parametrize("symmetrize", [False, True])
+@pytest.mark.parametrize("dedup,drop", [(True, True), (False, False), (True, False)])
+def test_threaded_csr_equals_serial(threads, symmetrize, dedup, drop):
+    """The row-partitioned builder gives the serial builder's CSR bit for bit
+    (which the brute-force pin above fixes), for any thread count, with
+    duplicates, self-loops, hubs and isolated vertices in the draws."""
+    import gapgen
+    cases = [(1 << 12, *gapgen.kron(12, 8, 0xC1)), (5000, *gapgen.urand(5000, 30000, 0xC2))]
+    rng = np.random.default_rng(0xC3)
+    n = 37
+    src = rng.integers(0, n, 400).astype(np.int32)
+    dst = rng.integers(0, n, 400).astype(np.int32)
+    dst[:50] = 5  # a hub with repeated arcs
+    src[50:60] = dst[50:60]  # self-loops
+    cases.append((n, src, dst))
+    cases.append((1, np.zeros(3, np.int32), np.zeros(3, np.int32)))
+    cases.append((9, np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    for n, src, dst in cases:
+        a = oracle.build_csr(n, src, dst, symmetrize, dedup, drop)
+        b = oracle.build_csr(n, src, dst, symmetrize, dedup, drop, threads=threads)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([0, 3], np.int32), np.array([1, 1], np.int32), threads=2)
+
+
+def test_pagerank_from_continues_the_iteration():
+    """Continuing x_k for j iterations gives x_{k+j} of one uninterrupted run
+    bit for bit, with the same deltas; the stop test applies to new deltas."""
+    import gapgen
+    n = 1 << 11
+    off, idx = oracle.build_csr(n, *gapgen.kron(11, 16, 0xC4), symmetrize=True)
+    x20, _, h20 = oracle.pagerank(off, idx, D, 0.0, 20)
+    x7, _, _ = oracle.pagerank(off, idx, D, 0.0, 7)
+    x, k, h = oracle.pagerank_from(off, idx, x7, 13, D)
+    assert k == 13 and np.array_equal(x, x20) and np.array_equal(h, h20[7:])
+    xt, kt, _ = oracle.pagerank(off, idx, D, 1e-4, 100)
+    xr, kr, hr = oracle.pagerank_from(off, idx, x7, 100, D, 1e-4)
+    assert 7 + kr == kt and np.array_equal(xr, xt) and hr[-1] < 1e-4
+    x0 = np.full(n, 1.0 / n)
+    xs, ks, _ = oracle.pagerank_from(off, idx, x0, 5, D)
+    assert np.array_equal(xs, oracle.pagerank(off, idx, D, 0.0, 5)[0])
+
+
 def test_csc_is_transpose():
     rng = np.random.default_rng(7)
     n, m = 30, 200
