@@ -599,6 +599,8 @@ def run_pagerank(a, ws, rank, local, dev, pg, oracle_proc=None):
     }
     if oracle_err is not None:
         line["error_vs_oracle"] = oracle_err
+    if a.workload == "all" and rank == 0:
+        line["l2_window"] = measure_l2_window(dev)
     if cc is not None:
         line["cc"] = cc
     if bfs is not None:
@@ -607,6 +609,48 @@ def run_pagerank(a, ws, rank, local, dev, pg, oracle_proc=None):
         line["cpu_baseline"] = cpu_baseline(a)
     return line
 
+
+
+def measure_l2_window(dev, steps=8):
+    """options.l2_window on the one benchmark-shaped graph where it engages: a
+    uniform random digraph of 2^22 vertices (degree 16), whose two FP32
+    contribution arrays (32 MB) fit the persisting L2 carve-out and need no L2
+    blocking.  Trials with the window off and on, graph loop, median times."""
+    import torch
+
+    import gapgen
+    from paper_1508_03619_gb300 import gap, tuning
+    scale = 22
+    src, dst = gapgen.urand_device(1 << scale, 16 << scale, 0x22, device=dev)
+    g = gap.Graph.from_edges(1 << scale, src, dst, symmetrize=False)
+    del src, dst
+    x = torch.empty(g.n, dtype=torch.float32, device=dev)
+    out = {"workload": f"urand{scale} directed, degree 16, FP32 pull PageRank to tol 1e-4 (whole rows, "
+                       f"no L2 blocking)", "n": g.n, "m": g.m}
+    for win in (0, 1):
+        o = tuning.pagerank_options()
+        o.l2_window = win
+        for _ in range(3):
+            gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, o, x)
+            gap.gap_pr_stats(g.handle)
+        ms, it = [], 0
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, o, x)
+            e1.record()
+            _, st = gap.gap_pr_stats(g.handle)
+            ms.append(e0.elapsed_time(e1))
+            it = st["iterations"]
+        med = sorted(ms)[len(ms) // 2]
+        out["on" if win else "off"] = {"ms_per_trial": med, "iterations": it,
+                                       "value": g.m * it / (med / 1e3) / 1e9, "unit": UNIT,
+                                       "window_bytes": st["l2_window_bytes"]}
+    out["speedup"] = out["off"]["ms_per_trial"] / out["on"]["ms_per_trial"]
+    g.close()
+    del x
+    torch.cuda.empty_cache()
+    return out
 
 
 # Bytes per vertex that one CC trial moves at the least (init 4; two sampling
