@@ -77,6 +77,7 @@ __device__ __forceinline__ float gather_c(const float* p) { return *p; }
 __device__ __forceinline__ int load_idx(const int32_t* p) { return __ldcs(p); }
 
 constexpr unsigned long long BARRIER_WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr int TILE_LANE_ROWS_MAX = 8;  // light tiles whose rows all have <= 8 in-arcs: a lane per row
 constexpr double DELTA_SCALE = 1152921504606846976.0;           // 2^60
 constexpr double DELTA_UNIT = 1.0 / DELTA_SCALE;
 
@@ -139,8 +140,11 @@ __device__ __forceinline__ unsigned long long to_fixed(double v) {
 // warp-merge (the tile's arcs taken 32 at a time in vertex order; each lane
 // finds its row by binary search over the exclusive degree scan; a keyed warp
 // scan forms per-row partials; the row's last lane in the batch hands its
-// partial to the row's owner lane).  Returns the tile's |x' - x| (FP64) in
-// every lane.
+// partial to the row's owner lane).  UB batches of 32 arcs are loaded before
+// any is summed, so UB gathers per lane are in flight; the batches' partials
+// are still added to each row in batch order.  Returns the tile's |x' - x|
+// (FP64) in every lane.
+template <int UB>
 __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float d, int heavy) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
@@ -161,30 +165,49 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
   const int excl = incl - dd;
   const int total = __shfl_sync(FULL, incl, 31);
   float acc = 0.f;
-  for (int b0 = 0; b0 < total; b0 += 32) {
-    const int j = b0 + lane;
-    int rr = 0;  // last row whose exclusive start is <= j
+  if (__reduce_max_sync(FULL, (unsigned)dd) <= TILE_LANE_ROWS_MAX) {
+    // every light row of the tile has at most TILE_LANE_ROWS_MAX in-arcs (road-like
+    // graphs): each lane sums its own row, all its gathers in flight at once,
+    // in arc order (adding 0 past the row's end changes nothing)
+    float vv[TILE_LANE_ROWS_MAX];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int cand = rr + step;
-      const int ex = __shfl_sync(FULL, excl, cand & 31);
-      if (cand < 32 && ex <= j) rr = cand;
-    }
-    const int64_t rbr = __shfl_sync(FULL, rb, rr);
-    const int exr = __shfl_sync(FULL, excl, rr);
-    float val = 0.f;
-    if (j < total) val = gather_c(cin + load_idx(G.idx + rbr + (j - exr)));
-    float xs = val;
+    for (int k = 0; k < TILE_LANE_ROWS_MAX; ++k) vv[k] = k < dd ? gather_c(cin + load_idx(G.idx + rb + k)) : 0.f;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float t = __shfl_up_sync(FULL, xs, o);
-      const int ro = __shfl_up_sync(FULL, rr, o);
-      if (lane >= o && ro == rr) xs = __fadd_rn(xs, t);
+    for (int k = 0; k < TILE_LANE_ROWS_MAX; ++k) acc = __fadd_rn(acc, vv[k]);
+  } else
+  for (int base = 0; base < total; base += 32 * UB) {
+    int r[UB];
+    float val[UB];
+#pragma unroll
+    for (int q = 0; q < UB; ++q) {
+      const int j = base + q * 32 + lane;
+      int rr = 0;  // last row whose exclusive start is <= j
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = rr + step;
+        const int ex = __shfl_sync(FULL, excl, cand & 31);
+        if (cand < 32 && ex <= j) rr = cand;
+      }
+      r[q] = rr;
+      const int64_t rbr = __shfl_sync(FULL, rb, rr);
+      const int exr = __shfl_sync(FULL, excl, rr);
+      val[q] = j < total ? gather_c(cin + load_idx(G.idx + rbr + (j - exr))) : 0.f;
     }
-    const bool inter = dd > 0 && excl < b0 + 32 && incl > b0;
-    const int tl = (incl < b0 + 32 ? incl : b0 + 32) - 1 - b0;
-    const float part = __shfl_sync(FULL, xs, inter ? tl : lane);
-    if (inter) acc = __fadd_rn(acc, part);
+#pragma unroll
+    for (int q = 0; q < UB; ++q) {
+      const int b0 = base + q * 32;
+      float xs = val[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(FULL, xs, o);
+        const int ro = __shfl_up_sync(FULL, r[q], o);
+        if (lane >= o && ro == r[q]) xs = __fadd_rn(xs, t);
+      }
+      const bool inter = dd > 0 && excl < b0 + 32 && incl > b0;
+      const int tl = (incl < b0 + 32 ? incl : b0 + 32) - 1 - b0;
+      const float part = __shfl_sync(FULL, xs, inter ? tl : lane);
+      if (inter) acc = __fadd_rn(acc, part);
+    }
   }
   double dl = 0.0;
   if (mine) {
@@ -296,8 +319,11 @@ __global__ void k_batch_plan(int ng, const int64_t* __restrict__ tile_prefix, co
 
 // ---- the persistent kernel ----------------------------------------------------
 
+// The 512-thread kernel is held to three resident blocks per SM (<= 42
+// registers a thread): the loop is bound by memory latency, and with an open
+// register budget the compiler took 56 registers, leaving two blocks per SM.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batch_persistent(
+__global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_persistent(
     const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ task_base,
     const int64_t* __restrict__ chunk_base, const ChunkDesc* __restrict__ desc, float* partial, unsigned int* ctr,
     unsigned long long* acc /* [3][ng] */, BatchGraphState* st, BatchCtrl* ctrl, float d, double tol,
@@ -318,14 +344,15 @@ __global__ void __launch_bounds__(THREADS) k_batch_persistent(
   for (int it = 0; it < max_iters; ++it) {
     const int parity = it & 1;
     unsigned long long* acc_now = acc + (int64_t)(it % 3) * ng;
+    int i = 0;
     for (int64_t task = warp; task < ntasks; task += nwarps) {
-      const int i = find_graph(task_base, ng, task);
+      while (i + 1 < ng && __ldg(task_base + i + 1) <= task) ++i;  // a warp's tasks only move forward
       if (!((active[i >> 5] >> (i & 31)) & 1u)) continue;  // warp-uniform
       const BatchGraph& G = gs[i];
       const int64_t local = task - __ldg(task_base + i);
       double dl;
       if (local < G.tiles) {
-        dl = pull_tile(G, local, parity, d, heavy);
+        dl = pull_tile<1>(G, local, parity, d, heavy);
       } else {
         const int64_t cid = __ldg(chunk_base + i) + (local - G.tiles);
         dl = pull_chunk(G, desc[cid], cid, partial, ctr, parity, d);
