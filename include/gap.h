@@ -404,7 +404,14 @@ GAP_API gap_status gap_ppr_batch(gap_graph_t* g, int32_t q, const int64_t* seed_
  * tol (or max_iters), copying its scores out.  The column count is the
  * largest power of two <= max_cols (<= 128) whose buffers fit in the free HBM
  * minus hbm_reserve; creation fails with GAP_ERR_OOM if even 4 columns do not
- * fit.  A query's result does not depend on the other queries in flight. */
+ * fit.  From 16 columns up the narrow engine (a quarter of the columns) is
+ * allocated at creation and the wide one only when the load first needs it,
+ * and only if the free HBM minus hbm_reserve holds it at that moment and the
+ * allocator (gap_set_allocator) hands out its blocks; otherwise queries keep
+ * being admitted into the narrow engine's columns as they free up, and the
+ * wide engine is tried again (at most every 50 ms).  A wide engine unused for
+ * 2 s is released.  A query's result does not depend on the other queries in
+ * flight, nor on the engine it ran in. */
 typedef struct gap_ppr_server gap_ppr_server_t;
 typedef struct {
   int32_t iterations;
@@ -455,6 +462,12 @@ typedef struct {
   int64_t switches;       /* width changes so far */
   int64_t completed;
   int64_t steps;          /* engine iterations so far */
+  int32_t wide_ready;     /* 1 while the wide engine's memory is allocated */
+  int32_t pad2;
+  int64_t grow_refused;   /* times the wide engine was wanted but did not fit the free
+                             HBM minus the reserve, or the allocator refused it */
+  int64_t wide_allocs;    /* times the wide engine was allocated */
+  int64_t wide_releases;  /* times it was released after 2 s unused */
 } gap_ppr_server_info_t;
 GAP_API gap_status gap_ppr_server_info_ex(gap_ppr_server_t* s, gap_ppr_server_info_t* out);
 /* Stop the worker (queries not yet completed are abandoned: their out

@@ -372,6 +372,8 @@ __global__ void k_ppr_stop_all(PprCtrl* c, int KP) {
 gap_status ppr_engine_init(PprEngine* e, gap_graph* g, int kp, double d, cudaStream_t s) {
   e->g = g;
   e->KP = kp;
+  e->parity = 0;  // an engine may be initialized again after a release
+  e->resident = 0;
   e->mask_words = (kp + 31) / 32;
   e->d = d;
   e->nblocks = (g->n + PPR_ROWS - 1) / PPR_ROWS;

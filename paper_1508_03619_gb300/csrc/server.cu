@@ -21,6 +21,13 @@
 // moves down.  A move carries a column's scores, the contributions its next
 // iteration reads, its seed bit and its control state, so its result is
 // unchanged.
+//
+// Admission by free HBM: the narrow engine is allocated at creation; the wide
+// one only when the load first needs it, and only if at that moment the free
+// HBM minus the caller's reserve holds it (and the allocator hands out its
+// blocks).  While it does not fit, the server keeps serving on the narrow
+// engine (queries wait for its columns) and tries again at most every 50 ms.
+// A wide engine left unused for 2 s is released, giving its memory back.
 #include <algorithm>
 #include <cstring>
 #include <chrono>
@@ -81,6 +88,11 @@ struct gap_ppr_server {
   std::deque<std::chrono::steady_clock::time_point> arrivals;  // submits of the last second
   double t_iter[2] = {0.0, 0.0};  // measured seconds per iteration: [0] wide, [1] narrow
   double iters_per_query = 0.0;   // measured
+  size_t hbm_reserve = 0;
+  double wide_bytes = 0.0;        // device bytes the wide engine takes
+  bool wide_ready = false;        // the wide engine is allocated
+  int64_t grow_refused = 0, wide_allocs = 0, wide_releases = 0;
+  std::chrono::steady_clock::time_point last_grow_try{}, narrow_since{};
   cudaStream_t s = nullptr;
   std::thread worker;
   std::mutex mu;
@@ -116,6 +128,55 @@ static void srv_update_preference(gap_ppr_server* S) {
   else if (!S->prefer_narrow && rate < 0.7 * cap) S->prefer_narrow = true;
 }
 
+constexpr double SERVER_GROW_RETRY_S = 0.05;
+constexpr double SERVER_WIDE_IDLE_S = 2.0;
+
+// Allocates the wide engine when the free HBM (minus the reserve) holds it and
+// the allocator provides its blocks; a refusal leaves the server as it was.
+// Caller holds S->mu, between iterations.
+static gap_status srv_grow(gap_ppr_server* S) {
+  if (S->wide_ready) return GAP_OK;
+  const auto now = std::chrono::steady_clock::now();
+  if (S->wide_allocs + S->grow_refused > 0 &&
+      std::chrono::duration<double>(now - S->last_grow_try).count() < SERVER_GROW_RETRY_S)
+    return GAP_OK;
+  S->last_grow_try = now;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  if (S->wide_bytes + (double)S->hbm_reserve > (double)free_b) {
+    ++S->grow_refused;
+    return GAP_OK;
+  }
+  const gap_status st = ppr_engine_init(&S->eng, S->g, ppr_width_for(S->cols), S->d, S->s);
+  if (st == GAP_ERR_OOM) {  // the allocator refused: stay narrow
+    ppr_engine_release(&S->eng);
+    clear_error();
+    ++S->grow_refused;
+    return GAP_OK;
+  }
+  GAP_TRY(st);
+  GAP_CUDA(cudaStreamSynchronize(S->s));
+  S->wide_ready = true;
+  ++S->wide_allocs;
+  return GAP_OK;
+}
+
+// Gives the wide engine's memory back after SERVER_WIDE_IDLE_S on the narrow
+// engine.  Caller holds S->mu, between iterations.
+static gap_status srv_shrink(gap_ppr_server* S) {
+  if (!S->wide_ready || !S->narrow || S->ncols == 0) return GAP_OK;
+  const double idle = std::chrono::duration<double>(std::chrono::steady_clock::now() - S->narrow_since).count();
+  if (idle < SERVER_WIDE_IDLE_S) return GAP_OK;
+  GAP_CUDA(cudaStreamSynchronize(S->s));  // nothing in flight reads it
+  ppr_engine_release(&S->eng);
+  S->wide_ready = false;
+  ++S->wide_releases;
+  return GAP_OK;
+}
+
 static gap_status srv_switch(gap_ppr_server* S) {
   if (S->ncols == 0) return GAP_OK;
   srv_update_preference(S);
@@ -128,7 +189,12 @@ static gap_status srv_switch(gap_ppr_server* S) {
   std::vector<int32_t> from, to;
   if (S->narrow) {
     const bool overflow = live + waiting > S->ncols;
-    if ((overflow && !S->prefer_narrow) || waiting > 2 * S->ncols) {  // up: same column numbers
+    bool up = (overflow && !S->prefer_narrow) || waiting > 2 * S->ncols;
+    if (up) {
+      GAP_TRY(srv_grow(S));  // admission by free HBM: the wide engine must fit now
+      up = S->wide_ready;
+    }
+    if (up) {  // up: same column numbers
       for (int c = 0; c < S->ncols; ++c)
         if (S->slot[c]) {
           from.push_back(c);
@@ -146,8 +212,10 @@ static gap_status srv_switch(gap_ppr_server* S) {
       }
     GAP_TRY(ppr_engine_move_columns(&S->eng, &S->neng, from.data(), to.data(), (int)from.size(), S->s));
     S->narrow = 1;
+    S->narrow_since = std::chrono::steady_clock::now();
     ++S->switches;
   }
+  if (S->narrow) GAP_TRY(srv_shrink(S));
   return GAP_OK;
 }
 
@@ -229,7 +297,21 @@ static void srv_loop(gap_ppr_server* S) {
           if (r) return true;
         return false;
       };
-      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || busy(); });
+      while (!S->stop && S->pending.empty() && !busy()) {
+        // idle: wake up now and then to give an unused wide engine back
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(250));
+        if (!S->narrow && S->ncols > 0 && S->pending.empty() && !busy()) {  // nothing to move down
+          S->narrow = 1;
+          S->narrow_since = std::chrono::steady_clock::now();
+          ++S->switches;
+        }
+        if (srv_shrink(S) != GAP_OK) {
+          S->worker_status = GAP_ERR_CUDA;
+          S->stop = true;
+          S->cv_done.notify_all();
+          return;
+        }
+      }
       if (S->stop) return;
       gap_status st = srv_admit(S);
       if (st != GAP_OK) {
@@ -323,10 +405,17 @@ gap_status gap_ppr_server_create(gap_graph_t* g, int32_t max_cols, size_t hbm_re
   S->cols = std::min<int32_t>(max_cols, kp);
   S->ncols = narrow_for(S->cols);
   S->narrow = S->ncols > 0;
+  S->hbm_reserve = hbm_reserve;
+  S->wide_bytes = engine_bytes(ppr_width_for(S->cols));
+  S->narrow_since = std::chrono::steady_clock::now();
   gap_status st = GAP_OK;
   do {
     if (cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking) != cudaSuccess) { st = GAP_ERR_CUDA; break; }
-    if ((st = ppr_engine_init(&S->eng, g, kp, damping, S->s)) != GAP_OK) break;
+    if (S->ncols == 0) {  // one width only: it is allocated now
+      if ((st = ppr_engine_init(&S->eng, g, kp, damping, S->s)) != GAP_OK) break;
+      S->wide_ready = true;
+      S->wide_allocs = 1;
+    }
     if (S->ncols && (st = ppr_engine_init(&S->neng, g, ppr_width_for(S->ncols), damping, S->s)) != GAP_OK) break;
     if (cudaMalloc(&S->seed_dev, sizeof(int32_t) * SERVER_MAX_SEEDS * kp) != cudaSuccess ||
         cudaMalloc(&S->cols_dev, sizeof(int32_t) * kp) != cudaSuccess ||
@@ -382,6 +471,10 @@ gap_status gap_ppr_server_info_ex(gap_ppr_server_t* S, gap_ppr_server_info_t* ou
   out->switches = S->switches;
   out->completed = S->completed;
   out->steps = S->steps;
+  out->wide_ready = S->wide_ready ? 1 : 0;
+  out->grow_refused = S->grow_refused;
+  out->wide_allocs = S->wide_allocs;
+  out->wide_releases = S->wide_releases;
   return S->worker_status;
 }
 

@@ -127,10 +127,12 @@ class gap_ppr_query_info_t(ctypes.Structure):
 class gap_ppr_server_info_t(ctypes.Structure):
     _fields_ = [("columns", ctypes.c_int32), ("narrow_columns", ctypes.c_int32), ("narrow", ctypes.c_int32),
                 ("live", ctypes.c_int32), ("waiting", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("switches", ctypes.c_int64), ("completed", ctypes.c_int64), ("steps", ctypes.c_int64)]
+                ("switches", ctypes.c_int64), ("completed", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("wide_ready", ctypes.c_int32), ("pad2", ctypes.c_int32), ("grow_refused", ctypes.c_int64),
+                ("wide_allocs", ctypes.c_int64), ("wide_releases", ctypes.c_int64)]
 
     def to_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
 
 
 class gap_cc_stats_t(ctypes.Structure):

@@ -140,3 +140,113 @@ def test_server_width_changes_keep_results(cuda_device):
     finally:
         srv.close()
         g.close()
+
+
+class BudgetAllocator:
+    """Scratch blocks from torch's caching allocator within a byte budget the
+    test moves while the server runs: a block that would pass the budget is
+    refused (NULL), which the library sees as out of memory."""
+
+    def __init__(self):
+        import threading
+
+        import torch
+        self.torch = torch
+        self.lock = threading.Lock()
+        self.budget = None
+        self.used = 0
+        self.live = {}
+        self.refused = 0
+        self._a = gap.gap_allocator.ALLOC(self._alloc)
+        self._f = gap.gap_allocator.FREE(self._free)
+        self.c = gap.gap_allocator(self._a, self._f, None)
+
+    def _alloc(self, nbytes, stream, ctx):
+        with self.lock:
+            if self.budget is not None and self.used + nbytes > self.budget:
+                self.refused += 1
+                return None
+            t = self.torch.empty(nbytes, dtype=self.torch.uint8, device="cuda")
+            self.live[t.data_ptr()] = (t, nbytes)
+            self.used += nbytes
+            return t.data_ptr()
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        with self.lock:
+            _, nb = self.live.pop(ptr)
+            self.used -= nb
+
+
+def test_server_admission_by_free_memory(cuda_device):
+    """The wide engine is allocated only when the load needs it and the memory
+    is there at that moment.  With no room for it, a burst far beyond the
+    narrow width is served by the narrow engine alone (the growth is refused);
+    once room appears, the next burst moves up into a newly allocated wide
+    engine; 2 s after the load is gone the wide engine is released and its
+    memory returned.  Every query equals the same query run alone bit for bit,
+    and a sample matches the oracle within the FP32 bars."""
+    import torch
+
+    import oracle
+    from gpu_helpers import FP32_L1, FP32_REL
+    n = 1 << 12
+    src, dst = gapgen.kron(12, 16, 0x65)
+    off, idx = oracle_graph(n, src, dst, True)
+    cand = np.flatnonzero(np.diff(off) > 0)
+    rng = np.random.default_rng(7)
+    g = gpu_graph(n, src, dst, True)
+    alloc = BudgetAllocator()
+    queries, outs, infos = [], [], []
+    gap.gap_set_allocator(alloc.c)
+    try:
+        srv = gap.PprServer(g.handle, max_cols=16, damping=D, tol=1e-4, max_iters=100)
+        try:
+            i0 = srv.info()
+            assert i0["narrow"] == 1 and i0["narrow_columns"] == 4 and i0["wide_ready"] == 0
+            narrow_bytes = alloc.used
+
+            def burst(k):
+                tickets = []
+                for _ in range(k):
+                    seeds = rng.choice(cand, size=int(rng.integers(1, 20))).astype(np.int32)
+                    out = torch.zeros(n, dtype=torch.float32, device="cuda:0")
+                    queries.append(seeds)
+                    outs.append(out)
+                    tickets.append(srv.submit(seeds, out))
+                infos.extend(srv.wait(t) for t in tickets)
+
+            alloc.budget = alloc.used  # no room for the wide engine
+            burst(30)
+            s1 = srv.info()
+            assert s1["completed"] == 30 and s1["grow_refused"] >= 1
+            assert s1["wide_ready"] == 0 and s1["wide_allocs"] == 0 and s1["switches"] == 0
+            assert alloc.refused >= 1 and alloc.used == narrow_bytes
+            alloc.budget = None  # room again
+            time.sleep(0.06)
+            burst(30)
+            s2 = srv.info()
+            assert s2["completed"] == 60 and s2["wide_allocs"] == 1 and s2["switches"] >= 1
+            assert alloc.used > narrow_bytes or s2["wide_releases"] == 1
+            time.sleep(3.0)  # idle: the unused wide engine goes back
+            s3 = srv.info()
+            assert s3["wide_ready"] == 0 and s3["wide_releases"] == 1 and s3["narrow"] == 1
+            assert alloc.used == narrow_bytes
+        finally:
+            srv.close()
+    finally:
+        gap.gap_set_allocator(None)
+    try:
+        for j, (seeds, out, info) in enumerate(zip(queries, outs, infos)):
+            ref, st = alone(g, seeds)
+            assert info["iterations"] == st["iterations"] and info["converged"]
+            assert np.array_equal(out.cpu().numpy(), ref)
+            if j % 10 == 0:  # unreachable vertices score exactly 0 on both sides
+                xo, _, _ = oracle.ppr(off, idx, seeds, D, 0.0, info["iterations"])
+                x = out.cpu().numpy().astype(np.float64)
+                reach = xo > 0
+                assert np.all(x[~reach] == 0.0)
+                assert np.abs(x - xo).sum() <= FP32_L1
+                big = xo > 1e-6  # the bar the batch PPR tests apply
+                assert np.max(np.abs(x[big] - xo[big]) / xo[big]) <= FP32_REL
+    finally:
+        g.close()
