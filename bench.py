@@ -408,6 +408,14 @@ def error_vs_oracle(proc, out, gpu):
     files = {k - 1: "x_prev", k: "x_stop", k + 1: "x_next"}
     cache = {}
     for name, (x, iters) in gpu.items():
+        if iters is None:  # not an iterate of the classical iteration: against the oracle's stop iterate
+            xo = cache.get("x_stop")
+            if xo is None:
+                xo = cache["x_stop"] = np.load(os.path.join(out, "x_stop.npy"))
+            diff = np.abs(x - xo)
+            res[name] = {"l1_vs_oracle_stop_iterate": float(diff.sum()),
+                         "note": "both within d tol / (1 - d) of the fixed point"}
+            continue
         f = files.get(iters)
         if f is None or not os.path.exists(os.path.join(out, f + ".npy")):
             res[name] = {"iterations": iters, "l1": None, "max_rel": None,
@@ -568,6 +576,31 @@ def run_pagerank(a, ws, rank, local, dev, pg, oracle_proc=None):
                         "in-arcs; 'ladder' switches to FP32 contributions once delta <= 2^-10")
         del xb
 
+    # ---- residual algorithm (rounds of pulls or frontier pushes) on the same graph ----
+    delta = None
+    if not a.no_fp64:
+        od = options()
+        od.algorithm = gap.GAP_ALGO_DELTA
+        xd = torch.empty(n, dtype=torch.float32, device=dev)
+        gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, od, xd)
+        gap.gap_pr_stats(g.handle)
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kd = max(1, min(3, a.steps))
+        d0.record(stream)
+        for _ in range(kd):
+            gap.gap_pr_run_ex(g.handle, DAMPING, TOL, MAX_ITERS, od, xd)
+            _, sd = gap.gap_pr_stats(g.handle)
+        d1.record(stream)
+        torch.cuda.synchronize(dev)
+        dms = d0.elapsed_time(d1) / kd
+        delta = {"ms_per_trial": dms, "vs_pull_trial": (ms / a.steps) / dms, "rounds": sd["iterations"],
+                 "sparse_rounds": sd["sparse_rounds"], "arcs_traversed": sd["arcs_traversed"],
+                 "pull_arcs_traversed": m * iters[-1], "final_residual": sd["final_delta"],
+                 "note": "options.algorithm = GAP_ALGO_DELTA: stops on the exact residual sum |J(x) - x| < tol "
+                         "and returns J(x); a round pulls d P r or pushes a frontier's residual"}
+        gpu_results["delta"] = (xd.double().cpu().numpy(), None)
+        del xd
+
     cc = bfs = None
     if a.workload == "all":
         cc = measure_cc(g, dev, stream, max(1, a.steps), max(3, a.warmup), a.graph != "urand")
@@ -595,7 +628,7 @@ def run_pagerank(a, ws, rank, local, dev, pg, oracle_proc=None):
                       "median": sorted(trial_ms)[len(trial_ms) // 2],
                       "note": "each trial: allocation, binning, iterations to tol, output (paper §2.3); "
                               "the stats read between trials is outside these events"},
-        "roofline": roofline, "fp64": fp64, "bf16": bf16,
+        "roofline": roofline, "fp64": fp64, "bf16": bf16, "delta": delta,
     }
     if oracle_err is not None:
         line["error_vs_oracle"] = oracle_err

@@ -229,6 +229,16 @@ GAP_API gap_status gap_pr_run_f64(gap_graph_t* g, double damping, double tol, in
 #define GAP_LOOP_HOST 1u    /* host loop: one synchronization per iteration */
 #define GAP_NO_LADDER INT32_MIN
 #define GAP_ALGO_PULL 0u   /* pull over the CSC (§3): degree-binned gather-SpMV (default) */
+#define GAP_ALGO_DELTA 2u  /* residual iteration: keeps r = J(x) - x (J: one classical
+                              iteration) exactly and stops when sum |r| < tol, returning
+                              x + r, whose one-more-iteration change is at most
+                              d * sum |r|.  A round either pulls r <- d P r through the
+                              same kernels as GAP_ALGO_PULL (after x += r), or, when the
+                              vertices holding 90 % of the residual mass own at most a
+                              fifth of the arcs, pushes only their residuals along
+                              out-arcs (float atomics: run-to-run order noise).  FP32
+                              only; gap_pr_stats_t.iterations counts rounds and
+                              arcs_traversed the arcs they touched */
 #define GAP_ALGO_BINNED 1u /* propagation blocking: each iteration scatters (value,
                               target) pairs from the out-direction CSR into target
                               bins of 32768 vertices, then sums every bin in shared
@@ -259,10 +269,11 @@ typedef struct {
   int64_t small_max_degree; /* rows with at most this many in-edges are pulled in vertex
                                order by the warp-merge kernel (0 = default 64; at most
                                512, and 255 when L2 blocking is active) */
-  uint32_t algorithm;     /* GAP_ALGO_PULL | GAP_ALGO_BINNED; BINNED with FP64, BF16
-                             contributions, deterministic or > 2^27 vertices returns
-                             GAP_ERR_UNSUPPORTED.  With BINNED, phase_ms[PULL0] is the
-                             scatter and phase_ms[PULL1] the binned sums */
+  uint32_t algorithm;     /* GAP_ALGO_PULL | GAP_ALGO_BINNED | GAP_ALGO_DELTA; BINNED or DELTA
+                             with FP64, BF16 contributions or deterministic, and BINNED
+                             with > 2^27 vertices, return GAP_ERR_UNSUPPORTED.  With
+                             BINNED, phase_ms[PULL0] is the scatter and phase_ms[PULL1]
+                             the binned sums */
   uint32_t group_lanes;   /* lanes per row of bin 4: 8 or 32 (0 = 32 for whole rows,
                              8 when L2 blocking is active) */
   int64_t group_max_degree; /* upper in-degree of bin 4 (0 = 2048, or 512 when L2
@@ -314,6 +325,10 @@ typedef struct {
   int32_t kernel_launches; /* CUDA kernels this run launched (set by gap_pr_stats) */
   int32_t pad0;
   int64_t l2_window_bytes; /* bytes marked persisting in L2 (options.l2_window), 0 if none */
+  int64_t arcs_traversed;  /* arcs the run gathered or pushed over (every round of every
+                              algorithm; GAP_ALGO_DELTA's sparse rounds touch fewer) */
+  int32_t sparse_rounds;   /* GAP_ALGO_DELTA: rounds that pushed a frontier only */
+  int32_t pad1;
 } gap_pr_stats_t;
 
 /* Synchronize the stream of the last run on g and report it.  Returns GAP_OK,

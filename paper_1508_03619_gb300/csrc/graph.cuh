@@ -37,6 +37,8 @@ struct gap_graph {
   int32_t last_segments = 1;             // bin plan of the last run
   int64_t last_l2_window = 0;            // bytes the last run marked persisting in L2
   int l2_reset_pending = 0;              // persisting lines to release once that run is done
+  int64_t last_arcs = -1;                // arcs the last run touched (-1: m per iteration)
+  int32_t last_sparse_rounds = 0;        // frontier-only rounds of the last residual run
   // last connected-components run on this graph
   void* cc_host = nullptr;  // pinned copy of the run's device control block
   cudaStream_t cc_stream = nullptr;

@@ -1090,6 +1090,114 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
   if (threadIdx.x == 0) ctrl->st.mass = s;
 }
 
+// ---- residual iteration (options.algorithm = GAP_ALGO_DELTA, FP32) -----------
+// State: scores x and r = J(x) - x, J the classical iteration (paper §2.1
+// equation).  J is affine, so moving r into x and pushing it on keeps the
+// invariant exactly: with F a set of vertices, x' = x + r_F and
+// r' = r - r_F + d P r_F (P r_F: each u in F sends r(u)/|N+(u)| along its
+// out-arcs, a vertex without out-arcs sends nothing, as in the equation).  A
+// round with F = V is the pull r' = d P r; a round with a small F pushes only
+// F's out-arcs.  The run stops when sum |r| < tol and returns x + r = J(x),
+// whose one-more-iteration change d P r is at most d * sum |r| in L1.
+constexpr int DELTA_BUCKETS = 64;
+constexpr double DELTA_FIX = 1152921504606846976.0;  // 2^60: fixed-point residual mass
+constexpr double DELTA_MASS_FRACTION = 0.9;          // a frontier carries this much of sum |r|
+constexpr double DELTA_SPARSE_ARCS = 0.2;            // ... and is pushed when its out-arcs <= this * m
+
+struct DeltaState {
+  unsigned long long mass[DELTA_BUCKETS];  // sum |r| per magnitude bucket, units of 2^-60 (exact, order-free)
+  unsigned long long cost[DELTA_BUCKETS];  // out-arcs of the bucket's vertices
+  unsigned long long count;                // frontier size of a sparse round
+  unsigned long long pad;
+};
+
+// Bucket b holds |r| in [2^(-b-1), 2^-b); the smallest magnitudes share bucket 63.
+__device__ __forceinline__ int delta_bucket(float a) {
+  int e;
+  frexpf(a, &e);
+  return e > 0 ? 0 : (-e > DELTA_BUCKETS - 1 ? DELTA_BUCKETS - 1 : -e);
+}
+
+__global__ void k_delta_setup(PrCtrl* ctrl) {
+  if (threadIdx.x == 0) ctrl->zero_fill_until = INT32_MAX;  // every row is written in every round
+}
+
+__global__ void __launch_bounds__(256) k_delta_hist(const float* __restrict__ r, const int32_t* __restrict__ outdeg,
+                                                    int64_t n, DeltaState* st) {
+  __shared__ unsigned long long sm[DELTA_BUCKETS], sc[DELTA_BUCKETS];
+  for (int b = threadIdx.x; b < DELTA_BUCKETS; b += blockDim.x) sm[b] = sc[b] = 0ull;
+  __syncthreads();
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const float a = fabsf(r[v]);
+    if (a > 0.f) {
+      const int b = delta_bucket(a);
+      atomicAdd(&sm[b], (unsigned long long)__double2ull_rn((double)a * DELTA_FIX));
+      atomicAdd(&sc[b], (unsigned long long)outdeg[v]);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < DELTA_BUCKETS; b += blockDim.x) {
+    if (sm[b]) atomicAdd(&st->mass[b], sm[b]);
+    if (sc[b]) atomicAdd(&st->cost[b], sc[b]);
+  }
+}
+
+// Frontier of a sparse round: vertices whose |r| falls in buckets 0..B.  Their
+// r moves into x; those with out-arcs are listed with the share d r(u)/|N+(u)|
+// each out-neighbour receives.
+__global__ void k_delta_frontier(float* __restrict__ x, float* __restrict__ r, const int32_t* __restrict__ outdeg,
+                                 int64_t n, int B, float d, int32_t* __restrict__ list, float* __restrict__ share,
+                                 DeltaState* st) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const float rv = r[v];
+    if (rv == 0.f || delta_bucket(fabsf(rv)) > B) continue;
+    x[v] = __fadd_rn(x[v], rv);
+    r[v] = 0.f;
+    const int32_t deg = outdeg[v];
+    if (deg > 0) {
+      const unsigned long long k = atomicAdd(&st->count, 1ull);
+      list[k] = (int32_t)v;
+      share[k] = __fmul_rn(d, rv) / (float)deg;
+    }
+  }
+}
+
+// One warp per frontier vertex adds its share to every out-neighbour's r.
+__global__ void __launch_bounds__(256) k_delta_push(const int32_t* __restrict__ list, const float* __restrict__ share,
+                                                    const DeltaState* st, const int64_t* __restrict__ ooff,
+                                                    const int32_t* __restrict__ oidx, float* r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t cnt = (int64_t)st->count;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t u = list[i];
+    const float p = share[i];
+    for (int64_t j = ooff[u] + lane; j < ooff[u + 1]; j += 32) atomicAdd(r + oidx[j], p);
+  }
+}
+
+// Before a pull round: x += r, and the contributions the round gathers are r/|N+(u)|.
+__global__ void k_delta_prep(float* __restrict__ x, const float* __restrict__ r, const int32_t* __restrict__ outdeg,
+                             int64_t n, const PrCtrl* ctrl, float* c0, float* c1) {
+  float* cin = (ctrl->iter & 1) ? c1 : c0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const float rv = r[v];
+    x[v] = __fadd_rn(x[v], rv);
+    const int32_t deg = outdeg[v];
+    cin[v] = deg > 0 ? rv / (float)deg : 0.f;
+  }
+}
+
+__global__ void k_delta_round_end(PrCtrl* ctrl) {
+  if (threadIdx.x == 0) ctrl->iter += 1;  // the next pull round reads the other contribution buffer
+}
+
+// Output: x + r.
+__global__ void k_delta_finish(float* __restrict__ x, const float* __restrict__ r, int64_t n) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    x[v] = __fadd_rn(x[v], r[v]);
+}
+
 // ---- host orchestration ------------------------------------------------------
 
 constexpr int64_t DEFAULT_SEGMENT_BYTES = 32ll << 20;  // GB300: ~126 MB of L2 over two dies
@@ -1561,6 +1669,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   a.kahan_thr = o.hub_threshold;
   double* pbase = partial.as<double>();
 
+  bool skip_finalize = false;  // the residual iteration takes its own stop decision
   auto launch_body = [&](cudaStream_t ls, cudaGraphConditionalHandle h, int use_h) -> gap_status {
     for (const LaunchRec& r : plan) {
       PrArgs<Acc> b = a;
@@ -1617,6 +1726,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
       GAP_LAUNCH_CHECK();
       tm.end(phase, tk);
     }
+    if (skip_finalize) return GAP_OK;
     int tk = tm.begin();
     k_finalize<<<1, 1024, 0, ls>>>(dctrl, pbase, np, tol, max_iters, h, use_h);
     GAP_LAUNCH_CHECK();
@@ -1624,12 +1734,97 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     return GAP_OK;
   };
 
+  // ---- residual iteration (GAP_ALGO_DELTA): rounds driven from the host ----
+  const bool delta = std::is_same<Acc, float>::value && o.algorithm == GAP_ALGO_DELTA;
+  std::vector<double> delta_hist;
+  int64_t delta_arcs = 0;
+  int32_t delta_sparse = 0;
+  if constexpr (std::is_same<Acc, float>::value) {
+    if (delta && max_iters > 0) {
+      nv.next("pr_iterations");
+      Scratch rbuf, dst, flist, fshare;
+      GAP_TRY(rbuf.get(sizeof(float) * n, s));
+      GAP_TRY(dst.get(sizeof(DeltaState), s));
+      GAP_TRY(flist.get(sizeof(int32_t) * n, s));
+      GAP_TRY(fshare.get(sizeof(float) * n, s));
+      const int64_t* ooff = nullptr;
+      const int32_t* oidx = nullptr;
+      GAP_TRY(graph_out_csr(g, s, &ooff, &oidx));  // the graph's out-direction (built once per graph)
+      float* r = rbuf.as<float>();
+      DeltaState hs;
+      const int eg = stride_grid(n, 256, 8);
+      k_delta_setup<<<1, 32, 0, s>>>(dctrl);
+      GAP_LAUNCH_CHECK();
+      // round 1: r = J(x0) - x0, one pull with base (1-d)/n - x0 into r (x = x0, c0 = x0/|N+|)
+      skip_finalize = true;
+      a.x = r;
+      a.base = (float)((1.0 - d) / (double)n - 1.0 / (double)n);
+      GAP_TRY(launch_body(s, 0, 0));
+      k_delta_round_end<<<1, 32, 0, s>>>(dctrl);
+      GAP_LAUNCH_CHECK();
+      delta_arcs += g->m;
+      a.base = 0.f;
+      for (int32_t round = 1;; ++round) {
+        GAP_CUDA(cudaMemsetAsync(dst.p, 0, sizeof(DeltaState), s));
+        k_delta_hist<<<eg, 256, 0, s>>>(r, g->outdeg, n, dst.as<DeltaState>());
+        GAP_LAUNCH_CHECK();
+        GAP_CUDA(cudaMemcpyAsync(&hs, dst.p, sizeof(DeltaState), cudaMemcpyDeviceToHost, s));
+        GAP_CUDA(cudaStreamSynchronize(s));
+        tm.collect();
+        double total = 0.0;
+        for (int b = 0; b < DELTA_BUCKETS; ++b) total += (double)hs.mass[b];
+        const double R = total / DELTA_FIX;
+        delta_hist.push_back(R);
+        if (R < tol || round >= max_iters) break;
+        // the frontier: the largest-|r| buckets that carry DELTA_MASS_FRACTION of the mass
+        int B = 0;
+        double cm = 0.0, cost = 0.0;
+        for (; B < DELTA_BUCKETS; ++B) {
+          cm += (double)hs.mass[B];
+          cost += (double)hs.cost[B];
+          if (cm >= DELTA_MASS_FRACTION * total) break;
+        }
+        if (B >= DELTA_BUCKETS) B = DELTA_BUCKETS - 1;
+        if (cost <= DELTA_SPARSE_ARCS * (double)g->m) {  // push the frontier's out-arcs only
+          int tk = tm.begin();
+          k_delta_frontier<<<eg, 256, 0, s>>>(x, r, g->outdeg, n, B, (float)d, flist.as<int32_t>(),
+                                              fshare.as<float>(), dst.as<DeltaState>());
+          GAP_LAUNCH_CHECK();
+          k_delta_push<<<stride_grid(n, 256, 8), 256, 0, s>>>(flist.as<int32_t>(), fshare.as<float>(),
+                                                              dst.as<DeltaState>(), ooff, oidx, r);
+          GAP_LAUNCH_CHECK();
+          tm.end(GAP_PHASE_PULL0, tk);
+          delta_arcs += (int64_t)cost;
+          ++delta_sparse;
+        } else {  // x += r, then r <- d P r through the pull kernels
+          int tk = tm.begin();
+          k_delta_prep<<<eg, 256, 0, s>>>(x, r, g->outdeg, n, dctrl, static_cast<float*>(c0),
+                                          static_cast<float*>(c1));
+          GAP_LAUNCH_CHECK();
+          tm.end(GAP_PHASE_INIT, tk);
+          GAP_TRY(launch_body(s, 0, 0));
+          k_delta_round_end<<<1, 32, 0, s>>>(dctrl);
+          GAP_LAUNCH_CHECK();
+          delta_arcs += g->m;
+        }
+      }
+      k_delta_finish<<<eg, 256, 0, s>>>(x, r, n);
+      GAP_LAUNCH_CHECK();
+      a.x = x;
+      GAP_CUDA(cudaStreamSynchronize(s));  // r and the frontier buffers are released below
+    }
+  }
+
   cudaAccessPolicyWindow win;
-  const size_t win_bytes = (o.l2_window && S == 1) ? l2_window_setup(cbuf.p, 2 * (bf16 ? xbytes / 2 : xbytes), &win)
-                                                   : 0;
-  nv.next("pr_iterations");
-  GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing != 0,
-                     win_bytes ? &win : nullptr));
+
+  const size_t win_bytes = (o.l2_window && S == 1 && !delta)
+                               ? l2_window_setup(cbuf.p, 2 * (bf16 ? xbytes / 2 : xbytes), &win)
+                               : 0;
+  if (!delta) {
+    nv.next("pr_iterations");
+    GAP_TRY(drive_loop(g, s, max_iters, dctrl, tm, launch_body, o.loop == GAP_LOOP_HOST || o.timing != 0,
+                       win_bytes ? &win : nullptr));
+  }
   nv.next("pr_output");
 
   // ---- output + stats ----
@@ -1646,13 +1841,24 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   if (!user_dev) GAP_CUDA(cudaMemcpyAsync(user_scores, x, xbytes, cudaMemcpyDefault, s));
   tm.end(GAP_PHASE_OUTPUT, tok);
   GAP_CUDA(cudaMemcpyAsync(g->stats_host, &dctrl->st, sizeof(gap_pr_stats_t), cudaMemcpyDeviceToHost, s));
-  if (tm.on) {
+  if (tm.on || delta) {
     GAP_CUDA(cudaStreamSynchronize(s));
     tm.collect();
     for (int q = 0; q < GAP_PR_PHASES; ++q) {
       g->stats_host->phase_ms[q] = tm.ms[q];
       g->stats_host->phase_launches[q] = tm.launches[q];
     }
+  }
+  g->last_arcs = -1;
+  g->last_sparse_rounds = 0;
+  if (delta) {  // rounds, residual history and stop come from the host loop
+    gap_pr_stats_t* st = g->stats_host;
+    st->iterations = (int32_t)delta_hist.size();
+    for (size_t k = 0; k < delta_hist.size() && k < GAP_PR_HIST; ++k) st->delta_hist[k] = delta_hist[k];
+    st->final_delta = delta_hist.empty() ? 0.0 : delta_hist.back();
+    st->converged = !delta_hist.empty() && delta_hist.back() < tol;
+    g->last_arcs = delta_arcs;
+    g->last_sparse_rounds = delta_sparse;
   }
   // host-side facts of this run, merged into the stats by gap_pr_stats()
   int per_iter = 1;  // finalize
@@ -2064,7 +2270,15 @@ gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max
     set_error("deterministic mode is defined for F64 precision");
     return GAP_ERR_UNSUPPORTED;
   }
-  if (o.algorithm != GAP_ALGO_PULL && o.algorithm != GAP_ALGO_BINNED) { set_error("bad algorithm"); return GAP_ERR_INVALID_ARG; }
+  if (o.algorithm != GAP_ALGO_PULL && o.algorithm != GAP_ALGO_BINNED && o.algorithm != GAP_ALGO_DELTA) {
+    set_error("bad algorithm");
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (o.algorithm == GAP_ALGO_DELTA &&
+      (o.precision != GAP_PREC_F32 || o.contrib != GAP_CONTRIB_F32 || o.deterministic)) {
+    set_error("the residual algorithm runs FP32 scores with FP32 contributions only");
+    return GAP_ERR_UNSUPPORTED;
+  }
   if ((o.group_lanes != 0 && o.group_lanes != 8 && o.group_lanes != 32) || o.group_max_degree < 0 ||
       o.cta_max_degree < 0 || (o.hub_chunk_arcs != 0 && (o.hub_chunk_arcs < 1024 || o.hub_chunk_arcs > (1 << 24)))) {
     set_error("bad bin options (group_lanes 8 or 32, degrees >= 0, hub_chunk_arcs in [1024, 2^24])");
@@ -2107,6 +2321,8 @@ gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out) {
   out->kernel_launches = g->launches_fixed + out->iterations * g->launches_per_iter;
   out->segments = g->last_segments;
   out->l2_window_bytes = g->last_l2_window;
+  out->arcs_traversed = g->last_arcs >= 0 ? g->last_arcs : g->m * (int64_t)out->iterations;
+  out->sparse_rounds = g->last_sparse_rounds;
   if (g->l2_reset_pending) {  // the run is over: its persisting lines become normal again
     cudaCtxResetPersistingL2Cache();
     cudaGetLastError();

@@ -64,6 +64,7 @@ GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
 GAP_ALGO_PULL = 0
 GAP_ALGO_BINNED = 1
+GAP_ALGO_DELTA = 2
 
 
 class gap_batch_tuning(ctypes.Structure):
@@ -97,7 +98,8 @@ class gap_pr_stats_t(ctypes.Structure):
                 ("phase_ms", ctypes.c_double * GAP_PR_PHASES),
                 ("phase_launches", ctypes.c_int32 * GAP_PR_PHASES),
                 ("kernel_launches", ctypes.c_int32), ("pad0", ctypes.c_int32),
-                ("l2_window_bytes", ctypes.c_int64)]
+                ("l2_window_bytes", ctypes.c_int64), ("arcs_traversed", ctypes.c_int64),
+                ("sparse_rounds", ctypes.c_int32), ("pad1", ctypes.c_int32)]
 
     def to_dict(self):
         k = min(self.iterations, GAP_PR_HIST)
@@ -111,7 +113,8 @@ class gap_pr_stats_t(ctypes.Structure):
                 "phase_ms": dict(zip(PHASE_NAMES, self.phase_ms)),
                 "phase_launches": dict(zip(PHASE_NAMES, self.phase_launches)),
                 "kernel_launches": self.kernel_launches,
-                "l2_window_bytes": self.l2_window_bytes}
+                "l2_window_bytes": self.l2_window_bytes, "arcs_traversed": self.arcs_traversed,
+                "sparse_rounds": self.sparse_rounds}
 
 
 class gap_ppr_query_info_t(ctypes.Structure):

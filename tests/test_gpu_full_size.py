@@ -7,6 +7,8 @@ oracle's own CSR (its row-partitioned builder, identical to the serial one):
   - FP64: L1 <= 1e-12 against the oracle's iterate of the same count;
   - BF16 contributions with the FP32 ladder: converged, the §3 verifier
     < 1e-4, errors against the oracle's iterate of the same count printed;
+  - the residual algorithm (GAP_ALGO_DELTA): the §3 verifier < 1e-4 and L1 to
+    the oracle's iterate within 2 d tol / (1 - d);
   - every score >= (1-d)/n, the FP64 mass matches the scores, mass <= 1."""
 import os
 
@@ -96,13 +98,21 @@ def test_full_size_against_oracle(cuda_device, kind):
         v32 = oracle.verify(off, idx, x32, D)
         vbf = oracle.verify(off, idx, xbf, D)
         assert v32 < 1e-4 and vbf < 1e-4, (v32, vbf)
+        # the residual algorithm: the paper's criterion, and within twice the
+        # contraction bound d*tol/(1-d) of the oracle's own converged iterate
+        xdl, stdl = gpu_run(g, n, algorithm=gap.GAP_ALGO_DELTA)
+        vdl = oracle.verify(off, idx, xdl, D)
+        l1_dl = float(np.abs(xdl - x_t).sum())
+        assert vdl < 1e-4 and l1_dl <= 2 * D * 1e-4 / (1 - D), (vdl, l1_dl)
         base = (1 - D) / n
         assert x32.min() >= base * (1 - 1e-6)
         assert abs(st32["mass"] - x32.sum()) <= 1e-9 and st32["mass"] <= 1 + 1e-5
         print(f"{kind}: m={g.m} iterations fp32/fp64/bf16 {st32['iterations']}/{st64['iterations']}/"
               f"{stbf['iterations']} (oracle {k_t}); vs oracle: fp32 L1 {l1:.3e} rel {rel:.3e}, "
               f"fp64 L1 {l1_64:.3e}, bf16-ladder L1 {l1_bf:.3e} rel {rel_bf:.3e}; "
-              f"verifier fp32 {v32:.3e} bf16 {vbf:.3e}")
+              f"verifier fp32 {v32:.3e} bf16 {vbf:.3e}; residual algorithm {stdl['iterations']} rounds "
+              f"({stdl['sparse_rounds']} sparse), {stdl['arcs_traversed'] / g.m:.2f} m arcs, verifier "
+              f"{vdl:.3e}, L1 to the oracle {l1_dl:.3e}")
     finally:
         g.close()
 

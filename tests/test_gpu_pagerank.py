@@ -295,6 +295,60 @@ def test_l2_window_engages_and_changes_no_result(cuda_device):
         g.close()
 
 
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_delta_algorithm_meets_the_criterion(cuda_device, case, seg):
+    """options.algorithm = GAP_ALGO_DELTA (residual rounds, pull or frontier
+    push): the returned scores pass the paper's §3 verifier (< 1e-4), and lie
+    within d*tol/(1-d) (+ FP32 noise) of the oracle's converged vector in L1 --
+    the bound a residual below tol gives, since one iteration contracts by d.
+    The stats report rounds, the residual history and the arcs touched."""
+    name, n, src, dst, sym = case
+    off, idx = oracle_graph(n, src, dst, sym)
+    x_star, _, _ = oracle.pagerank(off, idx, D, 1e-13, 1000)
+    g = gpu_graph(n, src, dst, sym)
+    try:
+        tol = 1e-4
+        x, st, status = run_gpu(g, tol, 100, algorithm=gap.GAP_ALGO_DELTA,
+                                segment_bytes=seg_bytes_for(n) if seg else 0)
+        assert status == gap.GAP_OK and st["converged"] and st["final_delta"] < tol
+        assert st["segments"] > 1 if seg else st["segments"] == 1
+        v = oracle.verify(off, idx, x, D)
+        assert v < tol, v
+        l1 = np.abs(x - x_star).sum()
+        assert l1 <= D * tol / (1 - D) + 1e-5, l1
+        assert 0 < st["arcs_traversed"] <= st["iterations"] * g.m
+        assert len(st["deltas"]) == st["iterations"] and st["deltas"][-1] == st["final_delta"]
+        print(f"{name} seg={seg}: rounds {st['iterations']} (sparse {st['sparse_rounds']}), "
+              f"arcs {st['arcs_traversed']} = {st['arcs_traversed'] / g.m:.2f} m, verifier {v:.2e}, "
+              f"L1 to x* {l1:.2e}")
+        # a pull run of the same graph touches m arcs per iteration
+        _, sp, _ = run_gpu(g, tol, 100, segment_bytes=seg_bytes_for(n) if seg else 0)
+        assert sp["arcs_traversed"] == sp["iterations"] * g.m and sp["sparse_rounds"] == 0
+    finally:
+        g.close()
+
+
+def test_delta_algorithm_edges(cuda_device):
+    """No rounds at max_iters = 0 (x0 returned); an empty graph; FP64 or BF16
+    with the residual algorithm are refused."""
+    import torch
+    n = 1000
+    g = gpu_graph(n, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    try:
+        x, st, _ = run_gpu(g, 1e-4, 0, algorithm=gap.GAP_ALGO_DELTA)
+        assert st["iterations"] == 0 and np.allclose(x, 1.0 / n)
+        x, st, _ = run_gpu(g, 1e-4, 100, algorithm=gap.GAP_ALGO_DELTA)
+        assert st["converged"] and np.allclose(x, (1 - D) / n, rtol=1e-6)  # every vertex isolated
+        for bad in ({"precision": gap.GAP_PREC_F64}, {"contrib": gap.GAP_CONTRIB_BF16}):
+            with pytest.raises(gap.GapError) as e:
+                run_gpu(g, 1e-4, 10, algorithm=gap.GAP_ALGO_DELTA, f64=bad.get("precision") is not None,
+                        **{k: v for k, v in bad.items() if k != "precision"})
+            assert e.value.status == gap.GAP_ERR_UNSUPPORTED
+    finally:
+        g.close()
+
+
 @pytest.mark.parametrize("case", ["urand_directed", "kron_sym", "ragged_bins"])
 def test_binned_algorithm_fp32_parity(cuda_device, case):
     """options.algorithm = GAP_ALGO_BINNED (scatter into target bins, shared-
