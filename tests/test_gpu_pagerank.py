@@ -329,6 +329,46 @@ def test_delta_algorithm_meets_the_criterion(cuda_device, case, seg):
         g.close()
 
 
+@pytest.mark.parametrize("case", ["path", "kron_and_path"])
+def test_delta_algorithm_frontier_rounds(cuda_device, case):
+    """Graphs whose residual stays local, so the residual algorithm pushes
+    frontiers along out-arcs: a directed path (from x0 = 1/n only its first
+    vertex has a residual, which travels one arc per round), and a Kronecker
+    graph with a long directed path beside it.  The paper's criterion (§3
+    verifier) and the contraction bound to the oracle's fixed point hold at
+    tol 1e-6; the frontier rounds touch fewer arcs than full rounds would."""
+    if case == "path":
+        n = 4096
+        src = np.arange(n - 1, dtype=np.int32)
+        dst = src + 1
+    else:
+        k = 1 << 12
+        ks, kd = gapgen.kron(12, 16, 0x33)
+        ks = np.concatenate([ks, kd]).astype(np.int32)  # symmetric Kronecker part
+        kd = np.concatenate([kd, gapgen.kron(12, 16, 0x33)[0]]).astype(np.int32)
+        p = np.arange(k, 2 * k - 1, dtype=np.int32)
+        n = 2 * k
+        src = np.concatenate([ks, p])
+        dst = np.concatenate([kd, p + 1])
+    off, idx = oracle_graph(n, src, dst, False)
+    x_star, _, _ = oracle.pagerank(off, idx, D, 1e-14, 2000)
+    g = gpu_graph(n, src, dst, False)
+    try:
+        tol = 1e-6
+        for seg in (0, seg_bytes_for(n)):
+            x, st, status = run_gpu(g, tol, 1000, algorithm=gap.GAP_ALGO_DELTA, segment_bytes=seg)
+            assert status == gap.GAP_OK and st["converged"]
+            assert st["sparse_rounds"] >= 1
+            assert st["arcs_traversed"] < st["iterations"] * g.m
+            v = oracle.verify(off, idx, x, D)
+            l1 = np.abs(x - x_star).sum()
+            assert v < tol and l1 <= D * tol / (1 - D) + 1e-6, (v, l1)
+            print(f"{case} seg={seg}: rounds {st['iterations']} (sparse {st['sparse_rounds']}), arcs "
+                  f"{st['arcs_traversed'] / g.m:.2f} m, verifier {v:.2e}, L1 to x* {l1:.2e}")
+    finally:
+        g.close()
+
+
 def test_delta_algorithm_edges(cuda_device):
     """No rounds at max_iters = 0 (x0 returned); an empty graph; FP64 or BF16
     with the residual algorithm are refused."""
