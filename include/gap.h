@@ -282,6 +282,13 @@ typedef struct {
                                pulled in chunks */
   int64_t hub_chunk_arcs;   /* arcs per hub chunk, in [1024, 2^24] (0 = 32768, or 4096
                                when L2 blocking is active) */
+  uint32_t check_worklists; /* 1: before the iterations, validate the work lists the trial
+                               built on the device (degree-bin list a permutation with
+                               every row in its bin, segment split points, packed
+                               small-row arcs, hub chunk tables); a violation returns
+                               GAP_ERR_BOUNDS naming the list and position, and no pull
+                               kernel runs.  Debug aid: one extra pass over the lists */
+  uint32_t reserved1;       /* must be 0 */
 } gap_pr_options;
 
 /* Fill *o with the defaults: F32, FP32 contributions, no ladder, Kahan hubs on
@@ -565,6 +572,28 @@ GAP_API gap_status gap_bfs_stats(gap_graph_t* g, gap_bfs_stats_t* out);
  * No fault is raised and the context stays usable.  Synchronous.
  * Returns GAP_OK when the self-test ran; INVALID_ARG (NULL), OOM, CUDA. */
 GAP_API gap_status gap_selftest_barrier_timeout(int32_t* observed, double* waited_ms, void* stream);
+
+/* The paper has no counterpart.  Self-tests of the work-list validators that
+ * options.check_worklists runs inside a trial: each runs one validator on
+ * lists the caller provides (device memory), which no pull kernel reads, and
+ * reports the first violation: *code = 0 (valid) or the check that failed
+ * (1 entry outside [0,n), 2 vertex listed twice, 3 row in the wrong bin,
+ * 6 packed source outside its segment, 7 packed row invalid or not small),
+ * *where = its position.  Synchronous.  Returns GAP_OK when the check ran;
+ * INVALID_ARG (NULL, n < 1, S < 1, wbits outside [0,31]), OOM, CUDA.
+ *  - bin list: off int64[n+1] (CSC offsets), list int32[n]; bin_start (host)
+ *    GAP_PR_BINS+1 positions (bin q holds list[bin_start[q] .. bin_start[q+1]),
+ *    bin_start[GAP_PR_BINS] = n); bin_hi (host) GAP_PR_BINS-1 inclusive upper
+ *    in-degrees (a row belongs to the first bin whose bound is not below it).
+ *  - packed arcs: packed / prow int32[seg_end[S-1]] (source and row of each
+ *    arc), seg_end int64[S] (end of each segment's arcs), sources of segment
+ *    s in [s * 2^wbits, (s+1) * 2^wbits), rows of in-degree <= small_max. */
+GAP_API gap_status gap_selftest_check_bin_list(int64_t n, const int64_t* off, const int32_t* list,
+                                               const int64_t* bin_start, const int64_t* bin_hi, int32_t* code,
+                                               int64_t* where, void* stream);
+GAP_API gap_status gap_selftest_check_packed(int64_t n, const int64_t* off, const int32_t* packed,
+                                             const int32_t* prow, const int64_t* seg_end, int32_t S, int32_t wbits,
+                                             int64_t small_max, int32_t* code, int64_t* where, void* stream);
 
 /* ------------------------------------------------- no-allocation variant --- */
 /* The paper has no counterpart to this entry point.  It serves callers that

@@ -1090,6 +1090,131 @@ __global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, i
   if (threadIdx.x == 0) ctrl->st.mass = s;
 }
 
+// ---- work-list checks (options.check_worklists) ------------------------------
+// The degree bins, segment split points, packed small-row arcs and hub chunk
+// tables are built on the device in every trial; with the option set, these
+// validators read them before any pull kernel does and record the first
+// violation.  Every index a validator follows has been range-checked first.
+enum CheckCode {
+  CHK_OK = 0,
+  CHK_LIST_RANGE = 1,   // a bin list entry outside [0, n)
+  CHK_LIST_TWICE = 2,   // a vertex listed twice (so another is missing)
+  CHK_LIST_BIN = 3,     // a row listed in a bin its in-degree does not belong to
+  CHK_SPLIT = 4,        // split points not monotone, past the row or not ending at its length
+  CHK_SPLIT_SOURCE = 5, // a segment's first or last source outside the segment
+  CHK_PACKED_SOURCE = 6, // a packed arc's source outside its segment (or outside [0, n))
+  CHK_PACKED_ROW = 7,   // a packed arc's row outside [0, n) or not a small row
+  CHK_HUB_CHUNKS = 8,   // a hub's chunk count does not match its (segment) length
+};
+
+struct CheckErr {
+  int32_t code;
+  int32_t pad;
+  unsigned long long where;
+};
+
+__device__ __forceinline__ void check_fail(CheckErr* e, int code, unsigned long long where) {
+  if (atomicCAS(&e->code, 0, code) == 0) e->where = where;
+}
+
+struct BinStart {
+  int64_t b[NBINS + 1];  // position of the first row of each bin in the list; b[NBINS] = n
+};
+
+__global__ void k_check_list(const int32_t* __restrict__ list, int64_t n, const int64_t* __restrict__ off,
+                             BinStart bs, BinHi hi, uint32_t* __restrict__ seen, CheckErr* e) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = list[i];
+    if (v < 0 || v >= n) {
+      check_fail(e, CHK_LIST_RANGE, (unsigned long long)i);
+      continue;
+    }
+    const uint32_t bit = 1u << (v & 31);
+    if (atomicOr(seen + (v >> 5), bit) & bit) check_fail(e, CHK_LIST_TWICE, (unsigned long long)i);
+    int q = 0;  // the bin whose positions hold i
+    while (q + 1 < NBINS && bs.b[q + 1] <= i) ++q;
+    if (bin_of(off[v + 1] - off[v], hi) != q) check_fail(e, CHK_LIST_BIN, (unsigned long long)i);
+  }
+}
+
+__global__ void k_check_split(const int32_t* __restrict__ list, int64_t base, int64_t rows,
+                              const int64_t* __restrict__ off, const int32_t* __restrict__ idx, int S, int wbits,
+                              const int64_t* __restrict__ rs, const int32_t* __restrict__ bnd, CheckErr* e) {
+  for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < rows;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = list[base + li];  // in range: the list check ran first
+    const int64_t r0 = off[v], deg = off[v + 1] - r0;
+    if (rs[li] != r0) {
+      check_fail(e, CHK_SPLIT, (unsigned long long)li);
+      continue;
+    }
+    int64_t prev = 0;
+    bool ok = true;
+    for (int k = 0; k < S && ok; ++k) {
+      const int64_t b = bnd[li * S + k];
+      if (b < prev || b > deg || (k + 1 == S && b != deg)) {
+        check_fail(e, CHK_SPLIT, (unsigned long long)li);
+        ok = false;
+      } else if (b > prev) {  // sources are sorted: the ends bound the whole sub-range
+        const int32_t u0 = idx[r0 + prev], u1 = idx[r0 + b - 1];
+        if ((u0 >> wbits) != k || (u1 >> wbits) != k) {
+          check_fail(e, CHK_SPLIT_SOURCE, (unsigned long long)li);
+          ok = false;
+        }
+      }
+      prev = b;
+    }
+  }
+}
+
+__global__ void k_check_packed(const int32_t* __restrict__ packed, const int32_t* __restrict__ prow,
+                               const int64_t* __restrict__ seg_end, int S, int wbits, int64_t n,
+                               const int64_t* __restrict__ off, int64_t small_max, CheckErr* e) {
+  const int64_t total = seg_end[S - 1];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+    int sg = 0;  // the segment whose range holds position j
+    while (sg + 1 < S && seg_end[sg] <= j) ++sg;
+    const int64_t u = packed[j];
+    if (u < 0 || u >= n || (u >> wbits) != sg) check_fail(e, CHK_PACKED_SOURCE, (unsigned long long)j);
+    const int64_t r = prow[j];
+    if (r < 0 || r >= n || off[r + 1] - off[r] > small_max) check_fail(e, CHK_PACKED_ROW, (unsigned long long)j);
+  }
+}
+
+// Hub h (rows list[hub0 + h]) must own ceil(len / chunk) chunks, len its row
+// length (bnd == nullptr) or its segment-s sub-range (segmented tables).
+__global__ void k_check_hubs(const int32_t* __restrict__ list, int64_t hub0, int64_t nh,
+                             const int64_t* __restrict__ off, const int32_t* __restrict__ bnd, int64_t hub_li0, int S,
+                             int s, int64_t chunk, const int64_t* __restrict__ cstart, CheckErr* e) {
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
+    int64_t len;
+    if (bnd) {
+      const int32_t* bd = bnd + (hub_li0 + h) * S;
+      len = (int64_t)bd[s] - (s ? (int64_t)bd[s - 1] : 0);
+    } else {
+      const int64_t v = list[hub0 + h];
+      len = off[v + 1] - off[v];
+    }
+    const int64_t want = (len + chunk - 1) / chunk;
+    if ((h == 0 && cstart[0] != 0) || cstart[h + 1] - cstart[h] != want)
+      check_fail(e, CHK_HUB_CHUNKS, (unsigned long long)h);
+  }
+}
+
+static const char* check_name(int code) {
+  switch (code) {
+    case CHK_LIST_RANGE: return "a bin list entry outside [0, n)";
+    case CHK_LIST_TWICE: return "a vertex listed twice in the bin lists";
+    case CHK_LIST_BIN: return "a row listed in the wrong degree bin";
+    case CHK_SPLIT: return "segment split points of a row inconsistent";
+    case CHK_SPLIT_SOURCE: return "a segment sub-range holding a source of another segment";
+    case CHK_PACKED_SOURCE: return "a packed small-row arc whose source lies outside its segment";
+    case CHK_PACKED_ROW: return "a packed small-row arc whose row is invalid or not small";
+    case CHK_HUB_CHUNKS: return "a hub chunk table inconsistent with the hub rows";
+    default: return "unknown check";
+  }
+}
+
 // ---- residual iteration (options.algorithm = GAP_ALGO_DELTA, FP32) -----------
 // State: scores x and r = J(x) - x, J the classical iteration (paper §2.1
 // equation).  J is affine, so moving r into x and pushing it on keeps the
@@ -1565,6 +1690,59 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   }
   tm.end(GAP_PHASE_PREP, tok);
   tm.collect();
+
+  // ---- optional: validate the work lists before any pull kernel reads them ----
+  if (o.check_worklists) {
+    Scratch cerr, seen;
+    GAP_TRY(cerr.get(sizeof(CheckErr), s));
+    GAP_TRY(seen.get(sizeof(uint32_t) * ((n + 31) / 32), s));
+    GAP_CUDA(cudaMemsetAsync(cerr.p, 0, sizeof(CheckErr), s));
+    GAP_CUDA(cudaMemsetAsync(seen.p, 0, sizeof(uint32_t) * ((n + 31) / 32), s));
+    BinStart bs;
+    for (int q = 0; q <= NBINS; ++q) bs.b[q] = mt[q];
+    CheckErr he;
+    k_check_list<<<stride_grid(n, 256, 8), 256, 0, s>>>(list.as<int32_t>(), n, g->in_off, bs, bh, seen.as<uint32_t>(),
+                                                        cerr.as<CheckErr>());
+    GAP_LAUNCH_CHECK();
+    GAP_CUDA(cudaMemcpyAsync(&he, cerr.p, sizeof(CheckErr), cudaMemcpyDeviceToHost, s));
+    GAP_CUDA(cudaStreamSynchronize(s));
+    if (he.code == 0) {  // the list is a permutation: the others may follow its entries
+      int wb = 0;
+      while ((int64_t(1) << wb) < t.seg_width) ++wb;
+      if (S > 1 && seg_rows > 0) {
+        k_check_split<<<stride_grid(seg_rows, 256, 8), 256, 0, s>>>(list.as<int32_t>(), seg_base, seg_rows, g->in_off,
+                                                                     g->in_idx, S, wb, sg.rs, sg.bnd, cerr.as<CheckErr>());
+        GAP_LAUNCH_CHECK();
+      }
+      if (small_packed) {
+        k_check_packed<<<stride_grid(g->m, 256, 8), 256, 0, s>>>(sm_packed.as<int32_t>(), sm_prow.as<int32_t>(),
+                                                                 sm_tend.as<int64_t>(), S, wb, n, g->in_off,
+                                                                 t.bin[BIN_ZERO].hi, cerr.as<CheckErr>());
+        GAP_LAUNCH_CHECK();
+      }
+      if (nhubs > 0) {
+        const int hg = stride_grid(nhubs, 256, 2);
+        if (S > 1) {
+          for (int sgi = 0; sgi < S; ++sgi) {
+            k_check_hubs<<<hg, 256, 0, s>>>(list.as<int32_t>(), mt[BIN_HUB], nhubs, g->in_off, sg.bnd,
+                                            mt[BIN_HUB] - seg_base, S, sgi, t.hub_chunk,
+                                            seg_cstart.as<int64_t>() + (int64_t)sgi * (nhubs + 1), cerr.as<CheckErr>());
+            GAP_LAUNCH_CHECK();
+          }
+        } else {
+          k_check_hubs<<<hg, 256, 0, s>>>(list.as<int32_t>(), mt[BIN_HUB], nhubs, g->in_off, nullptr, 0, 1, 0,
+                                          t.hub_chunk, cstart.as<int64_t>(), cerr.as<CheckErr>());
+          GAP_LAUNCH_CHECK();
+        }
+      }
+      GAP_CUDA(cudaMemcpyAsync(&he, cerr.p, sizeof(CheckErr), cudaMemcpyDeviceToHost, s));
+      GAP_CUDA(cudaStreamSynchronize(s));
+    }
+    if (he.code != 0) {
+      set_error("work-list check: %s (position %llu)", check_name(he.code), he.where);
+      return GAP_ERR_BOUNDS;
+    }
+  }
 
   // ---- launch plan of one iteration ----
   std::vector<LaunchRec> plan;
@@ -2250,6 +2428,8 @@ void gap_pr_options_default(gap_pr_options* o) {
   o->group_max_degree = 0;
   o->cta_max_degree = 0;
   o->hub_chunk_arcs = 0;
+  o->check_worklists = 0;
+  o->reserved1 = 0;
 }
 
 gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max_iters, const gap_pr_options* opt,
@@ -2272,6 +2452,10 @@ gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int32_t max
   }
   if (o.algorithm != GAP_ALGO_PULL && o.algorithm != GAP_ALGO_BINNED && o.algorithm != GAP_ALGO_DELTA) {
     set_error("bad algorithm");
+    return GAP_ERR_INVALID_ARG;
+  }
+  if (o.check_worklists > 1 || o.reserved1 != 0) {
+    set_error("check_worklists must be 0 or 1 and reserved1 0");
     return GAP_ERR_INVALID_ARG;
   }
   if (o.algorithm == GAP_ALGO_DELTA &&
@@ -2482,5 +2666,65 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
   g->last_stream = s;
   g->has_run = 1;
   g->last_tol = tol;
+  return GAP_OK;
+}
+
+// ============================================================================
+// Self-tests of the work-list validators (the paper has no counterpart): run
+// one validator on lists the caller provides, which no pull kernel reads.
+extern "C" gap_status gap_selftest_check_bin_list(int64_t n, const int64_t* off, const int32_t* list,
+                                                  const int64_t* bin_start, const int64_t* bin_hi, int32_t* code,
+                                                  int64_t* where, void* stream) {
+  using namespace gap;
+  clear_error();
+  if (n < 1 || !off || !list || !bin_start || !bin_hi || !code || !where) {
+    set_error("gap_selftest_check_bin_list: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BinStart bs;
+  BinHi hi;
+  for (int q = 0; q <= NBINS; ++q) bs.b[q] = bin_start[q];
+  for (int q = 0; q < NBINS - 1; ++q) hi.hi[q] = bin_hi[q];
+  Scratch cerr, seen;
+  GAP_TRY(cerr.get(sizeof(CheckErr), s));
+  GAP_TRY(seen.get(sizeof(uint32_t) * ((n + 31) / 32), s));
+  GAP_CUDA(cudaMemsetAsync(cerr.p, 0, sizeof(CheckErr), s));
+  GAP_CUDA(cudaMemsetAsync(seen.p, 0, sizeof(uint32_t) * ((n + 31) / 32), s));
+  k_check_list<<<stride_grid(n, 256, 8), 256, 0, s>>>(list, n, off, bs, hi, seen.as<uint32_t>(), cerr.as<CheckErr>());
+  GAP_LAUNCH_CHECK();
+  CheckErr he;
+  GAP_CUDA(cudaMemcpyAsync(&he, cerr.p, sizeof(CheckErr), cudaMemcpyDeviceToHost, s));
+  GAP_CUDA(cudaStreamSynchronize(s));
+  *code = he.code;
+  *where = (int64_t)he.where;
+  return GAP_OK;
+}
+
+extern "C" gap_status gap_selftest_check_packed(int64_t n, const int64_t* off, const int32_t* packed,
+                                                const int32_t* prow, const int64_t* seg_end, int32_t S,
+                                                int32_t wbits, int64_t small_max, int32_t* code, int64_t* where,
+                                                void* stream) {
+  using namespace gap;
+  clear_error();
+  if (n < 1 || !off || !packed || !prow || !seg_end || S < 1 || wbits < 0 || wbits > 31 || !code || !where) {
+    set_error("gap_selftest_check_packed: bad argument");
+    return GAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t total = 0;
+  GAP_CUDA(cudaMemcpyAsync(&total, seg_end + S - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GAP_CUDA(cudaStreamSynchronize(s));
+  Scratch cerr;
+  GAP_TRY(cerr.get(sizeof(CheckErr), s));
+  GAP_CUDA(cudaMemsetAsync(cerr.p, 0, sizeof(CheckErr), s));
+  k_check_packed<<<stride_grid(total > 0 ? total : 1, 256, 8), 256, 0, s>>>(packed, prow, seg_end, S, wbits, n, off,
+                                                                              small_max, cerr.as<CheckErr>());
+  GAP_LAUNCH_CHECK();
+  CheckErr he;
+  GAP_CUDA(cudaMemcpyAsync(&he, cerr.p, sizeof(CheckErr), cudaMemcpyDeviceToHost, s));
+  GAP_CUDA(cudaStreamSynchronize(s));
+  *code = he.code;
+  *where = (int64_t)he.where;
   return GAP_OK;
 }

@@ -59,6 +59,7 @@ EXPORTED = (
     "gap_edge_list_read", "gap_edge_list_info", "gap_edge_list_arrays", "gap_edge_list_destroy",
     "gap_graph_load", "gap_graph_save", "gap_graph_build_flags",
     "gap_cc_run", "gap_cc_stats", "gap_bfs_run", "gap_bfs_stats", "gap_selftest_barrier_timeout",
+    "gap_selftest_check_bin_list", "gap_selftest_check_packed",
 )
 GAP_NOALLOC_MAX_VERTICES = 1 << 20
 GAP_BATCH_MAX_GRAPHS = 65536
@@ -83,7 +84,8 @@ class gap_pr_options(ctypes.Structure):
                 ("timing", ctypes.c_uint32), ("segment_bytes", ctypes.c_int64),
                 ("small_max_degree", ctypes.c_int64), ("algorithm", ctypes.c_uint32),
                 ("group_lanes", ctypes.c_uint32), ("group_max_degree", ctypes.c_int64),
-                ("cta_max_degree", ctypes.c_int64), ("hub_chunk_arcs", ctypes.c_int64)]
+                ("cta_max_degree", ctypes.c_int64), ("hub_chunk_arcs", ctypes.c_int64),
+                ("check_worklists", ctypes.c_uint32), ("reserved1", ctypes.c_uint32)]
 
 
 class gap_pr_stats_t(ctypes.Structure):
@@ -223,6 +225,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_bfs_run": ([vp, i32, vp, vp], st),
         "gap_bfs_stats": ([vp, ctypes.POINTER(gap_bfs_stats_t)], st),
         "gap_selftest_barrier_timeout": ([ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], st),
+        "gap_selftest_check_bin_list": ([i64, vp, vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i64), vp], st),
+        "gap_selftest_check_packed": ([i64, vp, vp, vp, vp, i32, i32, i64, ctypes.POINTER(i32),
+                                       ctypes.POINTER(i64), vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -616,6 +621,42 @@ def bfs_sources(outdeg, count: int = 64, seed: int = 0x5EED):
 
 
 # ------------------------------------------------------- failure detection ---
+
+def _device_i(t, dtype_size, count, name):
+    """A contiguous CUDA integer tensor of `count` elements of `dtype_size` bytes."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and t.element_size() == dtype_size
+            and not t.is_floating_point() and t.numel() >= count):
+        raise ValueError(f"{name}: needs a contiguous CUDA integer tensor of {count} x {dtype_size}-byte elements")
+    return _ptr(t)
+
+
+def gap_selftest_check_bin_list(off, lst, bin_start, bin_hi, stream=None):
+    """Run the bin-list validator on caller lists; returns (code, where)."""
+    import numpy as np
+    n = int(lst.numel())
+    bs = np.ascontiguousarray(bin_start, np.int64)
+    hi = np.ascontiguousarray(bin_hi, np.int64)
+    if len(bs) != GAP_PR_BINS + 1 or len(hi) != GAP_PR_BINS - 1:
+        raise ValueError("bin_start needs GAP_PR_BINS + 1 entries and bin_hi GAP_PR_BINS - 1")
+    code, where = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().gap_selftest_check_bin_list(n, _device_i(off, 8, n + 1, "off"), _device_i(lst, 4, n, "list"),
+                                              _ptr(bs), _ptr(hi), ctypes.byref(code), ctypes.byref(where),
+                                              _stream(stream)), "gap_selftest_check_bin_list")
+    return code.value, where.value
+
+
+def gap_selftest_check_packed(off, packed, prow, seg_end, wbits, small_max, stream=None):
+    """Run the packed-arc validator on caller lists; returns (code, where)."""
+    n = int(off.numel()) - 1
+    S = int(seg_end.numel())
+    total = int(seg_end[-1].item()) if S else 0
+    code, where = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().gap_selftest_check_packed(n, _device_i(off, 8, n + 1, "off"), _device_i(packed, 4, total, "packed"),
+                                            _device_i(prow, 4, total, "prow"), _device_i(seg_end, 8, S, "seg_end"),
+                                            S, wbits, small_max, ctypes.byref(code), ctypes.byref(where),
+                                            _stream(stream)), "gap_selftest_check_packed")
+    return code.value, where.value
+
 
 def gap_selftest_barrier_timeout(stream=None):
     """Run the grid barrier's bounded-wait self-test; returns (observed status,

@@ -138,3 +138,91 @@ def test_grid_barrier_wait_runs_out_and_reports_timeout(cuda_device):
         xo, _, _ = oracle.pagerank(off, idx, D, 0.0, 20)
         assert st[0]["iterations"] == 20
         assert_fp32_parity(x[0].cpu().numpy().astype(np.float64), xo)
+
+
+def test_worklist_checks_pass_on_real_trials_and_change_nothing(cuda_device):
+    """options.check_worklists validates the trial's device-built work lists
+    (bin list, split points, packed small-row arcs, hub chunk tables) before the
+    iterations: on real graphs -- whole rows, L2 segments, hubs -- every check
+    passes and the scores equal an unchecked run bit for bit."""
+    import gapgen
+    from gpu_helpers import oracle_graph, run_gpu, seg_bytes_for
+    from test_gpu_pagerank import threshold_graph
+    n, src, dst = threshold_graph()
+    cases = [(n, src, dst, False), (1 << 14, *gapgen.kron(14, 16, 0x14), True)]
+    for n, src, dst, sym in cases:
+        g = gpu_graph(n, src, dst, sym)
+        try:
+            for seg in (0, seg_bytes_for(n)):
+                x0, st0, _ = run_gpu(g, 0.0, 6, segment_bytes=seg)
+                x1, st1, s1 = run_gpu(g, 0.0, 6, segment_bytes=seg, check_worklists=1)
+                assert s1 == gap.GAP_OK and np.array_equal(x0, x1)
+                assert st1["segments"] == st0["segments"]
+            if n == cases[0][0]:
+                assert st1["bins"][6]["rows"] > 0  # hub chunk tables were checked too
+        finally:
+            g.close()
+
+
+def test_worklist_validators_report_broken_lists(cuda_device):
+    """The validators report each kind of broken list (fed to them directly; no
+    pull kernel reads these lists): an entry outside [0, n), a vertex listed
+    twice, a row in the wrong bin, a packed source outside its segment, a
+    packed row outside [0, n) or not a small row; valid lists pass."""
+    import torch
+
+    import gapgen
+    from gpu_helpers import oracle_graph
+    n = 1024
+    src, dst = gapgen.kron(10, 16, 0x15)
+    off, idx = oracle_graph(n, dst, src, True)  # a CSC (symmetric anyway)
+    deg = np.diff(off)
+    hi = np.array([64, 64, 64, 64, 256, 512], np.int64)  # bins 0 (<= 64), 4 (<= 256), 5 (<= 512), 6
+    bins = np.searchsorted(hi, deg, side="left")         # first bin whose bound is not below the degree
+    order = np.argsort(bins, kind="stable").astype(np.int32)
+    bin_start = np.searchsorted(bins[order], np.arange(8)).astype(np.int64)
+    dev = torch.device("cuda:0")
+    t_off = torch.from_numpy(off).to(dev)
+
+    def check_list(lst):
+        return gap.gap_selftest_check_bin_list(t_off, torch.from_numpy(lst).to(dev), bin_start, hi)
+
+    assert check_list(order) == (0, 0)
+    bad = order.copy()
+    bad[5] = n + 7
+    assert check_list(bad) == (1, 5)
+    bad = order.copy()
+    bad[5] = bad[6]                # positions 5 and 6 share bin 0
+    assert check_list(bad)[0] == 2
+    big = int(np.flatnonzero(bins[order] == bins[order][-1])[0])
+    bad = order.copy()
+    bad[0], bad[big] = bad[big], bad[0]   # a bin-0 row and a top-bin row trade places
+    assert check_list(bad)[0] == 3
+
+    # packed small-row arcs, two segments of 512 sources
+    wbits, small_max = 9, 64
+    rows, srcs = [], []
+    for sg in range(2):
+        for v in range(n):
+            if deg[v] <= small_max:
+                for u in idx[off[v]:off[v + 1]]:
+                    if u >> wbits == sg:
+                        rows.append(v)
+                        srcs.append(u)
+    seg_end = np.array([sum(1 for u in srcs if u >> wbits == 0), len(srcs)], np.int64)
+
+    def check_packed(p, r):
+        return gap.gap_selftest_check_packed(t_off, torch.tensor(p, dtype=torch.int32, device=dev),
+                                             torch.tensor(r, dtype=torch.int32, device=dev),
+                                             torch.from_numpy(seg_end).to(dev), wbits, small_max)
+
+    assert check_packed(srcs, rows) == (0, 0)
+    p = list(srcs)
+    p[0] = 600                     # a segment-1 source among segment 0's arcs
+    assert check_packed(p, rows) == (6, 0)
+    r = list(rows)
+    r[1] = n + 5
+    assert check_packed(srcs, r) == (7, 1)
+    r = list(rows)
+    r[2] = int(np.flatnonzero(deg > small_max)[0])  # a row that is not small
+    assert check_packed(srcs, r) == (7, 2)
