@@ -495,23 +495,45 @@ def run_pagerank(a, ws, rank, local, dev, pg, oracle_proc=None):
     ms, arcs = combine_ranks(ms, m * sum(iters), pg, dev)
     value = arcs / (ms / 1e3) / 1e9
 
-    # ---- end to end through the C ABI with a pinned host output buffer ----
+    # ---- end to end through the C ABI: every step uploads the graph's CSR from
+    #      pinned host memory (gap_graph_create_csc: copy + device check), runs the
+    #      trial into pinned host scores, and releases the uploaded graph ----
     host_scores = torch.empty(n, dtype=torch.float32).pin_memory()
+    h_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    h_idx = torch.empty(m, dtype=torch.int32).pin_memory()
+    gap.gap_graph_export_csr(g.handle, 1, h_off, h_idx)
+    e_steps = max(1, min(a.steps, 8))
+    torch.cuda.synchronize(dev)
+    e_iters = []
+    t_e0 = time.perf_counter()
+    for _ in range(e_steps):
+        gu = gap.Graph.from_csc(n, h_off, h_idx)
+        gap.gap_pr_run_ex(gu.handle, DAMPING, TOL, MAX_ITERS, opts, host_scores)
+        _, st_e = gap.gap_pr_stats(gu.handle)  # the scores are on the host when it returns
+        e_iters.append(st_e["iterations"])
+        gu.close()
+    e_s = time.perf_counter() - t_e0
+    e2e = {"value": m * sum(e_iters) / e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n, "steps": e_steps,
+           "ms_per_step": e_s / e_steps * 1e3,
+           "note": "per step, host clock: the in-direction CSR uploaded from pinned host memory "
+                   "(gap_graph_create_csc: copy, device structure check, out-degrees), one trial into "
+                   "pinned host scores, the uploaded graph released"}
+    # the same trials with the graph kept on the device (paper §2.3: only the graph is reused)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_iters = []
+    r_iters = []
     e0.record(stream)
     for _ in range(a.steps):
         trial(host_scores)
-        _, st_e = gap.gap_pr_stats(g.handle)
-        e_iters.append(st_e["iterations"])
+        _, st_r = gap.gap_pr_stats(g.handle)
+        r_iters.append(st_r["iterations"])
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e_ms = e0.elapsed_time(e1)
-    e2e = {"value": m * sum(e_iters) / (e_ms / 1e3) / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n,
-           "note": "gap_pr_run into pinned host memory (D2H of the FP32 scores inside the step); "
-                   "the graph stays resident between trials (paper §2.3)"}
+    e2e["resident_graph"] = {"value": m * sum(r_iters) / (e0.elapsed_time(e1) / 1e3) / 1e9, "unit": UNIT,
+                             "d2h_bytes_per_step": 4 * n,
+                             "note": "gap_pr_run into pinned host memory, graph resident on the device"}
+    del h_off, h_idx
 
     # ---- per-kernel durations (CUDA events around every launch) ----
     prof = options()

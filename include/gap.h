@@ -114,6 +114,18 @@ GAP_API gap_status gap_graph_create(int64_t n, int64_t m, const int64_t* row_off
                             const int32_t* col_idx, uint32_t flags, void* stream,
                             gap_graph_t** out);
 
+/* A graph from a prebuilt in-direction CSR (row v lists the sources u of the
+ * arcs u->v, ascending), host or device memory: in_offsets int64[n+1] (0 ..
+ * m), in_idx int32[m].  The arrays are copied (the caller keeps ownership),
+ * checked on the device (offsets monotone in [0, m], sources in [0, n),
+ * non-decreasing within each row) and the out-degrees counted; no sorting or
+ * cleaning is done, so repeated arcs count as given.  This is how a CSR built
+ * elsewhere (or exported with gap_graph_export_csr) is handed back without a
+ * rebuild.  Errors: INVALID_ARG (n outside [1, 2^31-1], m < 0, NULL, or a CSR
+ * that fails the check, named in the message), OOM, CUDA.  Synchronous. */
+GAP_API gap_status gap_graph_create_csc(int64_t n, int64_t m, const int64_t* in_offsets, const int32_t* in_idx,
+                                        void* stream, gap_graph_t** out);
+
 /* n vertices, m stored arcs, and the number of vertices with out-degree 0. */
 GAP_API gap_status gap_graph_info(const gap_graph_t* g, int64_t* n, int64_t* m, int64_t* n_dangling);
 

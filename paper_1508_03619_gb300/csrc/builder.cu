@@ -5,6 +5,7 @@
 // utility shared with the degree binning.
 #include <stdlib.h>
 #include <string.h>
+#include <vector>
 
 #include "graph.cuh"
 #include "scan.cuh"
@@ -505,12 +506,16 @@ static gap_status build_from_device_edges(int64_t n, int64_t m, const int32_t* d
   return GAP_OK;
 }
 
-// Structure check of an adopted CSC, one thread per row: 0 <= off[v] <=
-// off[v+1] <= m, every source in [0, n), sources non-decreasing within a row
-// (the order the builder writes and the segment passes rely on).  Counts the
-// out-degrees as it goes.  Only in-bounds addresses are ever touched.
-__global__ void k_check_csc(const int64_t* __restrict__ off, const int32_t* __restrict__ idx, int64_t n,
-                            int64_t m, int32_t* __restrict__ outdeg, unsigned* __restrict__ err) {
+// Structure check of an adopted CSC in two coalesced passes (only in-bounds
+// addresses are ever touched):
+//   rows: 0 <= off[v] <= off[v+1] <= m (bit 1) and off[0] = 0, off[n] = m (the
+//         caller checks those two); each non-empty row marks its first arc in
+//         a bitmap of m bits;
+//   arcs: every source in [0, n) (bit 2), and non-decreasing within its row --
+//         each arc against its left neighbour unless it starts a row (bit 4);
+//         the out-degrees are counted on the way.
+__global__ void k_check_csc_rows(const int64_t* __restrict__ off, int64_t n, int64_t m,
+                                 unsigned* __restrict__ starts, unsigned* __restrict__ err) {
   unsigned bad = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = off[v], e = off[v + 1];
@@ -518,23 +523,63 @@ __global__ void k_check_csc(const int64_t* __restrict__ off, const int32_t* __re
       bad |= 1u;
       continue;
     }
-    int32_t prev = INT32_MIN;
-    for (int64_t i = b; i < e; ++i) {
-      const int32_t u = idx[i];
-      if (u < 0 || (int64_t)u >= n) {
-        bad |= 2u;
-        continue;
-      }
-      if (u < prev) bad |= 4u;
-      prev = u;
-      atomicAdd(outdeg + u, 1);
-    }
+    if (b < e) atomicOr(starts + (b >> 5), 1u << (b & 31));
   }
   if (bad) atomicOr(err, bad);
 }
 
+__global__ void k_check_csc_arcs(const int32_t* __restrict__ idx, int64_t n, int64_t j0, int64_t j1,
+                                 const unsigned* __restrict__ starts, int32_t* __restrict__ outdeg,
+                                 unsigned* __restrict__ err) {
+  unsigned bad = 0;
+  for (int64_t j = j0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < j1; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = idx[j];
+    if (u < 0 || (int64_t)u >= n) {
+      bad |= 2u;
+      continue;
+    }
+    atomicAdd(outdeg + u, 1);
+    if (j > 0 && !((starts[j >> 5] >> (j & 31)) & 1u) && idx[j - 1] > u) bad |= 4u;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+// Copies the column indices from host memory in chunks on a second stream; the
+// arcs of each chunk are checked on `s` as soon as it has landed, so the copy
+// and the check overlap.  An arc's left neighbour sits in an earlier chunk or
+// its own, both copied before its check runs.
+static gap_status upload_and_check_arcs(int32_t* d_idx, const int32_t* h_idx, int64_t n, int64_t m,
+                                        const unsigned* starts, int32_t* outdeg, unsigned* err, cudaStream_t s) {
+  constexpr int64_t CHUNK = int64_t(1) << 28;  // 1 GB of indices
+  cudaStream_t cs = nullptr;
+  GAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  std::vector<cudaEvent_t> evs;
+  gap_status st = GAP_OK;
+  for (int64_t c0 = 0; c0 < m && st == GAP_OK; c0 += CHUNK) {
+    const int64_t c1 = c0 + CHUNK < m ? c0 + CHUNK : m;
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__);
+      break;
+    }
+    evs.push_back(ev);
+    if (cudaMemcpyAsync(d_idx + c0, h_idx + c0, sizeof(int32_t) * (c1 - c0), cudaMemcpyDefault, cs) != cudaSuccess ||
+        cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "chunked upload", __FILE__, __LINE__);
+      break;
+    }
+    k_check_csc_arcs<<<stride_grid(c1 - c0, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(d_idx, n, c0, c1, starts, outdeg, err);
+    if (cudaGetLastError() != cudaSuccess) st = cuda_fail(cudaErrorLaunchFailure, "k_check_csc_arcs", __FILE__, __LINE__);
+  }
+  cudaStreamSynchronize(cs);
+  cudaStreamSynchronize(s);
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
 gap_status graph_from_csc(int64_t n, int64_t m, int64_t* d_off, int32_t* d_idx, uint32_t build_flags,
-                          cudaStream_t s, gap_graph** out) {
+                          cudaStream_t s, gap_graph** out, const int32_t* h_idx) {
   gap_graph* g = new gap_graph();
   g->n = n;
   g->m = m;
@@ -562,8 +607,21 @@ gap_status graph_from_csc(int64_t n, int64_t m, int64_t* d_off, int32_t* d_idx, 
       st = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
       break;
     }
-    k_check_csc<<<stride_grid(n, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(g->in_off, g->in_idx, n, m, g->outdeg, err);
-    if (cudaGetLastError() != cudaSuccess) { st = cuda_fail(cudaErrorLaunchFailure, "k_check_csc", __FILE__, __LINE__); break; }
+    Scratch starts;
+    if ((st = starts.get(sizeof(unsigned) * ((m + 31) / 32 + 1), s)) != GAP_OK) break;
+    if (cudaMemsetAsync(starts.p, 0, sizeof(unsigned) * ((m + 31) / 32 + 1), s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
+      break;
+    }
+    k_check_csc_rows<<<stride_grid(n, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(g->in_off, n, m, starts.as<unsigned>(), err);
+    if (cudaGetLastError() != cudaSuccess) { st = cuda_fail(cudaErrorLaunchFailure, "k_check_csc_rows", __FILE__, __LINE__); break; }
+    if (h_idx) {  // the indices are still on the host: upload them while checking
+      if ((st = upload_and_check_arcs(d_idx, h_idx, n, m, starts.as<unsigned>(), g->outdeg, err, s)) != GAP_OK) break;
+    } else {
+      k_check_csc_arcs<<<stride_grid(m > 0 ? m : 1, BLD_THREADS, 8), BLD_THREADS, 0, s>>>(
+          g->in_idx, n, 0, m, starts.as<unsigned>(), g->outdeg, err);
+      if (cudaGetLastError() != cudaSuccess) { st = cuda_fail(cudaErrorLaunchFailure, "k_check_csc_arcs", __FILE__, __LINE__); break; }
+    }
     unsigned herr = 0;
     if (cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -681,6 +739,47 @@ gap_status gap_graph_create(int64_t n, int64_t m, const int64_t* row_offsets, co
     return GAP_ERR_INVALID_ARG;
   }
   return build_from_device_edges(n, m, ds.as<int32_t>(), dd.as<int32_t>(), flags | GAP_INPUT_ON_DEVICE, s, out);
+}
+
+gap_status gap_graph_create_csc(int64_t n, int64_t m, const int64_t* in_offsets, const int32_t* in_idx, void* stream,
+                                gap_graph_t** out) {
+  GAP_TRY(check_create_args(n, m, in_offsets, m > 0 ? in_idx : (const int32_t*)in_offsets, out));
+  if (!in_offsets) {
+    set_error("in_offsets is NULL");
+    return GAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t* d_off = nullptr;
+  int32_t* d_idx = nullptr;
+  if (cudaMalloc(&d_off, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&d_idx, sizeof(int32_t) * (m > 0 ? m : 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d_off);
+    set_error("graph allocation failed");
+    return GAP_ERR_OOM;
+  }
+  int64_t ends[2] = {-1, -1};
+  // indices in host memory are uploaded in chunks while they are checked
+  const bool upload = m > 0 && !is_device_ptr(in_idx);
+  cudaError_t e = cudaMemcpyAsync(d_off, in_offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, s);
+  if (e == cudaSuccess && m > 0 && !upload)
+    e = cudaMemcpyAsync(d_idx, in_idx, sizeof(int32_t) * m, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[0], d_off, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], d_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(d_off);
+    cudaFree(d_idx);
+    return cuda_fail(e, "gap_graph_create_csc copies", __FILE__, __LINE__);
+  }
+  if (ends[0] != 0 || ends[1] != m) {
+    cudaFree(d_off);
+    cudaFree(d_idx);
+    set_error("in_offsets must start at 0 and end at m");
+    return GAP_ERR_INVALID_ARG;
+  }
+  // checks the structure, counts out-degrees
+  return graph_from_csc(n, m, d_off, d_idx, 0u, s, out, upload ? in_idx : nullptr);
 }
 
 gap_status gap_graph_info(const gap_graph_t* g, int64_t* n, int64_t* m, int64_t* n_dangling) {

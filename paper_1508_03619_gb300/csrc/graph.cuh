@@ -72,7 +72,9 @@ gap_status graph_out_csr(gap_graph* g, cudaStream_t s, const int64_t** off, cons
 // and frees them if it fails).  Checks the structure on the device (offsets
 // monotone in [0, m], sources in [0, n) and sorted within each row), counts the
 // out-degrees and the degree statistics.  Used by the serialized-graph loader.
+// With h_idx (the same indices in host memory), d_idx is filled from it in
+// chunks while the arcs already copied are checked.
 gap_status graph_from_csc(int64_t n, int64_t m, int64_t* d_off, int32_t* d_idx, uint32_t build_flags,
-                          cudaStream_t s, gap_graph** out);
+                          cudaStream_t s, gap_graph** out, const int32_t* h_idx = nullptr);
 
 }  // namespace gap

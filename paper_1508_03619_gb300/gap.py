@@ -50,7 +50,8 @@ PULL_PHASES = PHASE_NAMES[2:9]
 # every symbol include/gap.h declares (checked by the ABI test)
 EXPORTED = (
     "gap_status_string", "gap_last_error_message", "gap_version", "gap_set_allocator",
-    "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_info", "gap_graph_export_csr",
+    "gap_graph_create_from_edges", "gap_graph_create", "gap_graph_create_csc", "gap_graph_info",
+    "gap_graph_export_csr",
     "gap_graph_export_outdeg", "gap_graph_destroy", "gap_pr_run", "gap_pr_run_f64",
     "gap_pr_options_default", "gap_pr_run_ex", "gap_pr_stats", "gap_pr_run_noalloc",
     "gap_batch_tuning_default", "gap_pr_run_batch", "gap_pr_run_batch_ex", "gap_ppr_batch",
@@ -190,6 +191,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "gap_set_allocator": ([vp], st),
         "gap_graph_create_from_edges": ([i64, i64, vp, vp, u32, vp, ctypes.POINTER(vp)], st),
         "gap_graph_create": ([i64, i64, vp, vp, u32, vp, ctypes.POINTER(vp)], st),
+        "gap_graph_create_csc": ([i64, i64, vp, vp, vp, ctypes.POINTER(vp)], st),
         "gap_graph_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
         "gap_graph_export_csr": ([vp, ctypes.c_int, vp, vp, vp], st),
         "gap_graph_export_outdeg": ([vp, vp, vp], st),
@@ -299,6 +301,22 @@ def gap_graph_create_from_edges(n: int, src, dst, flags: int, stream=None):
     _check(load().gap_graph_create_from_edges(n, len(src), _ptr(src), _ptr(dst), flags,
                                               _stream(stream), ctypes.byref(out)),
            "gap_graph_create_from_edges")
+    return out
+
+
+def gap_graph_create_csc(n: int, in_offsets, in_idx, stream=None):
+    """A graph from a prebuilt in-direction CSR (host or device arrays; int64
+    offsets of n+1 entries, int32 sources); copied and checked, not rebuilt."""
+    for a, size, count, name in ((in_offsets, 8, n + 1, "in_offsets"), (in_idx, 4, None, "in_idx")):
+        esz = a.element_size() if hasattr(a, "element_size") else a.itemsize
+        cnt = a.numel() if hasattr(a, "numel") else a.size
+        if esz != size or (count is not None and cnt != count):
+            raise ValueError(f"gap_graph_create_csc: {name} needs {size}-byte integers"
+                             + (f", {count} of them" if count is not None else ""))
+    m = int(in_idx.numel() if hasattr(in_idx, "numel") else in_idx.size)
+    out = ctypes.c_void_p()
+    _check(load().gap_graph_create_csc(n, m, _ptr(in_offsets), _ptr(in_idx), _stream(stream), ctypes.byref(out)),
+           "gap_graph_create_csc")
     return out
 
 
@@ -704,6 +722,11 @@ class Graph:
         flags = ((GAP_SYMMETRIZE if symmetrize else 0) | (GAP_DEDUP if dedup else 0)
                  | (GAP_DROP_SELF_LOOPS if drop_self_loops else 0))
         return cls(gap_graph_create(n, row_offsets, col_idx, flags, stream))
+
+    @classmethod
+    def from_csc(cls, n, in_offsets, in_idx, stream=None):
+        """A graph from a prebuilt in-direction CSR (copied and checked, not rebuilt)."""
+        return cls(gap_graph_create_csc(n, in_offsets, in_idx, stream))
 
     @classmethod
     def load(cls, path, fmt: int = GAP_FMT_AUTO, symmetrize=False, dedup=True, drop_self_loops=True,

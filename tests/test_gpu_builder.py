@@ -100,3 +100,56 @@ def test_device_generators_match_host(cuda_device):
     s1, d1 = gapgen.chung_lu(1 << 14, 200_000, 2.1, 0x5, table=tab)
     s2, d2 = gapgen.chung_lu_device(1 << 14, 200_000, 2.1, 0x5, table=tab)
     assert np.array_equal(s1, s2.cpu().numpy()) and np.array_equal(d1, d2.cpu().numpy())
+
+
+def test_create_csc_adopts_a_prebuilt_csr(cuda_device):
+    """gap_graph_create_csc takes an in-direction CSR built elsewhere (here: the
+    oracle's, from host memory and from device memory) without rebuilding it:
+    the stored CSR and out-degrees equal the oracle's, PageRank equals the run
+    on the graph built from the same draws bit for bit, and malformed CSRs
+    (a row out of order, a source outside [0, n), offsets not ending at m) are
+    refused."""
+    import torch
+
+    import gapgen
+    import oracle
+    from gpu_helpers import D, run_gpu
+    n = 1 << 14
+    src, dst = gapgen.kron(14, 16, 0x17)
+    coff, cidx = oracle.build_csc(n, src, dst, symmetrize=True)
+    built = gap.Graph.from_edges(n, src, dst, symmetrize=True)
+    try:
+        x_built, _, _ = run_gpu(built, 0.0, 20)
+        for where in ("host", "device"):
+            if where == "host":
+                a_off, a_idx = coff, cidx
+            else:
+                a_off, a_idx = torch.from_numpy(coff).cuda(), torch.from_numpy(cidx).cuda()
+            g = gap.Graph.from_csc(n, a_off, a_idx)
+            try:
+                off2, idx2 = g.export_csr(1)
+                assert np.array_equal(off2, coff) and np.array_equal(idx2, cidx)
+                assert np.array_equal(g.export_outdeg(), np.bincount(cidx, minlength=n).astype(np.int32))
+                x, st, _ = run_gpu(g, 0.0, 20)
+                assert np.array_equal(x, x_built)
+                xo, _, _ = oracle.pagerank(*oracle.build_csr(n, src, dst, symmetrize=True), D, 0.0, 20)
+                assert np.abs(x - xo).sum() <= 1e-5
+            finally:
+                g.close()
+    finally:
+        built.close()
+    bad_rows = cidx.copy()
+    r = int(np.flatnonzero(np.diff(coff) >= 2)[0])
+    bad_rows[coff[r]], bad_rows[coff[r] + 1] = bad_rows[coff[r] + 1], bad_rows[coff[r]]
+    bad_src = cidx.copy()
+    bad_src[3] = n
+    bad_end = coff.copy()
+    bad_end[-1] -= 1
+    bad_mono = coff.copy()
+    r2 = int(np.flatnonzero(np.diff(coff) >= 1)[5])
+    bad_mono[r2 + 1] = bad_mono[r2] - 1   # a row whose end lies before its start
+    for o, i, why in ((coff, bad_rows, "sorted"), (coff, bad_src, "outside"), (bad_end, cidx, "end at m"),
+                      (bad_mono, cidx, "monotone")):
+        with pytest.raises(gap.GapError) as e:
+            gap.Graph.from_csc(n, o, i)
+        assert e.value.status == gap.GAP_ERR_INVALID_ARG and why in gap.last_error_message()
