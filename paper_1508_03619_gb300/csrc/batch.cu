@@ -75,11 +75,11 @@ struct BatchGraphState {
 // iteration and loaded with the evict-first hint to leave L1 to the gathers.
 __device__ __forceinline__ float gather_c(const float* p) { return *p; }
 __device__ __forceinline__ int load_idx(const int32_t* p) { return __ldcs(p); }
+// A hint that brings a line into L1 ahead of its loads (holds no register).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 constexpr unsigned long long BARRIER_WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int TILE_LANE_ROWS_MAX = 8;  // light tiles whose rows all have <= 8 in-arcs: a lane per row
-constexpr double DELTA_SCALE = 1152921504606846976.0;           // 2^60
-constexpr double DELTA_UNIT = 1.0 / DELTA_SCALE;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -132,9 +132,6 @@ __device__ __forceinline__ int find_graph(const int64_t* __restrict__ base, int 
   return lo;
 }
 
-__device__ __forceinline__ unsigned long long to_fixed(double v) {
-  return (unsigned long long)__double2ull_rn(v * DELTA_SCALE);
-}
 
 // One 32-vertex light tile: rows of degree <= heavy are pulled with the
 // warp-merge (the tile's arcs taken 32 at a time in vertex order; each lane
@@ -143,9 +140,9 @@ __device__ __forceinline__ unsigned long long to_fixed(double v) {
 // partial to the row's owner lane).  UB batches of 32 arcs are loaded before
 // any is summed, so UB gathers per lane are in flight; the batches' partials
 // are still added to each row in batch order.  Returns the tile's |x' - x|
-// (FP64) in every lane.
+// (units of 2^-60, exact) in every lane.
 template <int UB>
-__device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float d, int heavy) {
+__device__ unsigned long long pull_tile(const BatchGraph& G, int64_t tile, int parity, float d, int heavy) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const float* cin = parity ? G.c1 : G.c0;
@@ -156,6 +153,9 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
   const int64_t re = valid ? __ldg(G.off + v + 1) : 0;
   const bool mine = valid && re - rb <= heavy;  // heavy rows belong to chunk tasks
   const int dd = mine ? (int)(re - rb) : 0;
+  // loaded with the offsets, so they are not at the end of the gather chain
+  const float xo = mine ? __ldcg(G.x + v) : 0.f;
+  const int od = mine ? __ldg(G.outdeg + v) : 0;
   int incl = dd;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -174,75 +174,76 @@ __device__ double pull_tile(const BatchGraph& G, int64_t tile, int parity, float
     for (int k = 0; k < TILE_LANE_ROWS_MAX; ++k) vv[k] = k < dd ? gather_c(cin + load_idx(G.idx + rb + k)) : 0.f;
 #pragma unroll
     for (int k = 0; k < TILE_LANE_ROWS_MAX; ++k) acc = __fadd_rn(acc, vv[k]);
-  } else
-  for (int base = 0; base < total; base += 32 * UB) {
-    int r[UB];
-    float val[UB];
+  } else {
+    // the light rows' index lines into L1 first: each batch below then waits on its gathers only
+    if (dd > 0)
+      for (int64_t p = rb & ~(int64_t)31; p < re; p += 32) prefetch_l1(G.idx + p);
+    for (int base = 0; base < total; base += 32 * UB) {
+      int r[UB];
+      float val[UB];
 #pragma unroll
-    for (int q = 0; q < UB; ++q) {
-      const int j = base + q * 32 + lane;
-      int rr = 0;  // last row whose exclusive start is <= j
+      for (int q = 0; q < UB; ++q) {
+        const int j = base + q * 32 + lane;
+        int rr = 0;  // last row whose exclusive start is <= j
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = rr + step;
-        const int ex = __shfl_sync(FULL, excl, cand & 31);
-        if (cand < 32 && ex <= j) rr = cand;
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = rr + step;
+          const int ex = __shfl_sync(FULL, excl, cand & 31);
+          if (cand < 32 && ex <= j) rr = cand;
+        }
+        r[q] = rr;
+        const int64_t rbr = __shfl_sync(FULL, rb, rr);
+        const int exr = __shfl_sync(FULL, excl, rr);
+        val[q] = j < total ? gather_c(cin + load_idx(G.idx + rbr + (j - exr))) : 0.f;
       }
-      r[q] = rr;
-      const int64_t rbr = __shfl_sync(FULL, rb, rr);
-      const int exr = __shfl_sync(FULL, excl, rr);
-      val[q] = j < total ? gather_c(cin + load_idx(G.idx + rbr + (j - exr))) : 0.f;
-    }
 #pragma unroll
-    for (int q = 0; q < UB; ++q) {
-      const int b0 = base + q * 32;
-      float xs = val[q];
+      for (int q = 0; q < UB; ++q) {
+        const int b0 = base + q * 32;
+        float xs = val[q];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float t = __shfl_up_sync(FULL, xs, o);
-        const int ro = __shfl_up_sync(FULL, r[q], o);
-        if (lane >= o && ro == r[q]) xs = __fadd_rn(xs, t);
+        for (int o = 1; o < 32; o <<= 1) {
+          const float t = __shfl_up_sync(FULL, xs, o);
+          const int ro = __shfl_up_sync(FULL, r[q], o);
+          if (lane >= o && ro == r[q]) xs = __fadd_rn(xs, t);
+        }
+        const bool inter = dd > 0 && excl < b0 + 32 && incl > b0;
+        const int tl = (incl < b0 + 32 ? incl : b0 + 32) - 1 - b0;
+        const float part = __shfl_sync(FULL, xs, inter ? tl : lane);
+        if (inter) acc = __fadd_rn(acc, part);
       }
-      const bool inter = dd > 0 && excl < b0 + 32 && incl > b0;
-      const int tl = (incl < b0 + 32 ? incl : b0 + 32) - 1 - b0;
-      const float part = __shfl_sync(FULL, xs, inter ? tl : lane);
-      if (inter) acc = __fadd_rn(acc, part);
     }
   }
-  double dl = 0.0;
+  unsigned long long dl = 0;
   if (mine) {
-    const float xo = __ldcg(G.x + v);
     const float xn = __fadd_rn(G.base, __fmul_rn(d, acc));
     __stcg(G.x + v, xn);
-    const int od = __ldg(G.outdeg + v);
     __stcg(cout + v, od > 0 ? xn / (float)od : 0.f);
-    const double df = (double)xn - (double)xo;
-    dl = df < 0 ? -df : df;
+    dl = fixed60_absdiff(xn, xo);
   }
   return warp_sum(dl);
 }
 
-// Update of one row from its finished in-sum; returns |x' - x|.
-__device__ __forceinline__ double update_row(const BatchGraph& G, int64_t v, float sum, int parity, float d) {
+// Update of one row from its finished in-sum; returns |x' - x| (units of 2^-60).
+__device__ __forceinline__ unsigned long long update_row(const BatchGraph& G, int64_t v, float sum, int parity, float d) {
   float* cout = parity ? G.c0 : G.c1;
   const float xo = __ldcg(G.x + v);
   const float xn = __fadd_rn(G.base, __fmul_rn(d, sum));
   __stcg(G.x + v, xn);
   const int od = __ldg(G.outdeg + v);
   __stcg(cout + v, od > 0 ? xn / (float)od : 0.f);
-  const double df = (double)xn - (double)xo;
-  return df < 0 ? -df : df;
+  return fixed60_absdiff(xn, xo);
 }
 
 // One chunk of a heavy row: lanes take arcs lane, lane+32, ... (4 loads in
-// flight per lane), then a fixed-order warp tree sum.  Returns |x' - x| in
-// lane 0 when this warp updated the row, else 0.
-__device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t cid, float* partial,
+// flight per lane), then a fixed-order warp tree sum.  Returns |x' - x|
+// (units of 2^-60) in lane 0 when this warp updated the row, else 0.
+__device__ unsigned long long pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t cid, float* partial,
                              unsigned int* ctr, int parity, float d) {
   const int lane = threadIdx.x & 31;
   const float* cin = parity ? G.c1 : G.c0;
   const int32_t* ix = G.idx + c.a0;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (int p = lane * 32; p < c.len; p += 32 * 32) prefetch_l1(ix + p);  // the chunk's index lines
   int j = lane;
   for (; j + 96 < c.len; j += 128) {
     const int u0 = load_idx(ix + j), u1 = load_idx(ix + j + 32), u2 = load_idx(ix + j + 64),
@@ -256,7 +257,7 @@ __device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t ci
   float s = __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
   s = warp_sum(s);
   if (c.nch == 1) {
-    double dl = 0.0;
+    unsigned long long dl = 0;
     if (lane == 0) dl = update_row(G, c.v, s, parity, d);
     return dl;
   }
@@ -268,12 +269,12 @@ __device__ double pull_chunk(const BatchGraph& G, const ChunkDesc& c, int64_t ci
     last = atomicAdd(ctr + c.first, 1u) + 1u == (unsigned)c.nch;
   }
   last = __shfl_sync(0xffffffffu, last, 0);
-  if (!last) return 0.0;
+  if (!last) return 0;
   __threadfence();
   float t = 0.f;
   for (int k = lane; k < c.nch; k += 32) t = __fadd_rn(t, __ldcg(partial + c.first + k));
   t = warp_sum(t);
-  double dl = 0.0;
+  unsigned long long dl = 0;
   if (lane == 0) {
     dl = update_row(G, c.v, t, parity, d);
     ctr[c.first] = 0;  // ready for the next iteration (after the grid barrier)
@@ -319,17 +320,106 @@ __global__ void k_batch_plan(int ng, const int64_t* __restrict__ tile_prefix, co
 
 // ---- the persistent kernel ----------------------------------------------------
 
+// Shared memory of the persistent kernel: one activity bit per graph, then
+// (compact mode) the active graphs' task ranges: abase[k] = first task of the
+// k-th active graph in a virtual task space holding only active graphs'
+// tasks, abase[nact] = their total, agraph[k] = that graph's index.
+__host__ __device__ inline size_t batch_bits_bytes(int ng) { return ((sizeof(unsigned int) * ((ng + 31) / 32)) + 7) & ~(size_t)7; }
+inline size_t batch_compact_bytes(int ng) {
+  return batch_bits_bytes(ng) + sizeof(int64_t) * (ng + 1) + sizeof(int32_t) * ng;
+}
+constexpr size_t BATCH_COMPACT_SMEM_MAX = 32 * 1024;  // larger batches walk every graph's tasks
+
+// Rebuild the compact list from the activity bits (every thread of the block
+// calls it; graphs keep their batch order, so a warp's tasks still move forward).
+template <int THREADS>
+__device__ void build_active_list(const unsigned int* active, int ng, const int64_t* __restrict__ task_base,
+                                  int64_t* abase, int32_t* agraph, int* nact) {
+  constexpr int W = THREADS / 32;
+  __shared__ int wc[W];
+  __shared__ int64_t wt[W];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int per = (ng + THREADS - 1) / THREADS;
+  const int g0 = min((int)threadIdx.x * per, ng), g1 = min(g0 + per, ng);
+  int c = 0;
+  int64_t t = 0;
+  for (int i = g0; i < g1; ++i)
+    if ((active[i >> 5] >> (i & 31)) & 1u) {
+      ++c;
+      t += __ldg(task_base + i + 1) - __ldg(task_base + i);
+    }
+  int ci = c;
+  int64_t ti = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, ci, o);
+    const int64_t z = __shfl_up_sync(0xffffffffu, ti, o);
+    if (lane >= o) ci += y, ti += z;
+  }
+  if (lane == 31) wc[w] = ci, wt[w] = ti;
+  __syncthreads();
+  if (w == 0) {
+    int cw = lane < W ? wc[lane] : 0;
+    int64_t tw = lane < W ? wt[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, cw, o);
+      const int64_t z = __shfl_up_sync(0xffffffffu, tw, o);
+      if (lane >= o) cw += y, tw += z;
+    }
+    if (lane < W) wc[lane] = cw, wt[lane] = tw;
+  }
+  __syncthreads();
+  int k = ci - c + (w ? wc[w - 1] : 0);
+  int64_t b = ti - t + (w ? wt[w - 1] : 0);
+  for (int i = g0; i < g1; ++i)
+    if ((active[i >> 5] >> (i & 31)) & 1u) {
+      agraph[k] = i;
+      abase[k] = b;
+      ++k;
+      b += __ldg(task_base + i + 1) - __ldg(task_base + i);
+    }
+  if (threadIdx.x == THREADS - 1) {
+    abase[k] = b;
+    *nact = k;
+  }
+  __syncthreads();
+}
+
+// One task (a light tile or a heavy-row chunk of graph i); its |x' - x| goes
+// to the graph's fixed-point accumulator.
+__device__ __forceinline__ void run_task(const BatchGraph* __restrict__ gs, int i, int64_t local,
+                                         const int64_t* __restrict__ chunk_base, const ChunkDesc* __restrict__ desc,
+                                         float* partial, unsigned int* ctr, unsigned long long* acc_now, int parity,
+                                         float d, int heavy) {
+  const BatchGraph& G = gs[i];
+  unsigned long long dl;
+  if (local < G.tiles) {
+    dl = pull_tile<2>(G, local, parity, d, heavy);
+  } else {
+    const int64_t cid = __ldg(chunk_base + i) + (local - G.tiles);
+    dl = pull_chunk(G, desc[cid], cid, partial, ctr, parity, d);
+  }
+  if ((threadIdx.x & 31) == 0 && dl != 0) atomicAdd(acc_now + i, dl);
+}
+
 // The 512-thread kernel is held to three resident blocks per SM (<= 42
 // registers a thread): the loop is bound by memory latency, and with an open
 // register budget the compiler took 56 registers, leaving two blocks per SM.
-template <int THREADS>
+// With COMPACT, warps stride over the active graphs' tasks only (a graph
+// that has stopped costs nothing); otherwise they stride over every task and
+// skip those of stopped graphs.
+template <int THREADS, bool COMPACT>
 __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_persistent(
     const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ task_base,
     const int64_t* __restrict__ chunk_base, const ChunkDesc* __restrict__ desc, float* partial, unsigned int* ctr,
     unsigned long long* acc /* [3][ng] */, BatchGraphState* st, BatchCtrl* ctrl, float d, double tol,
     int32_t max_iters, int heavy) {
-  extern __shared__ unsigned int active[];  // one bit per graph
-  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(8) unsigned char bsh[];
+  unsigned int* active = reinterpret_cast<unsigned int*>(bsh);  // one bit per graph
+  int64_t* abase = reinterpret_cast<int64_t*>(bsh + batch_bits_bytes(ng));
+  int32_t* agraph = reinterpret_cast<int32_t*>(abase + ng + 1);
+  __shared__ int nact;
   const int64_t warp = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * THREADS) >> 5;
   const unsigned int nb = gridDim.x;
@@ -340,24 +430,26 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_per
     active[w] = max_iters > 0 ? (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u)) : 0u;
   }
   __syncthreads();
+  if (COMPACT) build_active_list<THREADS>(active, ng, task_base, abase, agraph, &nact);
   __shared__ int running;
   for (int it = 0; it < max_iters; ++it) {
     const int parity = it & 1;
     unsigned long long* acc_now = acc + (int64_t)(it % 3) * ng;
-    int i = 0;
-    for (int64_t task = warp; task < ntasks; task += nwarps) {
-      while (i + 1 < ng && __ldg(task_base + i + 1) <= task) ++i;  // a warp's tasks only move forward
-      if (!((active[i >> 5] >> (i & 31)) & 1u)) continue;  // warp-uniform
-      const BatchGraph& G = gs[i];
-      const int64_t local = task - __ldg(task_base + i);
-      double dl;
-      if (local < G.tiles) {
-        dl = pull_tile<1>(G, local, parity, d, heavy);
-      } else {
-        const int64_t cid = __ldg(chunk_base + i) + (local - G.tiles);
-        dl = pull_chunk(G, desc[cid], cid, partial, ctr, parity, d);
+    if (COMPACT) {
+      const int na = nact;
+      const int64_t total = abase[na];
+      int k = 0;
+      for (int64_t task = warp; task < total; task += nwarps) {
+        while (k + 1 < na && abase[k + 1] <= task) ++k;  // a warp's tasks only move forward
+        run_task(gs, agraph[k], task - abase[k], chunk_base, desc, partial, ctr, acc_now, parity, d, heavy);
       }
-      if (lane == 0 && dl != 0.0) atomicAdd(acc_now + i, to_fixed(dl));
+    } else {
+      int i = 0;
+      for (int64_t task = warp; task < ntasks; task += nwarps) {
+        while (i + 1 < ng && __ldg(task_base + i + 1) <= task) ++i;  // a warp's tasks only move forward
+        if (!((active[i >> 5] >> (i & 31)) & 1u)) continue;  // warp-uniform
+        run_task(gs, i, task - __ldg(task_base + i), chunk_base, desc, partial, ctr, acc_now, parity, d, heavy);
+      }
     }
     if (blockIdx.x == 0) {  // the accumulator of iteration it+1 starts at zero
       unsigned long long* acc_next = acc + (int64_t)((it + 1) % 3) * ng;
@@ -368,7 +460,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_per
     int any = 0;
     for (int i = threadIdx.x; i < ng; i += THREADS) {
       if (!((active[i >> 5] >> (i & 31)) & 1u)) continue;
-      const double delta = (double)__ldcg(acc_now + i) * DELTA_UNIT;
+      const double delta = (double)__ldcg(acc_now + i) * FIXED60_UNIT;
       const bool conv = delta < tol;
       const bool stop = conv || it + 1 >= max_iters;
       if (blockIdx.x == 0) {
@@ -388,6 +480,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_per
     }
     __syncthreads();
     if (!running) return;
+    if (COMPACT) build_active_list<THREADS>(active, ng, task_base, abase, agraph, &nact);
   }
 }
 
@@ -423,11 +516,11 @@ using PersistentFn = void (*)(const BatchGraph*, int, const int64_t*, const int6
                               unsigned int*, unsigned long long*, BatchGraphState*, BatchCtrl*, float, double,
                               int32_t, int);
 
-PersistentFn persistent_for(int threads) {
+PersistentFn persistent_for(int threads, bool compact) {
   switch (threads) {
-    case 128: return k_batch_persistent<128>;
-    case 256: return k_batch_persistent<256>;
-    case 512: return k_batch_persistent<512>;
+    case 128: return compact ? k_batch_persistent<128, true> : k_batch_persistent<128, false>;
+    case 256: return compact ? k_batch_persistent<256, true> : k_batch_persistent<256, false>;
+    case 512: return compact ? k_batch_persistent<512, true> : k_batch_persistent<512, false>;
     default: return nullptr;
   }
 }
@@ -459,7 +552,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
               max_iters);
     return GAP_ERR_INVALID_ARG;
   }
-  if (tu.heavy_min_degree < 32 || tu.chunk_arcs < 32 || tu.chunk_arcs > (1 << 24) || !persistent_for(tu.block_threads) ||
+  if (tu.heavy_min_degree < 32 || tu.chunk_arcs < 32 || tu.chunk_arcs > (1 << 24) || !persistent_for(tu.block_threads, true) ||
       tu.blocks_per_sm < 0) {
     set_error("gap_pr_run_batch: bad tuning (heavy_min_degree %d >= 32, chunk_arcs %d in [32, 2^24], "
               "block_threads %d in {128, 256, 512}, blocks_per_sm %d >= 0)",
@@ -504,8 +597,9 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
     chunk_cap += chunk_capacity(g->m, tu.heavy_min_degree, tu.chunk_arcs);
   }
   const int threads = tu.block_threads;
-  const PersistentFn kfn = persistent_for(threads);
-  const size_t smem = sizeof(unsigned int) * ((count + 31) / 32);
+  const bool compact = batch_compact_bytes(count) <= BATCH_COMPACT_SMEM_MAX;
+  const PersistentFn kfn = persistent_for(threads, compact);
+  const size_t smem = compact ? batch_compact_bytes(count) : batch_bits_bytes(count);
   int per_sm = 0;
   GAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
   if (per_sm < 1) {

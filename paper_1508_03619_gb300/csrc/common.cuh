@@ -135,6 +135,33 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// ---- the stop test's |x' - x| in fixed point --------------------------------
+// FP32 scores are turned into integers in units of 2^-60 with integer ALU work
+// only (this GPU's FP64 rate is a small fraction of its FP32 rate, and a
+// per-row FP64 subtraction and FP64 sums made FP64 the busiest pipe of the
+// row-heavy passes).  A float v >= 2^-37 is an exact multiple of 2^-60, so
+// v * 2^60 is exact; below that, bits under 2^-60 are dropped (at most 2^-60
+// per row).  PageRank scores stay below 2 (the mass is at most 1); a value of
+// 2 or more saturates at 2^61, which keeps every sum of such terms far below
+// 2^64.  Differences and sums of these integers are exact, so a delta
+// accumulated in these units does not depend on the order of its terms.
+constexpr double FIXED60_UNIT = 1.0 / 1152921504606846976.0;  // 2^-60
+
+__device__ __forceinline__ unsigned long long fixed60(float v) {  // v >= 0
+  const unsigned int b = __float_as_uint(v) & 0x7fffffffu;
+  const int e = (int)(b >> 23);  // biased exponent; 0 for subnormals
+  if (e >= 128) return 1ull << 61;
+  const unsigned long long m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+  const int sh = (e ? e : 1) - 90;  // v * 2^60 = m * 2^(e - 150 + 60)
+  return sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0ull);
+}
+
+// |a - b| in units of 2^-60.
+__device__ __forceinline__ unsigned long long fixed60_absdiff(float a, float b) {
+  const unsigned long long fa = fixed60(a), fb = fixed60(b);
+  return fa > fb ? fa - fb : fb - fa;
+}
+
 // Block-wide sum for blockDim.x a multiple of 32 (<= 1024); result valid in all
 // threads.  `sh` must hold 32 elements.
 template <class T>

@@ -9,7 +9,8 @@
 // Per iteration, for every vertex v (row v of the in-direction CSR):
 //   sum[v] = sum_{u in N-(v)} c[u]                       (gather-SpMV)
 //   x'[v]  = (1-d)/n + d*sum[v]                          (update, fused)
-//   delta += |x'[v] - x[v]|   (FP64, block partials reduced in fixed order)
+//   delta += |x'[v] - x[v]|   (FP32 scores: exact integers in units of 2^-60,
+//                              u64 block partials; FP64: FP64, fixed order)
 //   c'[v]  = x'[v] / |N+(v)|, or 0 for a dangling v      (next contribution)
 // x is updated in place (a row is owned by one thread group); c ping-pongs
 // between two buffers because every row gathers from all of c.
@@ -82,6 +83,30 @@ struct PrCtrl {
   gap_pr_stats_t st;
 };
 
+// The stop test's delta.  FP32 scores: each row's |x' - x| is an exact integer
+// in units of 2^-60 (fixed60) and block partials are u64 sums, integer ALU work
+// only and exact, so the order of the terms does not matter.  FP64 scores: an
+// FP64 difference and FP64 sums in a fixed order (the deterministic FP64 mode
+// reproduces the oracle's delta history).
+template <class Acc>
+struct DeltaOf {
+  using T = double;
+};
+template <>
+struct DeltaOf<float> {
+  using T = unsigned long long;
+};
+template <class Acc>
+using delta_t = typename DeltaOf<Acc>::T;
+
+__device__ __forceinline__ unsigned long long row_delta(float xn, float xo) { return fixed60_absdiff(xn, xo); }
+__device__ __forceinline__ double row_delta(double xn, double xo) {
+  const double dd = xn - xo;
+  return dd < 0 ? -dd : dd;
+}
+__device__ __forceinline__ double delta_value(unsigned long long s) { return (double)s * FIXED60_UNIT; }
+__device__ __forceinline__ double delta_value(double s) { return s; }
+
 template <class Acc>
 struct PrArgs {
   const int64_t* __restrict__ off;
@@ -94,7 +119,7 @@ struct PrArgs {
   void* c1;
   Acc base, d;
   const PrCtrl* ctrl;
-  double* partial;  // this launch's block partials of delta
+  delta_t<Acc>* partial;  // this launch's block partials of delta
   int kahan;
   int64_t kahan_thr;
 };
@@ -199,7 +224,7 @@ __device__ __forceinline__ double lane_sum(const PrArgs<Acc>& a, const void* cin
 }
 
 template <class Acc>
-__device__ __forceinline__ double update_row(const PrArgs<Acc>& a, int64_t v, Acc sum, void* cout, bool wb) {
+__device__ __forceinline__ delta_t<Acc> update_row(const PrArgs<Acc>& a, int64_t v, Acc sum, void* cout, bool wb) {
   const Acc xo = __ldcs(a.x + v);
   Acc xn;
   if constexpr (std::is_same<Acc, double>::value)
@@ -217,8 +242,7 @@ __device__ __forceinline__ double update_row(const PrArgs<Acc>& a, int64_t v, Ac
     else
       reinterpret_cast<float*>(cout)[v] = cv;
   }
-  const double dd = (double)xn - (double)xo;
-  return dd < 0 ? -dd : dd;
+  return row_delta(xn, xo);
 }
 
 struct IterState {
@@ -241,8 +265,9 @@ __device__ __forceinline__ IterState iter_state(const PrArgs<Acc>& a) {
 
 constexpr int PR_THREADS = 256;
 
-__device__ __forceinline__ void write_partial(double dl, double* partial) {
-  __shared__ double sh[32];
+template <class T>
+__device__ __forceinline__ void write_partial(T dl, T* partial) {
+  __shared__ T sh[32];
   dl = block_sum(dl, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = dl;
 }
@@ -263,7 +288,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_small(PrArgs<Acc> a, int64_
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   const unsigned FULL = 0xffffffffu;
   const int zero_fill = a.ctrl->zero_fill_until;
-  double dl = 0.0;
+  delta_t<Acc> dl = 0;
   for (int64_t v0 = warp_id * 32; v0 < n; v0 += nwarps * 32) {
     const int64_t v = v0 + lane;
     const bool valid = v < n;
@@ -513,7 +538,7 @@ __global__ void __launch_bounds__(PR_THREADS, 4) k_pull_small_coo(PrArgs<Acc> a,
   const int64_t nchunks = (T + TPC - 1) / TPC;
   const bool last = s + 1 == S;
   const int zero_fill = a.ctrl->zero_fill_until;
-  double dl = 0.0;
+  delta_t<Acc> dl = 0;
   for (int64_t ch = warp_id; ch < nchunks; ch += nwarps) {
     const int64_t t0 = ch * TPC, t1 = t0 + TPC < T ? t0 + TPC : T;
     const int64_t r0 = t0 * 32;
@@ -665,8 +690,7 @@ __global__ void __launch_bounds__(PR_THREADS, 4) k_pull_small_coo(PrArgs<Acc> a,
             else
               reinterpret_cast<float*>(st.cout)[v[u]] = cv;
           }
-          const double dd = (double)xn - (double)xo[u];
-          dl += dd < 0 ? -dd : dd;
+          dl += row_delta(xn, xo[u]);
         }
       }
     }
@@ -684,7 +708,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_group(PrArgs<Acc> a) {
   const int grp = (threadIdx.x & 31) / G;
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
-  double dl = 0.0;
+  delta_t<Acc> dl = 0;
   for (int64_t wb0 = a.begin + warp_id * RPW; wb0 < a.end; wb0 += nwarps * RPW) {
     const int64_t i = wb0 + grp;
     const bool has = i < a.end;
@@ -710,7 +734,7 @@ template <class Acc>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_cta(PrArgs<Acc> a) {
   __shared__ double sh[32];
   const IterState st = iter_state(a);
-  double dl = 0.0;
+  delta_t<Acc> dl = 0;
   for (int64_t i = a.begin + blockIdx.x; i < a.end; i += gridDim.x) {
     const int64_t v = a.list[i];
     const int64_t b = a.off[v], e = a.off[v + 1];
@@ -771,7 +795,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_hub_fixup(PrArgs<Acc> a, SegArgs
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
-  double dl = 0.0;
+  delta_t<Acc> dl = 0;
   for (int64_t h = warp_id; h < nhubs; h += nwarps) {
     double t = 0.0;
     for (int64_t k = cstart[h] + lane; k < cstart[h + 1]; k += 32) t += csum[k];
@@ -802,7 +826,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_group_seg(PrArgs<Acc> a, Se
   const int64_t warp_id = ((int64_t)blockIdx.x * PR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * PR_THREADS) >> 5;
   const bool last = s + 1 == sg.S;
-  double dl = 0.0;
+  delta_t<Acc> dl = 0;
   for (int64_t wb0 = a.begin + warp_id * RPW; wb0 < a.end; wb0 += nwarps * RPW) {
     const int64_t i = wb0 + grp;
     const bool has = i < a.end;
@@ -831,14 +855,17 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_group_seg(PrArgs<Acc> a, Se
 }
 
 // ---- per-iteration finalize: fixed-order delta reduction and stop test -------
-__global__ void __launch_bounds__(1024) k_finalize(PrCtrl* ctrl, const double* __restrict__ partial, int64_t np,
+// T: the delta partials' type (u64 units of 2^-60 for FP32 scores, FP64 for FP64).
+template <class T>
+__global__ void __launch_bounds__(1024) k_finalize(PrCtrl* ctrl, const T* __restrict__ partial, int64_t np,
                                                     double tol, int32_t max_iters,
                                                     cudaGraphConditionalHandle handle, int use_handle) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
-  s = block_sum(s, sh);
+  __shared__ T sh[32];
+  T acc = 0;
+  for (int64_t i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+  acc = block_sum(acc, sh);
   if (threadIdx.x == 0) {
+    const double s = delta_value(acc);
     const int k = ctrl->iter;
     if (k < GAP_PR_HIST) ctrl->st.delta_hist[k] = s;
     ctrl->st.final_delta = s;
@@ -1256,7 +1283,7 @@ __global__ void __launch_bounds__(256) k_delta_hist(const float* __restrict__ r,
     const float a = fabsf(r[v]);
     if (a > 0.f) {
       const int b = delta_bucket(a);
-      atomicAdd(&sm[b], (unsigned long long)__double2ull_rn((double)a * DELTA_FIX));
+      atomicAdd(&sm[b], fixed60(a));  // exact for |r| >= 2^-37
       atomicAdd(&sc[b], (unsigned long long)outdeg[v]);
     }
   }
@@ -1845,7 +1872,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
   a.ctrl = dctrl;
   a.kahan = o.kahan_hubs ? 1 : 0;
   a.kahan_thr = o.hub_threshold;
-  double* pbase = partial.as<double>();
+  delta_t<Acc>* pbase = partial.as<delta_t<Acc>>();
 
   bool skip_finalize = false;  // the residual iteration takes its own stop decision
   auto launch_body = [&](cudaStream_t ls, cudaGraphConditionalHandle h, int use_h) -> gap_status {
@@ -2203,10 +2230,10 @@ __global__ void __launch_bounds__(PB_THREADS) k_pb_scatter(PbArgs a) {
 __global__ void __launch_bounds__(PB_THREADS) k_pb_sum(PrArgs<float> pa, const float* __restrict__ pval,
                                                        const uint16_t* __restrict__ ploc,
                                                        const int64_t* __restrict__ in_off, int64_t n, int nbins,
-                                                       unsigned long long* cursor, double* partial) {
+                                                       unsigned long long* cursor, unsigned long long* partial) {
   extern __shared__ __align__(16) unsigned char pb_smem[];
   float* acc = reinterpret_cast<float*>(pb_smem);  // [PB_BIN]
-  __shared__ double sh[32];
+  __shared__ unsigned long long sh[32];
   void* cout = (pa.ctrl->iter & 1) ? pa.c0 : pa.c1;
   for (int b = blockIdx.x; b < nbins; b += gridDim.x) {
     for (int t = threadIdx.x; t < PB_BIN; t += PB_THREADS) acc[t] = 0.f;
@@ -2227,7 +2254,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_pb_sum(PrArgs<float> pa, const f
     }
     for (; p < p1; p += PB_THREADS) atomicAdd(acc + __ldcs(ploc + p), __ldcs(pval + p));
     __syncthreads();
-    double dl = 0.0;
+    unsigned long long dl = 0;
     for (int64_t v = v0 + threadIdx.x; v < v1; v += PB_THREADS) dl += update_row(pa, v, acc[v - v0], cout, false);
     dl = block_sum(dl, sh);
     if (threadIdx.x == 0) {
@@ -2317,7 +2344,7 @@ static gap_status run_trial_binned(gap_graph* g, double d, double tol, int32_t m
   float* dpv = pv.as<float>();
   uint16_t* dpl = pl.as<uint16_t>();
   unsigned long long* dcur = cursor.as<unsigned long long>();
-  double* dpart = partial.as<double>();
+  unsigned long long* dpart = partial.as<unsigned long long>();
 
   // One iteration.  The kernels read the iteration count on the device to pick
   // the contribution buffer they read and the one they write, so the same
@@ -2604,7 +2631,8 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
   char* bytes = static_cast<char*>(base);
   void* c0 = bytes;
   void* c1 = bytes + sizeof(float) * GAP_NOALLOC_MAX_VERTICES;
-  double* partial = reinterpret_cast<double*>(bytes + NOALLOC_C_BYTES);
+  double* partial = reinterpret_cast<double*>(bytes + NOALLOC_C_BYTES);  // delta partials, then mass partials
+  unsigned long long* dpartial = reinterpret_cast<unsigned long long*>(partial);
   PrCtrl* dctrl = reinterpret_cast<PrCtrl*>(bytes + NOALLOC_C_BYTES + sizeof(double) * NOALLOC_PARTIALS);
   static_assert(sizeof(PrCtrl) <= 4096, "PrCtrl must fit its slot");
 
@@ -2629,7 +2657,7 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
   a.base = (float)((1.0 - damping) / (double)n);
   a.d = (float)damping;
   a.ctrl = dctrl;
-  a.partial = partial;
+  a.partial = dpartial;
   a.kahan = 0;
   a.kahan_thr = INT64_MAX;
   const int grid = stride_grid(n, PR_THREADS, 8);
@@ -2640,7 +2668,7 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
   for (int32_t k = 0; k < max_iters; ++k) {
     k_pull_small<float, SMALL_UB><<<grid, PR_THREADS, 0, s>>>(a, n, INT64_MAX);
     GAP_LAUNCH_CHECK();
-    k_finalize<<<1, 1024, 0, s>>>(dctrl, partial, grid, tol, max_iters, 0, 0);
+    k_finalize<<<1, 1024, 0, s>>>(dctrl, dpartial, grid, tol, max_iters, 0, 0);
     GAP_LAUNCH_CHECK();
     GAP_CUDA(cudaMemcpyAsync(g->flag_host, &dctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     GAP_CUDA(cudaStreamSynchronize(s));

@@ -58,10 +58,6 @@ struct PprArgs {
   unsigned long long* acc;                // [KP] fixed-point L1 delta of this iteration
 };
 
-__device__ __forceinline__ unsigned long long ppr_fixed(double v) {
-  return (unsigned long long)__double2ull_rn(v * PPR_DELTA_SCALE);
-}
-
 // Sequential (ascending) sums of 4 columns over arcs [b, e), by one lane.
 __device__ __forceinline__ float4 ppr_row_sum(const PprArgs& a, int64_t b, int64_t e, int col0) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
@@ -136,9 +132,9 @@ __device__ __forceinline__ float4 ppr_sum(const PprArgs& a, int64_t b, int64_t e
 }
 
 // Update of row v, columns col0..col0+3, from their in-sums; adds |x' - x| of
-// the active columns to dl[].
+// the active columns to qacc[] (exact, in units of 2^-60: fixed60).
 __device__ __forceinline__ void ppr_update(const PprArgs& a, int64_t v, int col0, float4 s4, const int* act,
-                                           const float* bq, double* dl) {
+                                           const float* bq, unsigned long long* qacc) {
   const float sum[4] = {s4.x, s4.y, s4.z, s4.w};
   const uint32_t mw = a.seedmask[v * a.mask_words + (col0 >> 5)];
   const int deg = a.outdeg[v];
@@ -152,8 +148,7 @@ __device__ __forceinline__ void ppr_update(const PprArgs& a, int64_t v, int col0
     if (act[q]) {
       const float bb = (mw >> ((col0 + q) & 31)) & 1u ? bq[q] : 0.f;
       xn[q] = __fadd_rn(bb, __fmul_rn(a.d, sum[q]));
-      const double dd = (double)xn[q] - (double)xo[q];
-      dl[q] += dd < 0 ? -dd : dd;
+      qacc[q] += fixed60_absdiff(xn[q], xo[q]);
     } else {
       xn[q] = xo[q];  // frozen column: keep its scores
     }
@@ -166,7 +161,7 @@ __device__ __forceinline__ void ppr_update(const PprArgs& a, int64_t v, int col0
 // One CTA = 32 row slots x LR lanes; lane g of a slot covers columns 4g..4g+3;
 // a slot's lanes are consecutive lanes of one warp.  Light rows are taken
 // grid-stride, one per slot; then the chunks of heavy rows, one per slot.  Each
-// row's |x' - x| is rounded to fixed point and summed in registers, so slots
+// row's |x' - x| is taken exactly in fixed point and summed in registers, so slots
 // never wait for each other; one atomic per column and thread at the end.
 template <int LR>
 __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
@@ -190,10 +185,7 @@ __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
   for (int64_t v = (int64_t)blockIdx.x * PPR_ROWS + r; v < a.n; v += slots) {
     const int64_t b = a.off[v], e = a.off[v + 1];
     if (e - b > PPR_HEAVY) continue;  // a chunked row
-    double dl[4] = {0.0, 0.0, 0.0, 0.0};
-    ppr_update(a, v, col0, ppr_sum<LR>(a, b, e, col0, g, mask), act, bq, dl);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) qacc[q] += ppr_fixed(dl[q]);
+    ppr_update(a, v, col0, ppr_sum<LR>(a, b, e, col0, g, mask), act, bq, qacc);
   }
   // ---- chunks of heavy rows, one per slot ----
   for (int64_t c0 = (int64_t)blockIdx.x * PPR_ROWS; c0 < a.nchunks; c0 += slots) {
@@ -207,10 +199,7 @@ __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
     }
     int last = 0;
     if (cd.nch == 1) {
-      double dl[4] = {0.0, 0.0, 0.0, 0.0};
-      ppr_update(a, cd.v, col0, s4, act, bq, dl);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) qacc[q] += ppr_fixed(dl[q]);
+      ppr_update(a, cd.v, col0, s4, act, bq, qacc);
     } else if (cd.nch > 1) {
       __stcg(reinterpret_cast<float4*>(a.cpart + cid * a.KP + col0), s4);
       __threadfence();
@@ -228,10 +217,7 @@ __global__ void __launch_bounds__(PPR_ROWS * LR) k_ppr_spmm(PprArgs a) {
         t2 = __fadd_rn(t2, p.z);
         t3 = __fadd_rn(t3, p.w);
       }
-      double dl[4] = {0.0, 0.0, 0.0, 0.0};
-      ppr_update(a, cd.v, col0, make_float4(t0, t1, t2, t3), act, bq, dl);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) qacc[q] += ppr_fixed(dl[q]);
+      ppr_update(a, cd.v, col0, make_float4(t0, t1, t2, t3), act, bq, qacc);
       if (g == 0) a.cctr[cd.first] = 0u;  // ready for the next iteration
     }
   }

@@ -63,3 +63,14 @@ def assert_fp32_parity(x_gpu, x_ref):
     assert l1 <= FP32_L1, f"L1 {l1:.3e} > {FP32_L1}"
     assert rel <= FP32_REL, f"max rel {rel:.3e} > {FP32_REL}"
     return l1, rel
+
+
+def exact_l1_change(x, prev):
+    """sum |x - prev| over FP32 scores, taken exactly: an FP32 score >= 2^-37 is a
+    multiple of 2^-60, so x * 2^60 is an integer (held exactly by float64), the
+    differences and their sum are Python integers, and the sum is converted to a
+    double once and scaled by 2^-60 (both roundings match the library's)."""
+    a = np.asarray(x, np.float32).astype(np.float64) * 2.0 ** 60
+    b = np.asarray(prev, np.float32).astype(np.float64) * 2.0 ** 60
+    total = sum(abs(int(p) - int(q)) for p, q in zip(a, b))
+    return float(total) * 2.0 ** -60

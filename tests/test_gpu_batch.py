@@ -6,7 +6,7 @@ import pytest
 
 import gapgen
 import oracle
-from gpu_helpers import D, FP32_L1, FP32_REL, gpu_graph, oracle_graph
+from gpu_helpers import D, FP32_L1, FP32_REL, exact_l1_change, gpu_graph, oracle_graph
 from paper_1508_03619_gb300 import gap
 
 pytestmark = pytest.mark.gpu
@@ -188,6 +188,24 @@ def test_batch_tunings(cuda_device):
                 gap.gap_pr_run_batch([graphs[0].handle], [torch.empty(graphs[0].n, device="cuda:0")],
                                      D, 0.0, 5, tuning=bad)
             assert e.value.status == gap.GAP_ERR_INVALID_ARG
+    finally:
+        for g in graphs:
+            g.close()
+
+
+def test_batch_delta_is_the_exact_l1_change(cuda_device):
+    """Each graph's delta of iteration k is sum |x_k - x_(k-1)| taken exactly
+    (fixed point in units of 2^-60, integer sums), for members of every kind."""
+    members = make_batch(gapgen.batch_specs(count=8, min_exp=10, max_exp=12), edge_members())
+    graphs = [gpu_graph(n, s, d, sym) for n, s, d, sym in members]
+    try:
+        prev = [np.full(g.n, np.float32(1.0 / g.n), np.float64) for g in graphs]
+        for k in (1, 2):
+            xs, st = run_batch(graphs, 0.0, k)
+            for i, g in enumerate(graphs):
+                assert st[i]["iterations"] == k
+                assert st[i]["deltas"][k - 1] == exact_l1_change(xs[i], prev[i]), (i, k)
+            prev = xs
     finally:
         for g in graphs:
             g.close()

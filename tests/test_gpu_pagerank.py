@@ -11,7 +11,7 @@ import pytest
 
 import gapgen
 import oracle
-from gpu_helpers import (D, FP64_L1, assert_fp32_parity, gpu_graph, oracle_graph, run_gpu,
+from gpu_helpers import (D, FP64_L1, assert_fp32_parity, exact_l1_change, gpu_graph, oracle_graph, run_gpu,
                          seg_bytes_for)
 from paper_1508_03619_gb300 import gap
 
@@ -77,6 +77,25 @@ def test_fp32_tolerance_mode(cuda_device, case, seg):
     np.testing.assert_allclose(st["deltas"], do[: st["iterations"]], rtol=1e-3, atol=1e-7)
     assert st["mass"] == pytest.approx(x.sum(), rel=1e-12)
     g.close()
+
+
+@pytest.mark.parametrize("seg", [False, True], ids=["whole", "segmented"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp32_delta_is_the_exact_l1_change(cuda_device, case, seg):
+    """The FP32 stop test's delta of iteration k equals sum |x_k - x_(k-1)| taken
+    exactly (fixed point in units of 2^-60, integer sums): the FP32 scores of
+    iterations 0..3 (x0 = float(1/n)) against the reported delta history."""
+    name, n, src, dst, sym = case
+    g = gpu_graph(n, src, dst, sym)
+    try:
+        prev = np.full(n, np.float32(1.0 / n), np.float64)
+        for k in (1, 2, 3):
+            x, st, _ = run_gpu(g, 0.0, k, segment_bytes=seg_bytes_for(n) if seg else 0)
+            assert st["iterations"] == k
+            assert st["deltas"][k - 1] == exact_l1_change(x, prev), (k, st["deltas"][k - 1])
+            prev = x
+    finally:
+        g.close()
 
 
 def test_fp64_deterministic_bitexact(cuda_device):
