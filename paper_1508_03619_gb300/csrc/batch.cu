@@ -484,10 +484,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_per
   }
 }
 
-// Mass of every graph in FP64: per-tile sums (one warp per 32-vertex tile),
-// then per graph the tile sums in a fixed order (one warp per graph).
+// Mass of every graph: per-tile sums (one warp per 32-vertex tile), then per
+// graph the tile sums (one warp per graph), all as exact u64 in units of 2^-60.
 __global__ void k_batch_mass_tiles(const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ tile_prefix,
-                                   double* tile_mass) {
+                                   unsigned long long* tile_mass) {
   const int lane = threadIdx.x & 31;
   const int64_t ntiles = tile_prefix[ng];
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles;
@@ -495,20 +495,20 @@ __global__ void k_batch_mass_tiles(const BatchGraph* __restrict__ gs, int ng, co
     const int i = find_graph(tile_prefix, ng, t);
     const BatchGraph& G = gs[i];
     const int64_t v = (t - tile_prefix[i]) * 32 + lane;
-    const double m = warp_sum(v < G.n ? (double)G.x[v] : 0.0);
+    const unsigned long long m = warp_sum(v < G.n ? fixed60(G.x[v]) : 0ull);
     if (lane == 0) tile_mass[t] = m;
   }
 }
 
-__global__ void k_batch_mass(int ng, const int64_t* __restrict__ tile_prefix, const double* __restrict__ tile_mass,
-                             BatchGraphState* st) {
+__global__ void k_batch_mass(int ng, const int64_t* __restrict__ tile_prefix,
+                             const unsigned long long* __restrict__ tile_mass, BatchGraphState* st) {
   const int lane = threadIdx.x & 31;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < ng;
        i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double m = 0.0;
+    unsigned long long m = 0;
     for (int64_t t = tile_prefix[i] + lane; t < tile_prefix[i + 1]; t += 32) m += tile_mass[t];
     m = warp_sum(m);
-    if (lane == 0) st[i].mass = m;
+    if (lane == 0) st[i].mass = (double)m * FIXED60_UNIT;
   }
 }
 
@@ -714,11 +714,12 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_CUDA(cudaEventRecord(ev.e[2], s));
   {
     Scratch tm;
-    GAP_TRY(tm.get(sizeof(double) * (all_tiles > 0 ? all_tiles : 1), s));
-    k_batch_mass_tiles<<<tile_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dtp.as<int64_t>(), tm.as<double>());
+    GAP_TRY(tm.get(sizeof(unsigned long long) * (all_tiles > 0 ? all_tiles : 1), s));
+    k_batch_mass_tiles<<<tile_grid, 256, 0, s>>>(dgs.as<BatchGraph>(), count, dtp.as<int64_t>(),
+                                                 tm.as<unsigned long long>());
     GAP_LAUNCH_CHECK();
-    k_batch_mass<<<stride_grid((int64_t)count * 32, 256, 8), 256, 0, s>>>(count, dtp.as<int64_t>(), tm.as<double>(),
-                                                                        dstate.as<BatchGraphState>());
+    k_batch_mass<<<stride_grid((int64_t)count * 32, 256, 8), 256, 0, s>>>(
+        count, dtp.as<int64_t>(), tm.as<unsigned long long>(), dstate.as<BatchGraphState>());
     GAP_LAUNCH_CHECK();
   }
   ++launches;

@@ -179,9 +179,64 @@ __device__ __forceinline__ Acc gather_lane(const int32_t* __restrict__ idx, cons
   return s;
 }
 
-// Kahan-compensated lane sum (Kahan 1965), returned as s - comp in FP64.
+// Lane sums of FP32 kernels are combined as an unevaluated pair of floats
+// hi + lo: hi + hi' by Knuth's error-free TwoSum, the rounding error and both
+// los added into lo.  The combination is nearly as exact as an FP64 sum but
+// runs on the FP32 pipe (this GPU's FP64 rate is a small fraction of it); one
+// lane turns the final pair into an FP64 value.  FP64 kernels combine doubles.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 red_add(F2 a, F2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+__device__ __forceinline__ double red_add(double a, double b) { return a + b; }
+__device__ __forceinline__ F2 red_shfl_xor(F2 v, int o, int width) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o, width), __shfl_xor_sync(0xffffffffu, v.lo, o, width)};
+}
+__device__ __forceinline__ double red_shfl_xor(double v, int o, int width) {
+  return __shfl_xor_sync(0xffffffffu, v, o, width);
+}
+__device__ __forceinline__ double red_value(F2 v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ double red_value(double v) { return v; }
+template <class Acc>
+struct RedOf {
+  using T = double;
+};
+template <>
+struct RedOf<float> {
+  using T = F2;
+};
+template <class Acc>
+using red_t = typename RedOf<Acc>::T;
+
+// Sum over the first `width` lanes' values, in every one of them (xor butterfly).
+template <class T>
+__device__ __forceinline__ T red_group(T v, int width) {
+  for (int o = width / 2; o > 0; o >>= 1) v = red_add(v, red_shfl_xor(v, o, width));
+  return v;
+}
+
+// Block-wide combination for blockDim.x a multiple of 32; result valid in all
+// threads.  `sh` must hold 32 elements.
+template <class T>
+__device__ __forceinline__ T red_block(T v, T* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = red_group(v, 32);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  T r = lane < nw ? sh[lane] : T{};
+  return red_group(r, 32);
+}
+
+// Kahan-compensated lane sum (Kahan 1965), returned as the pair s + (-comp).
 template <class CT>
-__device__ __forceinline__ double gather_lane_kahan(const int32_t* __restrict__ idx, const CT* __restrict__ c,
+__device__ __forceinline__ F2 gather_lane_kahan(const int32_t* __restrict__ idx, const CT* __restrict__ c,
                                                     int64_t b, int64_t e, int lane, int stride) {
   float s = 0.f, comp = 0.f;
   int64_t j = b + lane;
@@ -203,23 +258,24 @@ __device__ __forceinline__ double gather_lane_kahan(const int32_t* __restrict__ 
     comp = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
   }
-  return (double)s - (double)comp;
+  return {s, -comp};
 }
 
 // Row sum over [b, e) by one lane of a group with STRIDE lanes: FP64 kernels
-// sum in FP64; FP32 kernels sum in FP32 (Kahan when asked) and return FP64.
+// sum in FP64; FP32 kernels sum in FP32 (Kahan when asked) and return a pair.
 template <int STRIDE, class Acc>
-__device__ __forceinline__ double lane_sum(const PrArgs<Acc>& a, const void* cin, bool rb, int64_t b, int64_t e,
-                                           int lane, bool kahan) {
+__device__ __forceinline__ red_t<Acc> lane_sum(const PrArgs<Acc>& a, const void* cin, bool rb, int64_t b, int64_t e,
+                                               int lane, bool kahan) {
   if constexpr (std::is_same<Acc, double>::value) {
     return gather_lane<STRIDE, double, double>(a.idx, reinterpret_cast<const double*>(cin), b, e, lane);
   } else {
     if (kahan)
       return rb ? gather_lane_kahan(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin), b, e, lane, STRIDE)
                 : gather_lane_kahan(a.idx, reinterpret_cast<const float*>(cin), b, e, lane, STRIDE);
-    return rb ? (double)gather_lane<STRIDE, float, __nv_bfloat16>(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin),
-                                                                  b, e, lane)
-              : (double)gather_lane<STRIDE, float, float>(a.idx, reinterpret_cast<const float*>(cin), b, e, lane);
+    const float t = rb ? gather_lane<STRIDE, float, __nv_bfloat16>(a.idx, reinterpret_cast<const __nv_bfloat16*>(cin),
+                                                                   b, e, lane)
+                       : gather_lane<STRIDE, float, float>(a.idx, reinterpret_cast<const float*>(cin), b, e, lane);
+    return F2{t, 0.f};
   }
 }
 
@@ -732,15 +788,15 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_group(PrArgs<Acc> a) {
 // ---- CTA-per-row kernel ------------------------------------------------------
 template <class Acc>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_cta(PrArgs<Acc> a) {
-  __shared__ double sh[32];
+  __shared__ red_t<Acc> sh[32];
   const IterState st = iter_state(a);
   delta_t<Acc> dl = 0;
   for (int64_t i = a.begin + blockIdx.x; i < a.end; i += gridDim.x) {
     const int64_t v = a.list[i];
     const int64_t b = a.off[v], e = a.off[v + 1];
-    const double part = lane_sum<PR_THREADS>(a, st.cin, st.rb, b, e, threadIdx.x, a.kahan != 0);
-    const double tot = block_sum(part, sh);
-    if (threadIdx.x == 0) dl += update_row(a, v, (Acc)tot, st.cout, st.wb);
+    const red_t<Acc> part = lane_sum<PR_THREADS>(a, st.cin, st.rb, b, e, threadIdx.x, a.kahan != 0);
+    const red_t<Acc> tot = red_block(part, sh);
+    if (threadIdx.x == 0) dl += update_row(a, v, (Acc)red_value(tot), st.cout, st.wb);
   }
   write_partial(dl, a.partial);
 }
@@ -761,7 +817,7 @@ template <class Acc, bool SEG>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_hub_chunks(PrArgs<Acc> a, SegArgs sg, int s,
                                                                  const int64_t* __restrict__ cstart, int64_t nhubs,
                                                                  int64_t chunk, double* __restrict__ csum) {
-  __shared__ double sh[32];
+  __shared__ red_t<Acc> sh[32];
   const IterState st = iter_state(a);
   const int64_t total = cstart[nhubs];
   for (int64_t cid = blockIdx.x; cid < total; cid += gridDim.x) {
@@ -779,9 +835,9 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_hub_chunks(PrArgs<Acc> a, S
     }
     const int64_t b = rb + (cid - cstart[h]) * chunk;
     const int64_t e = b + chunk < re ? b + chunk : re;
-    const double part = lane_sum<PR_THREADS>(a, st.cin, st.rb, b, e, threadIdx.x, a.kahan != 0);
-    const double tot = block_sum(part, sh);
-    if (threadIdx.x == 0) csum[cid] = tot;
+    const red_t<Acc> part = lane_sum<PR_THREADS>(a, st.cin, st.rb, b, e, threadIdx.x, a.kahan != 0);
+    const red_t<Acc> tot = red_block(part, sh);
+    if (threadIdx.x == 0) csum[cid] = red_value(tot);
   }
 }
 
@@ -840,11 +896,9 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_group_seg(PrArgs<Acc> a, Se
       deg = __ldcs(bd + sg.S - 1);
     }
     const bool kahan = a.kahan && deg > a.kahan_thr;
-    double t = lane_sum<G>(a, st.cin, st.rb, b, e, lane, kahan);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, G);
+    const red_t<Acc> t = red_group(lane_sum<G>(a, st.cin, st.rb, b, e, lane, kahan), G);
     if (has && lane == 0) {
-      const double run = s ? __ldcs(sg.pp + li) + t : t;
+      const double run = s ? __ldcs(sg.pp + li) + red_value(t) : red_value(t);
       if (!last)
         __stcs(sg.pp + li, run);
       else
@@ -1099,22 +1153,28 @@ __global__ void k_ctrl_init(PrCtrl* ctrl, int write_bf16, int ladder, double lad
   }
 }
 
+// Sum of the scores (reported as the mass), in the delta's number type: exact
+// u64 in units of 2^-60 for FP32 scores, FP64 in a fixed order for FP64 scores.
+__device__ __forceinline__ unsigned long long mass_term(float v) { return fixed60(v); }
+__device__ __forceinline__ double mass_term(double v) { return v; }
+
 template <class Acc>
-__global__ void k_mass_partial(const Acc* __restrict__ x, int64_t n, double* __restrict__ partial) {
-  __shared__ double sh[32];
-  double s = 0.0;
+__global__ void k_mass_partial(const Acc* __restrict__ x, int64_t n, delta_t<Acc>* __restrict__ partial) {
+  __shared__ delta_t<Acc> sh[32];
+  delta_t<Acc> s = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    s += (double)x[v];
+    s += mass_term(x[v]);
   s = block_sum(s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void k_mass_final(PrCtrl* ctrl, const double* __restrict__ partial, int np) {
-  __shared__ double sh[32];
-  double s = 0.0;
+template <class T>
+__global__ void k_mass_final(PrCtrl* ctrl, const T* __restrict__ partial, int np) {
+  __shared__ T sh[32];
+  T s = 0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) ctrl->st.mass = s;
+  if (threadIdx.x == 0) ctrl->st.mass = delta_value(s);
 }
 
 // ---- work-list checks (options.check_worklists) ------------------------------
@@ -2038,9 +2098,9 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     const int mg = stride_grid(n, 256, 4);
     Scratch mp;
     GAP_TRY(mp.get(sizeof(double) * mg, s));
-    k_mass_partial<Acc><<<mg, 256, 0, s>>>(x, n, mp.as<double>());
+    k_mass_partial<Acc><<<mg, 256, 0, s>>>(x, n, mp.as<delta_t<Acc>>());
     GAP_LAUNCH_CHECK();
-    k_mass_final<<<1, 1024, 0, s>>>(dctrl, mp.as<double>(), mg);
+    k_mass_final<<<1, 1024, 0, s>>>(dctrl, mp.as<delta_t<Acc>>(), mg);
     GAP_LAUNCH_CHECK();
   }
   if (!user_dev) GAP_CUDA(cudaMemcpyAsync(user_scores, x, xbytes, cudaMemcpyDefault, s));
@@ -2386,9 +2446,9 @@ static gap_status run_trial_binned(gap_graph* g, double d, double tol, int32_t m
     const int mg = stride_grid(n, 256, 4);
     Scratch mp;
     GAP_TRY(mp.get(sizeof(double) * mg, s));
-    k_mass_partial<float><<<mg, 256, 0, s>>>(x, n, mp.as<double>());
+    k_mass_partial<float><<<mg, 256, 0, s>>>(x, n, mp.as<unsigned long long>());
     GAP_LAUNCH_CHECK();
-    k_mass_final<<<1, 1024, 0, s>>>(dctrl, mp.as<double>(), mg);
+    k_mass_final<<<1, 1024, 0, s>>>(dctrl, mp.as<unsigned long long>(), mg);
     GAP_LAUNCH_CHECK();
   }
   if (!user_dev) GAP_CUDA(cudaMemcpyAsync(user_scores, x, xbytes, cudaMemcpyDefault, s));
@@ -2675,9 +2735,9 @@ extern "C" gap_status gap_pr_run_noalloc(gap_graph_t* g, double damping, double 
     if (*g->flag_host) break;
   }
   const int mg = stride_grid(n, 256, 4);
-  k_mass_partial<float><<<mg, 256, 0, s>>>(scores, n, partial);
+  k_mass_partial<float><<<mg, 256, 0, s>>>(scores, n, dpartial);
   GAP_LAUNCH_CHECK();
-  k_mass_final<<<1, 1024, 0, s>>>(dctrl, partial, mg);
+  k_mass_final<<<1, 1024, 0, s>>>(dctrl, dpartial, mg);
   GAP_LAUNCH_CHECK();
   GAP_CUDA(cudaMemcpyAsync(g->stats_host, &dctrl->st, sizeof(gap_pr_stats_t), cudaMemcpyDeviceToHost, s));
   // the mass kernels and the stats copy still read the shared array: wait for

@@ -74,3 +74,10 @@ def exact_l1_change(x, prev):
     b = np.asarray(prev, np.float32).astype(np.float64) * 2.0 ** 60
     total = sum(abs(int(p) - int(q)) for p, q in zip(a, b))
     return float(total) * 2.0 ** -60
+
+
+def exact_sum(x):
+    """sum x over FP32 scores taken exactly the same way (integers in units of
+    2^-60, one conversion to double at the end): the reported mass."""
+    a = np.asarray(x, np.float32).astype(np.float64) * 2.0 ** 60
+    return float(sum(int(p) for p in a)) * 2.0 ** -60

@@ -6,7 +6,7 @@ import pytest
 
 import gapgen
 import oracle
-from gpu_helpers import D, FP32_L1, FP32_REL, exact_l1_change, gpu_graph, oracle_graph
+from gpu_helpers import D, FP32_L1, FP32_REL, exact_l1_change, exact_sum, gpu_graph, oracle_graph
 from paper_1508_03619_gb300 import gap
 
 pytestmark = pytest.mark.gpu
@@ -205,6 +205,7 @@ def test_batch_delta_is_the_exact_l1_change(cuda_device):
             for i, g in enumerate(graphs):
                 assert st[i]["iterations"] == k
                 assert st[i]["deltas"][k - 1] == exact_l1_change(xs[i], prev[i]), (i, k)
+                assert st[i]["mass"] == exact_sum(xs[i])
             prev = xs
     finally:
         for g in graphs:

@@ -11,8 +11,8 @@ import pytest
 
 import gapgen
 import oracle
-from gpu_helpers import (D, FP64_L1, assert_fp32_parity, exact_l1_change, gpu_graph, oracle_graph, run_gpu,
-                         seg_bytes_for)
+from gpu_helpers import (D, FP64_L1, assert_fp32_parity, exact_l1_change, exact_sum, gpu_graph, oracle_graph,
+                         run_gpu, seg_bytes_for)
 from paper_1508_03619_gb300 import gap
 
 pytestmark = pytest.mark.gpu
@@ -93,6 +93,7 @@ def test_fp32_delta_is_the_exact_l1_change(cuda_device, case, seg):
             x, st, _ = run_gpu(g, 0.0, k, segment_bytes=seg_bytes_for(n) if seg else 0)
             assert st["iterations"] == k
             assert st["deltas"][k - 1] == exact_l1_change(x, prev), (k, st["deltas"][k - 1])
+            assert st["mass"] == exact_sum(x)
             prev = x
     finally:
         g.close()
