@@ -16,10 +16,11 @@
 // A set-up pass per call (inside the timed region: the split is a run-time
 // decision on the input, §2.3) counts and lists the chunks of every graph.
 //
-// Per iteration every warp walks the tasks of the graphs still running
-// (grid-stride), and each task adds its |x' - x| to its graph's accumulator as
-// a 64-bit fixed-point integer (units of 2^-60, exact integer atomics, so the
-// graph's delta does not depend on the order in which tasks finish).  After
+// Per iteration the warps take the tasks of the graphs still running (handed
+// out one at a time by a counter), and each task adds its |x' - x| to its
+// graph's accumulator as a 64-bit fixed-point integer (units of 2^-60, exact
+// integer atomics, so the graph's delta does not depend on which warp ran
+// which task or in what order the tasks finished).  After
 // one grid barrier every block reads all accumulators and takes the same stop
 // decision for every graph; accumulators rotate over three buffers so that
 // zeroing the next one never races with readers of the previous one.
@@ -58,6 +59,7 @@ struct BatchCtrl {
   int32_t iter;   // iterations the batch ran (max over graphs)
   int64_t ntasks;
   int64_t nchunks;
+  unsigned long long task_next[3];  // per iteration (mod 3): the next active task to hand out
 };
 
 struct BatchGraphState {
@@ -406,9 +408,9 @@ __device__ __forceinline__ void run_task(const BatchGraph* __restrict__ gs, int 
 // The 512-thread kernel is held to three resident blocks per SM (<= 42
 // registers a thread): the loop is bound by memory latency, and with an open
 // register budget the compiler took 56 registers, leaving two blocks per SM.
-// With COMPACT, warps stride over the active graphs' tasks only (a graph
-// that has stopped costs nothing); otherwise they stride over every task and
-// skip those of stopped graphs.
+// With COMPACT, warps take the active graphs' tasks only (a graph that has
+// stopped costs nothing), handed out by a counter; otherwise they stride over
+// every task and skip those of stopped graphs.
 template <int THREADS, bool COMPACT>
 __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_persistent(
     const BatchGraph* __restrict__ gs, int ng, const int64_t* __restrict__ task_base,
@@ -436,12 +438,21 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_per
     const int parity = it & 1;
     unsigned long long* acc_now = acc + (int64_t)(it % 3) * ng;
     if (COMPACT) {
+      // tasks handed out one at a time by a counter, so warps that drew cheap
+      // tasks take more of them; a warp's next grab is in flight while its
+      // current task runs
       const int na = nact;
       const int64_t total = abase[na];
+      unsigned long long* tnext = &ctrl->task_next[it % 3];
+      unsigned long long g = 0;
+      if ((threadIdx.x & 31) == 0) g = atomicAdd(tnext, 1ull);
+      int64_t task = (int64_t)__shfl_sync(0xffffffffu, g, 0);
       int k = 0;
-      for (int64_t task = warp; task < total; task += nwarps) {
-        while (k + 1 < na && abase[k + 1] <= task) ++k;  // a warp's tasks only move forward
+      while (task < total) {
+        if ((threadIdx.x & 31) == 0) g = atomicAdd(tnext, 1ull);
+        while (k + 1 < na && abase[k + 1] <= task) ++k;  // a warp's grabs only move forward
         run_task(gs, agraph[k], task - abase[k], chunk_base, desc, partial, ctr, acc_now, parity, d, heavy);
+        task = (int64_t)__shfl_sync(0xffffffffu, g, 0);
       }
     } else {
       int i = 0;
@@ -451,9 +462,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 ? 3 : 1)) k_batch_per
         run_task(gs, i, task - __ldg(task_base + i), chunk_base, desc, partial, ctr, acc_now, parity, d, heavy);
       }
     }
-    if (blockIdx.x == 0) {  // the accumulator of iteration it+1 starts at zero
+    if (blockIdx.x == 0) {  // the accumulator and task counter of iteration it+1 start at zero
       unsigned long long* acc_next = acc + (int64_t)((it + 1) % 3) * ng;
       for (int i = threadIdx.x; i < ng; i += THREADS) acc_next[i] = 0ull;
+      if (COMPACT && threadIdx.x == 0) ctrl->task_next[(it + 1) % 3] = 0ull;
     }
     if (!grid_barrier(ctrl, nb)) return;
     // every block takes the same stop decision for every graph
