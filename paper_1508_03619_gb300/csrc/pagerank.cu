@@ -468,18 +468,26 @@ __device__ __forceinline__ int arc_row(const TileRows& t, int jv, int64_t* pos, 
 }
 
 // cnt8[s][v] = arcs of small row v in segment s; ttot[s][tile] = tile totals.
+constexpr int COUNT_ROW_WORDS = 33;  // histogram words per segment (32 rows + 1 pad)
+// The per-warp histogram is segment-major with one word of padding per
+// segment (h[s*33 + row]): the per-segment reads at the end, and the adds of
+// one row's runs in several segments, fall in different banks.  Within a 32-arc batch the
+// (row, segment) keys come in runs (rows ascend, and a row's sources ascend),
+// so each run is counted once by its first lane: a shuffle finds the run
+// heads, a ballot their positions, and the head adds the run's length.
 __global__ void __launch_bounds__(PACK_THREADS) k_small_count(const int64_t* __restrict__ off,
                                                                const int32_t* __restrict__ idx, int64_t n,
                                                                int64_t small_max, int S, int wbits,
                                                                uint8_t* __restrict__ cnt8, uint32_t* __restrict__ ttot,
                                                                int64_t T) {
   extern __shared__ uint32_t pack_sh[];
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* h = pack_sh + warp * 32 * S;
+  uint32_t* h = pack_sh + warp * COUNT_ROW_WORDS * S;
   const int64_t gw = ((int64_t)blockIdx.x * PACK_THREADS + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * PACK_THREADS) >> 5;
   for (int64_t tile = gw; tile < T; tile += nw) {
-    for (int q = lane; q < 32 * S; q += 32) h[q] = 0;
+    for (int q = lane; q < COUNT_ROW_WORDS * S; q += 32) h[q] = 0;
     __syncwarp();
     const int64_t v = tile * 32 + lane;
     const TileRows tr = tile_rows(off, n, v, small_max);
@@ -488,15 +496,20 @@ __global__ void __launch_bounds__(PACK_THREADS) k_small_count(const int64_t* __r
       int64_t pos;
       int ex;
       const int r = arc_row(tr, jv, &pos, &ex);
-      const int key = jv < tr.total ? r * S + (idx[pos] >> wbits) : -1;
-      const unsigned peers = __match_any_sync(0xffffffffu, key);  // one add per distinct key
-      if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) h[key] += __popc(peers);
+      const int key = jv < tr.total ? (idx[pos] >> wbits) * COUNT_ROW_WORDS + r : -1;  // past the end: one run of -1
+      const int prev = __shfl_up_sync(FULL, key, 1);
+      const bool head = lane == 0 || key != prev;
+      const unsigned heads = __ballot_sync(FULL, head);
+      if (head && key >= 0) {
+        const unsigned later = lane == 31 ? 0u : heads >> (lane + 1);
+        h[key] += later ? (unsigned)__ffs(later) : (unsigned)(32 - lane);  // the run's length
+      }
+      __syncwarp();
     }
-    __syncwarp();
     for (int sg = 0; sg < S; ++sg) {
-      const uint32_t c = h[lane * S + sg];
+      const uint32_t c = h[sg * COUNT_ROW_WORDS + lane];
       if (v < n) cnt8[(int64_t)sg * n + v] = (uint8_t)c;
-      const uint32_t tot = warp_sum(c);
+      const uint32_t tot = __reduce_add_sync(FULL, c);
       if (lane == 0) ttot[(int64_t)sg * T + tile] = tot;
     }
     __syncwarp();
@@ -1749,7 +1762,7 @@ static gap_status run_trial(gap_graph* g, double d, double tol, int32_t max_iter
     GAP_TRY(sm_pp.get(sizeof(Acc) * n, s));
     int wbits = 0;
     while ((int64_t(1) << wbits) < t.seg_width) ++wbits;
-    const size_t count_smem = sizeof(uint32_t) * PACK_WARPS * 32 * S;
+    const size_t count_smem = sizeof(uint32_t) * PACK_WARPS * COUNT_ROW_WORDS * S;
     GAP_CUDA(cudaFuncSetAttribute(k_small_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem));
     k_small_count<<<stride_grid(T * 32, PACK_THREADS, 16), PACK_THREADS, count_smem, s>>>(
         g->in_off, g->in_idx, n, t.bin[BIN_ZERO].hi, S, wbits, sm_cnt.as<uint8_t>(), sm_ttot.as<uint32_t>(), T);
