@@ -70,35 +70,3 @@ def test_clock_record():
     assert c["reasons"] == ["sw_power_cap"]
     assert bench.parse_clock_samples([])["reasons"] == ["no samples"]
 
-
-def test_oracle_paused_stops_and_resumes_the_child():
-    """The e2e leg pauses the oracle child with SIGSTOP and always resumes it."""
-    import multiprocessing as mp
-    import time
-
-    import bench
-
-    ctx = mp.get_context("spawn")
-    p = ctx.Process(target=time.sleep, args=(30,))
-    p.start()
-    try:
-        def state():
-            with open(f"/proc/{p.pid}/stat") as f:
-                return f.read().split(")")[-1].split()[0]
-        with bench.OraclePaused(p) as paused:
-            assert paused.stopped
-            for _ in range(100):
-                if state() == "T":
-                    break
-                time.sleep(0.01)
-            assert state() == "T"
-        for _ in range(100):
-            if state() != "T":
-                break
-            time.sleep(0.01)
-        assert state() in ("S", "R")
-        with bench.OraclePaused(None) as none:  # no child: nothing to do
-            assert not none.stopped
-    finally:
-        p.kill()
-        p.join()
