@@ -49,7 +49,7 @@ struct BatchGraph {
   int64_t n;
   int64_t tiles;  // ceil(n / 32)
   float base;     // (1 - d) / n of this graph
-  float pad;
+  float x0;       // 1 / n of this graph, rounded once on the host
 };
 
 struct BatchCtrl {
@@ -297,7 +297,7 @@ __global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng, const in
     const BatchGraph& G = gs[i];
     const int64_t v = (t - tile_prefix[i]) * 32 + lane;
     if (v < G.n) {
-      const float x0 = (float)(1.0 / (double)G.n);
+      const float x0 = G.x0;
       G.x[v] = x0;
       const int od = G.outdeg[v];
       G.c0[v] = od > 0 ? x0 / (float)od : 0.f;
@@ -601,7 +601,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
     hg[i].n = g->n;
     hg[i].tiles = (g->n + 31) / 32;
     hg[i].base = (float)((1.0 - damping) / (double)g->n);
-    hg[i].pad = 0.f;
+    hg[i].x0 = (float)(1.0 / (double)g->n);
     hcg[i].off = g->in_off;
     hcg[i].n = g->n;
     tile_prefix[i + 1] = tile_prefix[i] + hg[i].tiles;
