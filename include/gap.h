@@ -224,7 +224,10 @@ GAP_API gap_status gap_graph_build_flags(const gap_graph_t* g, uint32_t* flags);
  * paper), tol = stop threshold on the summed absolute change (1e-4 in the paper;
  * 0 = run max_iters iterations), max_iters >= 0.  `scores` receives n FP32
  * scores (device or host memory; a host buffer is filled by a D2H copy at the
- * end of the run).  FP32 scores, FP32 accumulation, FP64 convergence reduction. */
+ * end of the run).  FP32 scores and FP32 accumulation.  The convergence test's
+ * delta is exact: each row's |x' - x| is taken as an integer in units of 2^-60
+ * (every FP32 score >= 2^-37 is a multiple of 2^-60) and the terms are summed as
+ * 64-bit integers, then converted to a double once. */
 GAP_API gap_status gap_pr_run(gap_graph_t* g, double damping, double tol, int32_t max_iters,
                       float* scores, void* stream);
 
@@ -327,8 +330,9 @@ GAP_API gap_status gap_pr_run_ex(gap_graph_t* g, double damping, double tol, int
 typedef struct {
   int32_t iterations;   /* iterations performed */
   int32_t converged;    /* 1 when the last delta < tol */
-  double final_delta;   /* summed |x_k - x_{k-1}| of the last iteration (FP64) */
-  double mass;          /* sum of the returned scores, FP64 */
+  double final_delta;   /* summed |x_k - x_{k-1}| of the last iteration (FP32 scores:
+                           exact in units of 2^-60, then a double; FP64: FP64 sums) */
+  double mass;          /* sum of the returned scores (taken the same way) */
   int32_t bf16_iters;   /* iterations that gathered BF16 contributions */
   int32_t device_error; /* 0, or a GAP_ERR_* raised on the device */
   double delta_hist[GAP_PR_HIST]; /* per-iteration deltas (first GAP_PR_HIST) */
@@ -364,10 +368,10 @@ GAP_API gap_status gap_pr_stats(gap_graph_t* g, gap_pr_stats_t* out);
  * tuning.heavy_min_degree in-arcs are gathered in chunks of at most
  * tuning.chunk_arcs arcs by separate warps and their chunk sums added in chunk
  * order; lighter rows are pulled 32 consecutive vertices per warp in vertex
- * order.  A graph's L1 delta is the sum of per-task FP64 deltas, each rounded
- * to a multiple of 2^-60 and added as integers (exact and independent of
- * the order in which tasks finish), so a graph's result does not depend on the
- * other graphs in the batch.
+ * order.  A graph's L1 delta is the sum of its rows' |x' - x|, each taken
+ * exactly as an integer in units of 2^-60 and added as integers (exact and
+ * independent of the order in which tasks finish), so a graph's result does not
+ * depend on the other graphs in the batch.
  *  - graphs: count handles (count <= GAP_BATCH_MAX_GRAPHS), all on the
  *    current device, each with fewer than 2^31 vertices; scores: count device
  *    pointers, scores[i] holding graphs[i]'s n_i floats (caller-owned; the
@@ -615,8 +619,8 @@ GAP_API gap_status gap_selftest_check_packed(int64_t n, const int64_t* off, cons
  * the library's allocator hook cannot reach), and latency-critical paths that
  * must never wait on an allocator or run out of memory half-way through.
  *
- * Same result contract as gap_pr_run (FP32 scores, FP32 accumulation, FP64
- * convergence reduction), but all scratch lives in one static device array of
+ * Same result contract as gap_pr_run (FP32 scores, FP32 accumulation, exact
+ * fixed-point convergence delta), but all scratch lives in one static device array of
  * about 8 MB that every GPU loading the library holds until the process exits.
  * It calls no cudaMalloc, cudaFree or other allocating routine.
  *  - Limits: at most GAP_NOALLOC_MAX_VERTICES vertices and fewer than 2^31
