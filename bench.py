@@ -52,7 +52,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # ncu DRAM bytes of one k_batch_persistent launch on the 256-graph batch with this
 # tuning (one capture of that launch; the batch is its own small case)
-BATCH_NCU_TRAFFIC = 17.279e9
+BATCH_NCU_TRAFFIC = None  # no capture of the current kernel yet
 BATCH_NCU_TUNING = {"heavy_min_degree": 512, "chunk_arcs": 2048, "block_threads": 512, "blocks_per_sm": 0}
 # ncu DRAM bytes (read + write) of one launch of each segmented pull kernel on the
 # small case (kron26 at edge factor 4: the benchmark's vertex count and source

@@ -47,9 +47,11 @@ struct BatchGraph {
   float* c0;
   float* c1;
   int64_t n;
-  int64_t tiles;  // ceil(n / 32)
+  int64_t tiles;  // light tasks: ceil(n / 32), or ceil(n / 64) for a pair graph
   float base;     // (1 - d) / n of this graph
   float x0;       // 1 / n of this graph, rounded once on the host
+  int32_t pair;   // every row has <= PAIR_ROWS_MAX in-arcs: light tasks of 64 rows
+  int32_t pad;
 };
 
 struct BatchCtrl {
@@ -82,6 +84,7 @@ __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefe
 
 constexpr unsigned long long BARRIER_WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int TILE_LANE_ROWS_MAX = 8;  // light tiles whose rows all have <= 8 in-arcs: a lane per row
+constexpr int PAIR_ROWS_MAX = 4;       // graphs whose rows all have <= 4 in-arcs: a lane per row pair
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -225,6 +228,47 @@ __device__ unsigned long long pull_tile(const BatchGraph& G, int64_t tile, int p
   return warp_sum(dl);
 }
 
+// One light task of a pair graph (every row has at most PAIR_ROWS_MAX in-arcs,
+// e.g. grids and road networks): lane l sums rows 64*task + l and + l + 32,
+// the loads of both rows in flight at once, each row in arc order as pull_tile's
+// lane-per-row path sums it.  Not inlined, so the registers it needs do not
+// raise the pressure on the warp-merge path of the other graphs.
+__device__ __noinline__ unsigned long long pull_pair(const BatchGraph& G, int64_t task, int parity, float d) {
+  const int lane = threadIdx.x & 31;
+  const float* cin = parity ? G.c1 : G.c0;
+  float* cout = parity ? G.c0 : G.c1;
+  const int64_t v0 = task * 64 + lane, v1 = v0 + 32;
+  const bool ok0 = v0 < G.n, ok1 = v1 < G.n;
+  const int64_t b0 = ok0 ? __ldg(G.off + v0) : 0, e0 = ok0 ? __ldg(G.off + v0 + 1) : 0;
+  const int64_t b1 = ok1 ? __ldg(G.off + v1) : 0, e1 = ok1 ? __ldg(G.off + v1 + 1) : 0;
+  const float xo0 = ok0 ? __ldcg(G.x + v0) : 0.f, xo1 = ok1 ? __ldcg(G.x + v1) : 0.f;
+  const int od0 = ok0 ? __ldg(G.outdeg + v0) : 0, od1 = ok1 ? __ldg(G.outdeg + v1) : 0;
+  const int d0 = (int)(e0 - b0), d1 = (int)(e1 - b1);
+  float a0[PAIR_ROWS_MAX], a1[PAIR_ROWS_MAX];
+#pragma unroll
+  for (int k = 0; k < PAIR_ROWS_MAX; ++k) {
+    a0[k] = k < d0 ? gather_c(cin + load_idx(G.idx + b0 + k)) : 0.f;
+    a1[k] = k < d1 ? gather_c(cin + load_idx(G.idx + b1 + k)) : 0.f;
+  }
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < PAIR_ROWS_MAX; ++k) s0 = __fadd_rn(s0, a0[k]), s1 = __fadd_rn(s1, a1[k]);
+  unsigned long long dl = 0;
+  if (ok0) {
+    const float xn = __fadd_rn(G.base, __fmul_rn(d, s0));
+    __stcg(G.x + v0, xn);
+    __stcg(cout + v0, od0 > 0 ? xn / (float)od0 : 0.f);
+    dl += fixed60_absdiff(xn, xo0);
+  }
+  if (ok1) {
+    const float xn = __fadd_rn(G.base, __fmul_rn(d, s1));
+    __stcg(G.x + v1, xn);
+    __stcg(cout + v1, od1 > 0 ? xn / (float)od1 : 0.f);
+    dl += fixed60_absdiff(xn, xo1);
+  }
+  return warp_sum(dl);
+}
+
 // Update of one row from its finished in-sum; returns |x' - x| (units of 2^-60).
 __device__ __forceinline__ unsigned long long update_row(const BatchGraph& G, int64_t v, float sum, int parity, float d) {
   float* cout = parity ? G.c0 : G.c1;
@@ -305,12 +349,12 @@ __global__ void k_batch_init(const BatchGraph* __restrict__ gs, int ng, const in
   }
 }
 
-// Task bases (tiles before graph i, from the host, plus chunks before graph
+// Task bases (light tasks before graph i, from the host, plus chunks before graph
 // i), per-graph state reset and the control block.
-__global__ void k_batch_plan(int ng, const int64_t* __restrict__ tile_prefix, const int64_t* __restrict__ chunk_base,
+__global__ void k_batch_plan(int ng, const int64_t* __restrict__ light_prefix, const int64_t* __restrict__ chunk_base,
                              int64_t* task_base, BatchGraphState* st, BatchCtrl* ctrl) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= ng; i += gridDim.x * blockDim.x) {
-    task_base[i] = tile_prefix[i] + chunk_base[i];
+    task_base[i] = light_prefix[i] + chunk_base[i];
     if (i < ng) st[i].iterations = 0;  // the rest of the state was zeroed on the stream
     if (i == ng) {
       memset(ctrl, 0, sizeof(BatchCtrl));
@@ -397,7 +441,7 @@ __device__ __forceinline__ void run_task(const BatchGraph* __restrict__ gs, int 
   const BatchGraph& G = gs[i];
   unsigned long long dl;
   if (local < G.tiles) {
-    dl = pull_tile<2>(G, local, parity, d, heavy);
+    dl = G.pair ? pull_pair(G, local, parity, d) : pull_tile<2>(G, local, parity, d, heavy);
   } else {
     const int64_t cid = __ldg(chunk_base + i) + (local - G.tiles);
     dl = pull_chunk(G, desc[cid], cid, partial, ctr, parity, d);
@@ -577,7 +621,8 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_CUDA(cudaGetDevice(&dev));
   std::vector<BatchGraph> hg(count);
   std::vector<ChunkGraph> hcg(count);
-  std::vector<int64_t> tile_prefix(count + 1, 0);
+  std::vector<int64_t> tile_prefix(count + 1, 0);   // 32-vertex tiles (set-up and mass kernels)
+  std::vector<int64_t> light_prefix(count + 1, 0);  // light tasks
   int64_t cells = 0, chunk_cap = 0;
   for (int i = 0; i < count; ++i) {
     gap_graph* g = graphs[i];
@@ -599,12 +644,15 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
     hg[i].outdeg = g->outdeg;
     hg[i].x = scores[i];
     hg[i].n = g->n;
-    hg[i].tiles = (g->n + 31) / 32;
+    hg[i].pair = g->max_in_degree <= PAIR_ROWS_MAX ? 1 : 0;
+    hg[i].pad = 0;
+    hg[i].tiles = hg[i].pair ? (g->n + 63) / 64 : (g->n + 31) / 32;
     hg[i].base = (float)((1.0 - damping) / (double)g->n);
     hg[i].x0 = (float)(1.0 / (double)g->n);
     hcg[i].off = g->in_off;
     hcg[i].n = g->n;
-    tile_prefix[i + 1] = tile_prefix[i] + hg[i].tiles;
+    tile_prefix[i + 1] = tile_prefix[i] + (g->n + 31) / 32;
+    light_prefix[i + 1] = light_prefix[i] + hg[i].tiles;
     cells += 2 * g->n;
     chunk_cap += chunk_capacity(g->m, tu.heavy_min_degree, tu.chunk_arcs);
   }
@@ -622,7 +670,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   const int nsm = device_info().sms;
   const int grid = nsm * per_sm;
 
-  Scratch cbuf, dgs, dstate, dctrl, dtb, dcb, dtp, dcg, ddesc, dpart, dctr, dacc;
+  Scratch cbuf, dgs, dstate, dctrl, dtb, dcb, dtp, dlp, dcg, ddesc, dpart, dctr, dacc;
   GAP_TRY(cbuf.get(sizeof(float) * cells, s));
   int64_t pos = 0;
   for (int i = 0; i < count; ++i) {
@@ -636,6 +684,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_TRY(dtb.get(sizeof(int64_t) * (count + 1), s));
   GAP_TRY(dcb.get(sizeof(int64_t) * (count + 1), s));
   GAP_TRY(dtp.get(sizeof(int64_t) * (count + 1), s));
+  GAP_TRY(dlp.get(sizeof(int64_t) * (count + 1), s));
   GAP_TRY(dcg.get(sizeof(ChunkGraph) * count, s));
   GAP_TRY(ddesc.get(sizeof(ChunkDesc) * chunk_cap, s));
   GAP_TRY(dpart.get(sizeof(float) * chunk_cap, s));
@@ -654,6 +703,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   GAP_CUDA(cudaMemsetAsync(dacc.p, 0, sizeof(unsigned long long) * 3 * count, s));
   GAP_CUDA(cudaEventRecord(ev.e[0], s));
   GAP_CUDA(cudaMemcpyAsync(dtp.p, tile_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  GAP_CUDA(cudaMemcpyAsync(dlp.p, light_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
   GAP_CUDA(cudaMemcpyAsync(dcg.p, hcg.data(), sizeof(ChunkGraph) * count, cudaMemcpyHostToDevice, s));
   const int64_t all_tiles = tile_prefix[count];
   const int tile_grid = stride_grid(all_tiles * 32, 256, 8);
@@ -663,7 +713,7 @@ extern "C" gap_status gap_pr_run_batch_ex(gap_graph_t* const* graphs, int32_t co
   ChunkBuilder cb;
   GAP_TRY(build_chunks(&cb, dcg.as<ChunkGraph>(), hcg.data(), count, tu.heavy_min_degree, tu.chunk_arcs,
                        ddesc.as<ChunkDesc>(), dctr.as<unsigned int>(), dcb.as<int64_t>(), s));
-  k_batch_plan<<<(count + 256) / 256, 256, 0, s>>>(count, dtp.as<int64_t>(), dcb.as<int64_t>(), dtb.as<int64_t>(),
+  k_batch_plan<<<(count + 256) / 256, 256, 0, s>>>(count, dlp.as<int64_t>(), dcb.as<int64_t>(), dtb.as<int64_t>(),
                                                    dstate.as<BatchGraphState>(), dctrl.as<BatchCtrl>());
   GAP_LAUNCH_CHECK();
   int launches = 5;
