@@ -6,7 +6,10 @@
 // Work items ("tasks"), laid out graph after graph:
 //   light tile  — 32 consecutive vertices of one graph; rows with in-degree
 //                 <= heavy_min_degree are pulled with the vertex-order
-//                 warp-merge reduction (heavier rows of the tile are skipped);
+//                 warp-merge reduction (heavier rows of the tile are skipped),
+//                 or one lane per row when none has more than 8 in-arcs; in a
+//                 graph whose rows all have at most 4 in-arcs a light task is
+//                 64 vertices, a lane summing two rows;
 //   row chunk   — up to chunk_arcs consecutive in-arcs of one heavy row,
 //                 gathered by a warp with coalesced index loads.  A row of one
 //                 chunk is updated by that warp; for a row of several chunks
